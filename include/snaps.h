@@ -1,0 +1,230 @@
+/*
+ * snaps.h -- C ABI of libsnaps, the B300 (sm_103a) hot path of SNAPS
+ * population outlier detection (Gowanlock et al., arXiv 2405.20176).
+ *
+ * The library computes, for N objects with F <= 15 features and any set of
+ * feature subspaces (bitmasks, Eq. 1), the exact distance similarity
+ * self-join (DSSJ, Sec. 3.5) and k-nearest-neighbour self-join (kNNSJ,
+ * Sec. 3.6) and the four per-object outlier metrics derived from them
+ * (Sec. 3.5.1, 3.6.1; Table 2): eps-neighbour count, mean eps-neighbour
+ * distance, kNN in-degree and mean kNN distance, with their rankings.
+ *
+ * Conventions shared by every entry point
+ *  - Every call returns a snaps_status and never aborts the process.  On
+ *    failure snaps_last_error() gives a message for the calling thread.
+ *  - Pointers are plain host or device pointers; the library tells them
+ *    apart with cudaPointerGetAttributes.  Unless a call says otherwise,
+ *    input arrays may be host or device memory, and so may outputs.  A call
+ *    that writes any host output returns only after that output is written
+ *    (it synchronises the stream); a call with device outputs only is
+ *    asynchronous on `stream`.
+ *  - The caller owns every array it passes in.  The library owns contexts
+ *    (snaps_ctx) and indexed populations (snaps_pop) and frees them in
+ *    snaps_destroy / snaps_release.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *    stream).  Device work is ordered on it.
+ *  - A subspace mask is a uint16_t with bit j set when feature j belongs to
+ *    it.  A valid mask has 2..F bits and no bit >= F.  Masks are always host
+ *    arrays.
+ *  - Distances are Euclidean over the subspace's features, computed in FP32
+ *    in one fixed order: the squared differences are accumulated with fused
+ *    multiply-adds from the highest feature index down to the lowest.  Every
+ *    path (plain, subspace-batched, tensor-core filtered) yields these same
+ *    bits.  A point is never its own neighbour.  The eps test is inclusive,
+ *    d^2 <= eps^2.  kNN order is by (distance, index).
+ *  - Default radius (eps == NULL): eps = 0.05 * sqrt(d) for a d-feature
+ *    subspace, i.e. eps^2 = 0.0025 * d rounded once to FP32.
+ */
+#ifndef SNAPS_H
+#define SNAPS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum snaps_status {
+    SNAPS_OK = 0,
+    SNAPS_EINVAL = 1,    /* an argument is out of range or inconsistent */
+    SNAPS_ENOMEM = 2,    /* device allocation failed or would exceed the context's HBM budget */
+    SNAPS_EBUSY = 3,     /* the object is in use (e.g. a population with requests in flight) */
+    SNAPS_EAGAIN = 4,    /* snaps_poll: the request has not finished within the timeout */
+    SNAPS_ETIMEOUT = 5,  /* a bounded device-side wait gave up; the context stays usable */
+    SNAPS_ECUDA = 6,     /* the CUDA runtime reported an error */
+    SNAPS_ECANCELED = 7  /* the request was cancelled before it ran */
+} snaps_status;
+
+#define SNAPS_MAX_FEATURES 15
+#define SNAPS_MAX_K 32
+#define SNAPS_N_SCORES 4
+/* score rows, in this order, in every scores / norm / top output */
+#define SNAPS_SCORE_EPS_COUNT 0  /* DSSJ distance-oblivious: eps-neighbour count (Sec. 3.5.1 item 1) */
+#define SNAPS_SCORE_EPS_MEAN 1   /* DSSJ distance-aware: mean eps-neighbour distance, 0 if none (item 2) */
+#define SNAPS_SCORE_KNN_INDEG 2  /* kNNSJ distance-oblivious: in-degree of the kNN graph (Sec. 3.6.1 item 1) */
+#define SNAPS_SCORE_KNN_MEAN 3   /* kNNSJ distance-aware: mean distance to the k neighbours (item 2) */
+
+/* snaps_index flags */
+#define SNAPS_NORM_MINMAX 0x1u   /* map every feature onto [0, 1] by its min and max (Sec. 3.3) */
+#define SNAPS_NAN_TO_MEAN 0x2u   /* replace NaN by the feature's mean first (Sec. 2.1) */
+
+/* precision argument of snaps_scores / snaps_request */
+#define SNAPS_FP32 0u            /* plain FP32 join */
+#define SNAPS_TC_F16 1u          /* tensor-core FP16 filter, exact FP32 recompute of survivors */
+
+typedef struct snaps_ctx snaps_ctx;
+typedef struct snaps_pop snaps_pop;
+
+/* Library version as "major.minor.patch"; static storage. */
+const char *snaps_version(void);
+
+/* Message describing the calling thread's most recent failure ("" if none);
+ * valid until that thread's next snaps_* call. */
+const char *snaps_last_error(void);
+
+/* Create a context on CUDA device `device`.  `hbm_budget_bytes` caps the
+ * device memory the context may hold (populations + scratch + in-flight
+ * requests); 0 means 90 % of the device's free memory at creation.
+ * Errors: EINVAL (bad device or out == NULL), ECUDA. */
+snaps_status snaps_create(int device, size_t hbm_budget_bytes, snaps_ctx **out);
+
+/* Finish all queued requests, free everything the context owns.  Populations
+ * not yet released are released.  NULL is a no-op. */
+snaps_status snaps_destroy(snaps_ctx *ctx);
+
+/* Device memory currently held and the budget, in bytes. */
+snaps_status snaps_mem_info(const snaps_ctx *ctx, size_t *held, size_t *budget);
+
+/* Index a population: the data set D of Sec. 3.1.
+ * feat: n x f float32, row-major, host or device; read before the call
+ *   returns (the call synchronises `stream`).
+ * flags: SNAPS_NORM_MINMAX and/or SNAPS_NAN_TO_MEAN.  Normalisation takes
+ *   each feature's min and max in FP64 and stores (x - min) / (max - min)
+ *   computed in FP64 and rounded to FP32; a constant feature becomes 0.
+ *   Without SNAPS_NORM_MINMAX the values are used unchanged.
+ * Requirements: n >= 2, 1 <= f <= 15, every value finite (NaN allowed only
+ *   with SNAPS_NAN_TO_MEAN).
+ * The population lives in device memory until snaps_release.
+ * Errors: EINVAL, ENOMEM (over budget), ECUDA. */
+snaps_status snaps_index(snaps_ctx *ctx, const float *feat, int64_t n, int f,
+                         uint32_t flags, void *stream, snaps_pop **out);
+
+/* Release a population.  EBUSY while requests that use it are in flight. */
+snaps_status snaps_release(snaps_pop *pop);
+
+/* Size of a population. */
+snaps_status snaps_pop_shape(const snaps_pop *pop, int64_t *n, int *f);
+
+/* Copy the population's stored (normalised) features out as n x f float32
+ * row-major into `out` (host or device). */
+snaps_status snaps_pop_features(const snaps_pop *pop, float *out, void *stream);
+
+/* kNN self-join (kNNSJ, Sec. 3.6) of every subspace in `masks`.
+ * masks: n_masks host uint16 masks.  1 <= k <= min(32, n - 1).
+ * idx:  n_masks x n x k int32 (subspace-major, then object, then rank):
+ *       the k nearest other objects, nearest first, exact ties by index.
+ * dist: same shape, float32 Euclidean distances, or NULL.
+ * Errors: EINVAL (bad mask, k, sizes), ENOMEM, ECUDA. */
+snaps_status snaps_knn_selfjoin(snaps_pop *pop, const uint16_t *masks, int n_masks,
+                                int k, int32_t *idx, float *dist, void *stream);
+
+/* Distance similarity self-join (DSSJ, Sec. 3.5) of every subspace.
+ * eps: n_masks host float radii, or NULL for 0.05 * sqrt(d) per subspace.
+ * count: n_masks x n int32, #{j != i : d(i, j) <= eps}, or NULL.
+ * mean_dist: n_masks x n float32, mean distance to those j (0 when count is
+ *   0), or NULL.
+ * Errors: EINVAL, ENOMEM, ECUDA. */
+snaps_status snaps_eps_selfjoin(snaps_pop *pop, const uint16_t *masks, int n_masks,
+                                const float *eps, int32_t *count, float *mean_dist,
+                                void *stream);
+
+/* Both joins and the four outlier metrics per object and subspace (Table 2).
+ * k, eps: as above.  precision: SNAPS_FP32 or SNAPS_TC_F16 (same results).
+ * scores: n_masks x 4 x n float32 raw metrics (rows SNAPS_SCORE_*), or NULL.
+ *   Counts and in-degrees are exact integers stored as float.
+ * norm:   n_masks x 4 x n float32, each metric mapped onto [0, 1] with
+ *   1 = most outlying, from its population min and max taken in FP64 (a
+ *   constant metric maps to 0; objects without eps-neighbours get 1 for the
+ *   eps mean distance and the rest are scaled among themselves), or NULL.
+ * top:    n_masks x 4 x top_n int32, the first top_n objects of each ranking
+ *   (Sec. 3.4, rank 0 = most outlying): counts and in-degrees ascending,
+ *   mean distances descending, objects without eps-neighbours first for the
+ *   eps mean distance; equal values in index order.  NULL or top_n == 0
+ *   skips it; 1 <= top_n <= min(n, 1024) otherwise.
+ * Errors: EINVAL, ENOMEM, ECUDA. */
+snaps_status snaps_scores(snaps_pop *pop, const uint16_t *masks, int n_masks, int k,
+                          const float *eps, uint32_t precision, float *scores,
+                          float *norm, int32_t *top, int top_n, void *stream);
+
+/* ---- serving: continuous batching of scoring requests ---- */
+
+/* One scoring request: snaps_scores on a resident population.  masks and
+ * eps are copied at submit; the outputs (device or host, caller-owned) must
+ * stay valid until the request completes. */
+typedef struct snaps_request {
+    snaps_pop *pop;
+    const uint16_t *masks;
+    int n_masks;
+    int k;
+    const float *eps;      /* NULL = default radius */
+    uint32_t precision;
+    float *scores;         /* may be NULL */
+    float *norm;           /* may be NULL */
+    int32_t *top;          /* may be NULL */
+    int top_n;
+} snaps_request;
+
+typedef struct snaps_result {
+    snaps_status status;   /* outcome of the request */
+    double queue_us;       /* submit -> admitted to a slot */
+    double latency_us;     /* submit -> results written */
+    int64_t objects_x_subspaces; /* n * n_masks */
+} snaps_result;
+
+/* Queue a request.  The context's scheduler admits queued requests in
+ * arrival order as soon as a slot and enough of the HBM budget are free, so
+ * requests that arrive while others run overlap them on the device.
+ * Errors: EINVAL (malformed request), ENOMEM (the request alone exceeds the
+ * budget). */
+snaps_status snaps_submit(snaps_ctx *ctx, const snaps_request *req, uint64_t *ticket);
+
+/* Wait up to timeout_us (0 = just test, < 0 = forever) for a request.
+ * Returns SNAPS_OK and fills *out once it has finished (whatever its own
+ * status), SNAPS_EAGAIN if it has not, EINVAL for an unknown ticket.  A
+ * finished ticket is forgotten after the first successful poll. */
+snaps_status snaps_poll(snaps_ctx *ctx, uint64_t ticket, int64_t timeout_us,
+                        snaps_result *out);
+
+/* Cancel a request that has not been admitted yet (ECANCELED becomes its
+ * status); EBUSY if it is already running or done. */
+snaps_status snaps_cancel(snaps_ctx *ctx, uint64_t ticket);
+
+/* Number of requests the scheduler may run at once (default 4, 1..64). */
+snaps_status snaps_set_slots(snaps_ctx *ctx, int slots);
+
+/* ---- tracing: device time per phase ---- */
+
+#define SNAPS_PHASE_INDEX 0      /* normalisation kernels of snaps_index */
+#define SNAPS_PHASE_JOIN_TREE 1  /* subspace-batched (tree) join kernel */
+#define SNAPS_PHASE_JOIN_LANE 2  /* lane-per-subspace join kernel */
+#define SNAPS_PHASE_NORM 3       /* normalised-metric kernel */
+#define SNAPS_PHASE_TOP 4        /* top-n ranking kernel */
+#define SNAPS_N_PHASES 5
+
+/* enable != 0: clear the counters and start recording, around every kernel
+ * launch of every later call on this context, a pair of CUDA events on the
+ * stream the kernel is launched on.  enable == 0 stops recording. */
+snaps_status snaps_trace(snaps_ctx *ctx, int enable);
+
+/* Wait for the recorded events, then report per phase the summed device time
+ * in milliseconds (ms[SNAPS_N_PHASES]) and the number of kernel launches
+ * (launches[SNAPS_N_PHASES]) since tracing was enabled or last read; either
+ * array may be NULL.  The counters restart from zero. */
+snaps_status snaps_trace_read(snaps_ctx *ctx, double *ms, int64_t *launches);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SNAPS_H */

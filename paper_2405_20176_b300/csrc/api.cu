@@ -1,0 +1,973 @@
+// C ABI of libsnaps (include/snaps.h): contexts, resident populations, the
+// synchronous join / scoring calls and the continuous-batching request loop.
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <deque>
+#include <mutex>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "common.cuh"
+#include "join.cuh"
+#include "prep.cuh"
+
+// ---- error plumbing -----------------------------------------------------------------
+
+namespace snaps {
+namespace {
+thread_local char g_err[512] = "";
+}
+const char *last_error_message() { return g_err; }
+void set_error(const char *fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+}
+void clear_error() { g_err[0] = '\0'; }
+}  // namespace snaps
+
+using namespace snaps;
+
+#define FAIL(code, ...)                 \
+    do {                                \
+        snaps::set_error(__VA_ARGS__);  \
+        return code;                    \
+    } while (0)
+
+// ---- objects -------------------------------------------------------------------------
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+// Grow-only device buffer charged to a context's budget.
+struct Scratch {
+    void *ptr = nullptr;
+    size_t cap = 0;
+};
+
+struct Request;
+
+struct Slot {
+    cudaStream_t stream = nullptr;
+    Scratch scratch;
+    DeviceControl *ctrl = nullptr;
+    std::thread worker;
+};
+
+}  // namespace
+
+struct snaps_ctx {
+    int device = 0;
+    size_t budget = 0;
+    size_t held = 0;  // bytes allocated through this context
+    std::mutex mem_mu;
+
+    // synchronous calls share one scratch area and control block
+    std::mutex sync_mu;
+    Scratch scratch;
+    DeviceControl *ctrl = nullptr;
+
+    // serving
+    std::mutex q_mu;
+    std::condition_variable q_cv;    // workers wait for work / memory
+    std::condition_variable done_cv; // pollers wait for completion
+    std::deque<Request *> queue;
+    std::unordered_map<uint64_t, Request *> tickets;
+    uint64_t next_ticket = 1;
+    size_t reserved = 0;  // bytes reserved by admitted requests
+    int n_slots = 4;
+    std::vector<Slot *> slots;
+    bool stopping = false;
+    std::atomic<int> n_pops{0};
+
+    // tracing
+    std::mutex tr_mu;
+    bool tracing = false;
+    struct Mark { int phase; int kernels; cudaEvent_t a, b; };
+    std::vector<Mark> marks;
+    std::vector<cudaEvent_t> spare;
+};
+
+struct snaps_pop {
+    snaps_ctx *ctx = nullptr;
+    int64_t n = 0, n_pad = 0;
+    int f = 0;
+    float4 *x = nullptr;
+    size_t bytes = 0;
+    std::atomic<int> inflight{0};
+};
+
+namespace {
+
+struct Request {
+    uint64_t ticket = 0;
+    snaps_request req{};
+    std::vector<uint16_t> masks;
+    std::vector<float> eps;
+    size_t footprint = 0;
+    Clock::time_point t_submit, t_admit, t_done;
+    bool done = false;
+    bool running = false;
+    snaps_status status = SNAPS_OK;
+};
+
+snaps_status ctx_alloc(snaps_ctx *ctx, size_t bytes, void **p)
+{
+    {
+        std::lock_guard<std::mutex> g(ctx->mem_mu);
+        if (ctx->held + bytes > ctx->budget)
+            FAIL(SNAPS_ENOMEM, "allocation of %zu bytes exceeds the HBM budget (%zu of %zu held)",
+                 bytes, ctx->held, ctx->budget);
+        ctx->held += bytes;
+    }
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        std::lock_guard<std::mutex> g(ctx->mem_mu);
+        ctx->held -= bytes;
+        cudaGetLastError();
+        FAIL(SNAPS_ENOMEM, "cudaMalloc(%zu) failed: %s", bytes, cudaGetErrorString(e));
+    }
+    return SNAPS_OK;
+}
+
+void ctx_free(snaps_ctx *ctx, void *p, size_t bytes)
+{
+    if (!p) return;
+    cudaFree(p);
+    std::lock_guard<std::mutex> g(ctx->mem_mu);
+    ctx->held -= bytes;
+}
+
+snaps_status scratch_reserve(snaps_ctx *ctx, Scratch &s, size_t bytes)
+{
+    if (bytes <= s.cap) return SNAPS_OK;
+    ctx_free(ctx, s.ptr, s.cap);
+    s.ptr = nullptr;
+    s.cap = 0;
+    bytes = (bytes + (1u << 20) - 1) & ~size_t((1u << 20) - 1);
+    SNAPS_TRY(ctx_alloc(ctx, bytes, &s.ptr));
+    s.cap = bytes;
+    return SNAPS_OK;
+}
+
+bool is_device_ptr(const void *p)
+{
+    if (!p) return false;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+inline int popc16(uint32_t m) { return __builtin_popcount(m); }
+
+// Carve aligned sub-buffers out of one scratch block.
+struct Carver {
+    size_t off = 0;
+    char *base = nullptr;
+    template <class T>
+    T *take(size_t count)
+    {
+        off = (off + 255) & ~size_t(255);
+        T *p = base ? reinterpret_cast<T *>(base + off) : nullptr;
+        off += count * sizeof(T);
+        return p;
+    }
+};
+
+// Everything one scoring / join call needs, independent of who calls it.
+struct JobSpec {
+    snaps_pop *pop = nullptr;
+    const uint16_t *masks = nullptr;
+    int n_masks = 0;
+    int k = 0;                 // 0: no kNN join
+    const float *eps = nullptr;
+    bool want_eps = true;
+    uint32_t precision = SNAPS_FP32;
+    float *scores = nullptr;   // n_masks x 4 x n
+    float *norm = nullptr;
+    int32_t *top = nullptr;
+    int top_n = 0;
+    int32_t *knn_idx = nullptr;
+    float *knn_dist = nullptr;
+    int32_t *eps_count = nullptr;
+    float *eps_mean = nullptr;
+};
+
+snaps_status validate(const JobSpec &j)
+{
+    if (!j.pop) FAIL(SNAPS_EINVAL, "population is NULL");
+    const snaps_pop *p = j.pop;
+    if (j.n_masks < 1) FAIL(SNAPS_EINVAL, "n_masks must be >= 1 (got %d)", j.n_masks);
+    if (!j.masks) FAIL(SNAPS_EINVAL, "masks is NULL");
+    if (is_device_ptr(j.masks)) FAIL(SNAPS_EINVAL, "masks must be a host array");
+    if (j.eps && is_device_ptr(j.eps)) FAIL(SNAPS_EINVAL, "eps must be a host array");
+    for (int m = 0; m < j.n_masks; ++m) {
+        const uint32_t v = j.masks[m];
+        if (popc16(v) < 2 || (v >> p->f) != 0)
+            FAIL(SNAPS_EINVAL, "mask %d (0x%x) must have 2..%d bits, all below feature %d", m, v,
+                 p->f, p->f);
+        if (j.eps && !(j.eps[m] >= 0.f && j.eps[m] < 3.0e18f))
+            FAIL(SNAPS_EINVAL, "eps[%d] must be a finite value >= 0", m);
+    }
+    if (j.k < 0 || j.k > SNAPS_MAX_K || (j.k > 0 && j.k > p->n - 1))
+        FAIL(SNAPS_EINVAL, "k must be in 1..min(%d, n-1) (got %d, n %lld)", SNAPS_MAX_K, j.k,
+             (long long)p->n);
+    if (j.top && (j.top_n < 1 || j.top_n > 1024 || j.top_n > p->n))
+        FAIL(SNAPS_EINVAL, "top_n must be in 1..min(1024, n) (got %d)", j.top_n);
+    if (j.precision != SNAPS_FP32 && j.precision != SNAPS_TC_F16)
+        FAIL(SNAPS_EINVAL, "unknown precision %u", j.precision);
+    if (j.precision == SNAPS_TC_F16)
+        FAIL(SNAPS_EINVAL, "precision SNAPS_TC_F16 is not available in this build");
+    return SNAPS_OK;
+}
+
+// Split the requested subspaces between the tree kernel (chunks with >= 2
+// requested subspaces) and the lane-per-subspace kernel (everything else).
+struct Plan {
+    std::vector<TreeChunk> chunks;
+    std::vector<MaskGroup> groups;
+};
+
+Plan make_plan(const JobSpec &j)
+{
+    Plan pl;
+    const int f = j.pop->f;
+    const int n_chunk = f > kTreeLowBits ? 1 << (f - kTreeLowBits) : 1;
+    std::vector<int> first(size_t(n_chunk) * kTreeWidth, -1);
+    std::vector<int> count(n_chunk, 0);
+    std::vector<int> extra;  // duplicates of an already-placed subspace
+    auto eps2_of = [&](int m) -> float {
+        if (!j.want_eps) return -1.f;
+        if (j.eps) return j.eps[m] * j.eps[m];
+        return default_eps2(popc16(j.masks[m]));
+    };
+    for (int m = 0; m < j.n_masks; ++m) {
+        const uint32_t v = j.masks[m];
+        const uint32_t c = v >> kTreeLowBits, L = v & (kTreeWidth - 1);
+        int &slot = first[size_t(c) * kTreeWidth + L];
+        if (slot >= 0) {
+            extra.push_back(m);
+            continue;
+        }
+        slot = m;
+        ++count[c];
+    }
+    std::vector<int> lone = extra;
+    for (int c = 0; c < n_chunk; ++c) {
+        if (count[c] == 0) continue;
+        if (count[c] == 1) {
+            for (int L = 0; L < kTreeWidth; ++L)
+                if (first[size_t(c) * kTreeWidth + L] >= 0) lone.push_back(first[size_t(c) * kTreeWidth + L]);
+            continue;
+        }
+        TreeChunk ch{};
+        ch.high = (uint32_t)c;
+        ch.active = 0;
+        for (int L = 0; L < kTreeWidth; ++L) {
+            const int m = first[size_t(c) * kTreeWidth + L];
+            ch.slot[L] = m;
+            ch.eps2[L] = m >= 0 ? eps2_of(m) : -1.f;
+            if (m >= 0) ch.active |= 1u << L;
+        }
+        pl.chunks.push_back(ch);
+    }
+    std::sort(lone.begin(), lone.end());
+    for (size_t b = 0; b < lone.size(); b += 32) {
+        MaskGroup g{};
+        for (int l = 0; l < 32; ++l) {
+            const size_t q = b + l;
+            if (q < lone.size()) {
+                const int m = lone[q];
+                g.mask[l] = j.masks[m];
+                g.eps2[l] = eps2_of(m);
+                g.slot[l] = m;
+            } else {
+                g.mask[l] = 0;
+                g.eps2[l] = -1.f;
+                g.slot[l] = -1;
+            }
+        }
+        pl.groups.push_back(g);
+    }
+    return pl;
+}
+
+// Device bytes a job needs beyond the population, and the layout inside them.
+struct Layout {
+    float *scores = nullptr;
+    float *norm = nullptr;
+    int32_t *top = nullptr;
+    int32_t *knn_idx = nullptr;
+    float *knn_dist = nullptr;
+    int32_t *eps_count = nullptr;
+    TreeChunk *chunks = nullptr;
+    MaskGroup *groups = nullptr;
+    size_t bytes = 0;
+};
+
+Layout layout_job(const JobSpec &j, const Plan &pl, char *base, bool dev_scores, bool dev_norm,
+                  bool dev_top, bool dev_idx, bool dev_dist, bool dev_cnt)
+{
+    Carver cv;
+    cv.base = base;
+    Layout L;
+    const size_t n = (size_t)j.pop->n, nm = (size_t)j.n_masks;
+    L.scores = dev_scores ? j.scores : cv.take<float>(nm * 4 * n);
+    if (j.norm) L.norm = dev_norm ? j.norm : cv.take<float>(nm * 4 * n);
+    if (j.top) L.top = dev_top ? j.top : cv.take<int32_t>(nm * 4 * (size_t)j.top_n);
+    if (j.knn_idx) L.knn_idx = dev_idx ? j.knn_idx : cv.take<int32_t>(nm * n * (size_t)j.k);
+    if (j.knn_dist) L.knn_dist = dev_dist ? j.knn_dist : cv.take<float>(nm * n * (size_t)j.k);
+    if (j.eps_count) L.eps_count = dev_cnt ? j.eps_count : cv.take<int32_t>(nm * n);
+    L.chunks = cv.take<TreeChunk>(pl.chunks.size());
+    L.groups = cv.take<MaskGroup>(pl.groups.size());
+    L.bytes = cv.off + 256;
+    return L;
+}
+
+size_t job_footprint(const JobSpec &j)
+{
+    Plan pl = make_plan(j);
+    Layout L = layout_job(j, pl, nullptr, is_device_ptr(j.scores), is_device_ptr(j.norm),
+                          is_device_ptr(j.top), is_device_ptr(j.knn_idx), is_device_ptr(j.knn_dist),
+                          is_device_ptr(j.eps_count));
+    return L.bytes;
+}
+
+// Record a CUDA event pair around a launch when the context is tracing.
+struct TraceScope {
+    snaps_ctx *ctx;
+    int phase;
+    cudaStream_t st;
+    int kernels;
+    cudaEvent_t a = nullptr, b = nullptr;
+    TraceScope(snaps_ctx *c, int ph, cudaStream_t s, int nk = 1) : ctx(c), phase(ph), st(s), kernels(nk)
+    {
+        std::lock_guard<std::mutex> g(ctx->tr_mu);
+        if (!ctx->tracing) return;
+        a = take();
+        b = take();
+        if (a && b) cudaEventRecord(a, st);
+    }
+    cudaEvent_t take()
+    {
+        if (!ctx->spare.empty()) {
+            cudaEvent_t e = ctx->spare.back();
+            ctx->spare.pop_back();
+            return e;
+        }
+        cudaEvent_t e = nullptr;
+        if (cudaEventCreate(&e) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        return e;
+    }
+    ~TraceScope()
+    {
+        if (!a || !b) return;
+        cudaEventRecord(b, st);
+        std::lock_guard<std::mutex> g(ctx->tr_mu);
+        ctx->marks.push_back({phase, kernels, a, b});
+    }
+};
+
+// Run one job on `st` with `scratch`.  Returns after host outputs are written
+// (it synchronises the stream when any output is host memory, or when
+// `sync` is set).
+snaps_status run_job(snaps_ctx *ctx, const JobSpec &j, cudaStream_t st, Scratch &scratch,
+                     DeviceControl *ctrl, bool sync)
+{
+    SNAPS_TRY(validate(j));
+    snaps_pop *p = j.pop;
+    const int64_t n = p->n;
+    const size_t nm = (size_t)j.n_masks;
+    const bool dev_scores = is_device_ptr(j.scores), dev_norm = is_device_ptr(j.norm),
+               dev_top = is_device_ptr(j.top), dev_idx = is_device_ptr(j.knn_idx),
+               dev_dist = is_device_ptr(j.knn_dist), dev_cnt = is_device_ptr(j.eps_count);
+    Plan pl = make_plan(j);
+    Layout L0 = layout_job(j, pl, nullptr, dev_scores, dev_norm, dev_top, dev_idx, dev_dist, dev_cnt);
+    SNAPS_TRY(scratch_reserve(ctx, scratch, L0.bytes));
+    Layout L = layout_job(j, pl, (char *)scratch.ptr, dev_scores, dev_norm, dev_top, dev_idx,
+                          dev_dist, dev_cnt);
+
+    if (!pl.chunks.empty())
+        SNAPS_CHECK_CUDA(cudaMemcpyAsync(L.chunks, pl.chunks.data(),
+                                         pl.chunks.size() * sizeof(TreeChunk),
+                                         cudaMemcpyHostToDevice, st));
+    if (!pl.groups.empty())
+        SNAPS_CHECK_CUDA(cudaMemcpyAsync(L.groups, pl.groups.data(),
+                                         pl.groups.size() * sizeof(MaskGroup),
+                                         cudaMemcpyHostToDevice, st));
+    SNAPS_CHECK_CUDA(cudaMemsetAsync(L.scores, 0, nm * 4 * (size_t)n * sizeof(float), st));
+    SNAPS_CHECK_CUDA(cudaMemsetAsync(&ctrl->error, 0, sizeof(unsigned), st));
+
+    JoinShape shape{p->x, n, p->n_pad, j.k};
+    JoinOut out{L.scores, L.knn_idx, L.knn_dist, L.eps_count};
+    if (!pl.chunks.empty()) {
+        TraceScope ts(ctx, SNAPS_PHASE_JOIN_TREE, st);
+        SNAPS_TRY(launch_join_tree(shape, L.chunks, (int)pl.chunks.size(), out, ctrl, st));
+    }
+    if (!pl.groups.empty()) {
+        TraceScope ts(ctx, SNAPS_PHASE_JOIN_LANE, st);
+        SNAPS_TRY(launch_join_lanemask(shape, L.groups, (int)pl.groups.size(), out, ctrl, st));
+    }
+    if (j.norm) {
+        TraceScope ts(ctx, SNAPS_PHASE_NORM, st);
+        SNAPS_TRY(launch_norm(L.scores, n, j.n_masks, L.norm, st));
+    }
+    if (j.top) {
+        TraceScope ts(ctx, SNAPS_PHASE_TOP, st);
+        SNAPS_TRY(launch_top(L.scores, n, j.n_masks, j.top_n, L.top, st));
+    }
+
+    bool host_out = false;
+    auto d2h = [&](void *dst, const void *src, size_t bytes) -> snaps_status {
+        SNAPS_CHECK_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, st));
+        host_out = true;
+        return SNAPS_OK;
+    };
+    if (j.scores && !dev_scores) SNAPS_TRY(d2h(j.scores, L.scores, nm * 4 * n * sizeof(float)));
+    if (j.norm && !dev_norm) SNAPS_TRY(d2h(j.norm, L.norm, nm * 4 * n * sizeof(float)));
+    if (j.top && !dev_top) SNAPS_TRY(d2h(j.top, L.top, nm * 4 * (size_t)j.top_n * sizeof(int32_t)));
+    if (j.knn_idx && !dev_idx)
+        SNAPS_TRY(d2h(j.knn_idx, L.knn_idx, nm * n * (size_t)j.k * sizeof(int32_t)));
+    if (j.knn_dist && !dev_dist)
+        SNAPS_TRY(d2h(j.knn_dist, L.knn_dist, nm * n * (size_t)j.k * sizeof(float)));
+    if (j.eps_count && !dev_cnt)
+        SNAPS_TRY(d2h(j.eps_count, L.eps_count, nm * n * sizeof(int32_t)));
+    if (j.eps_mean) {
+        // row 1 of every subspace's 4 x n block
+        const cudaMemcpyKind kind =
+            is_device_ptr(j.eps_mean) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+        SNAPS_CHECK_CUDA(cudaMemcpy2DAsync(j.eps_mean, n * sizeof(float), L.scores + n,
+                                           4 * n * sizeof(float), n * sizeof(float), nm, kind, st));
+        if (kind == cudaMemcpyDeviceToHost) host_out = true;
+    }
+    if (host_out || sync) {
+        unsigned err = 0;
+        SNAPS_CHECK_CUDA(cudaMemcpyAsync(&err, &ctrl->error, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+        SNAPS_CHECK_CUDA(cudaStreamSynchronize(st));
+        if (err) FAIL(SNAPS_ETIMEOUT, "a device-side wait gave up (error word 0x%x)", err);
+    }
+    return SNAPS_OK;
+}
+
+snaps_status device_guard(const snaps_ctx *ctx)
+{
+    SNAPS_CHECK_CUDA(cudaSetDevice(ctx->device));
+    return SNAPS_OK;
+}
+
+// ---- serving ---------------------------------------------------------------------------
+
+JobSpec spec_of(Request *r)
+{
+    JobSpec j;
+    j.pop = r->req.pop;
+    j.masks = r->masks.data();
+    j.n_masks = (int)r->masks.size();
+    j.k = r->req.k;
+    j.eps = r->eps.empty() ? nullptr : r->eps.data();
+    j.precision = r->req.precision;
+    j.scores = r->req.scores;
+    j.norm = r->req.norm;
+    j.top = r->req.top;
+    j.top_n = r->req.top ? r->req.top_n : 0;
+    return j;
+}
+
+void worker_loop(snaps_ctx *ctx, Slot *slot)
+{
+    cudaSetDevice(ctx->device);
+    for (;;) {
+        Request *r = nullptr;
+        {
+            std::unique_lock<std::mutex> lk(ctx->q_mu);
+            for (;;) {
+                if (ctx->stopping && ctx->queue.empty()) return;
+                if (!ctx->queue.empty()) {
+                    Request *h = ctx->queue.front();
+                    // admission by HBM footprint, in arrival order
+                    size_t held;
+                    {
+                        std::lock_guard<std::mutex> g(ctx->mem_mu);
+                        held = ctx->held;
+                    }
+                    const size_t grow = h->footprint > slot->scratch.cap ? h->footprint : 0;
+                    if (held + ctx->reserved + grow <= ctx->budget || ctx->reserved == 0) {
+                        ctx->queue.pop_front();
+                        ctx->reserved += grow;
+                        h->running = true;
+                        h->t_admit = Clock::now();
+                        r = h;
+                        break;
+                    }
+                }
+                ctx->q_cv.wait(lk);
+            }
+        }
+        const size_t grow = r->footprint > slot->scratch.cap ? r->footprint : 0;
+        snaps_status s = run_job(ctx, spec_of(r), slot->stream, slot->scratch, slot->ctrl, true);
+        {
+            std::lock_guard<std::mutex> lk(ctx->q_mu);
+            ctx->reserved -= grow;
+            r->status = s;
+            r->done = true;
+            r->running = false;
+            r->t_done = Clock::now();
+            r->req.pop->inflight.fetch_sub(1);
+        }
+        ctx->done_cv.notify_all();
+        ctx->q_cv.notify_all();
+    }
+}
+
+snaps_status start_slots(snaps_ctx *ctx)
+{
+    while ((int)ctx->slots.size() < ctx->n_slots) {
+        Slot *s = new Slot();
+        SNAPS_CHECK_CUDA(cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking));
+        void *c = nullptr;
+        SNAPS_TRY(ctx_alloc(ctx, sizeof(DeviceControl), &c));
+        s->ctrl = (DeviceControl *)c;
+        s->worker = std::thread(worker_loop, ctx, s);
+        ctx->slots.push_back(s);
+    }
+    return SNAPS_OK;
+}
+
+}  // namespace
+
+// ---- C ABI --------------------------------------------------------------------------------
+
+extern "C" {
+
+const char *snaps_version(void) { return "0.1.0"; }
+
+const char *snaps_last_error(void) { return snaps::last_error_message(); }
+
+snaps_status snaps_create(int device, size_t hbm_budget_bytes, snaps_ctx **out)
+{
+    clear_error();
+    if (!out) FAIL(SNAPS_EINVAL, "out is NULL");
+    *out = nullptr;
+    int count = 0;
+    SNAPS_CHECK_CUDA(cudaGetDeviceCount(&count));
+    if (device < 0 || device >= count) FAIL(SNAPS_EINVAL, "device %d out of range (%d devices)", device, count);
+    SNAPS_CHECK_CUDA(cudaSetDevice(device));
+    size_t free_b = 0, total_b = 0;
+    SNAPS_CHECK_CUDA(cudaMemGetInfo(&free_b, &total_b));
+    snaps_ctx *ctx = new snaps_ctx();
+    ctx->device = device;
+    ctx->budget = hbm_budget_bytes ? hbm_budget_bytes : (size_t)(0.9 * (double)free_b);
+    void *c = nullptr;
+    snaps_status s = ctx_alloc(ctx, sizeof(DeviceControl), &c);
+    if (s != SNAPS_OK) {
+        delete ctx;
+        return s;
+    }
+    ctx->ctrl = (DeviceControl *)c;
+    *out = ctx;
+    return SNAPS_OK;
+}
+
+snaps_status snaps_destroy(snaps_ctx *ctx)
+{
+    clear_error();
+    if (!ctx) return SNAPS_OK;
+    cudaSetDevice(ctx->device);
+    {
+        std::lock_guard<std::mutex> lk(ctx->q_mu);
+        ctx->stopping = true;
+    }
+    ctx->q_cv.notify_all();
+    for (Slot *s : ctx->slots) {
+        if (s->worker.joinable()) s->worker.join();
+        ctx_free(ctx, s->scratch.ptr, s->scratch.cap);
+        ctx_free(ctx, s->ctrl, sizeof(DeviceControl));
+        cudaStreamDestroy(s->stream);
+        delete s;
+    }
+    for (auto &kv : ctx->tickets) delete kv.second;
+    for (auto &m : ctx->marks) {
+        cudaEventDestroy(m.a);
+        cudaEventDestroy(m.b);
+    }
+    for (cudaEvent_t e : ctx->spare) cudaEventDestroy(e);
+    ctx_free(ctx, ctx->scratch.ptr, ctx->scratch.cap);
+    ctx_free(ctx, ctx->ctrl, sizeof(DeviceControl));
+    delete ctx;
+    return SNAPS_OK;
+}
+
+snaps_status snaps_mem_info(const snaps_ctx *ctx, size_t *held, size_t *budget)
+{
+    clear_error();
+    if (!ctx) FAIL(SNAPS_EINVAL, "ctx is NULL");
+    auto *c = const_cast<snaps_ctx *>(ctx);
+    std::lock_guard<std::mutex> g(c->mem_mu);
+    if (held) *held = c->held;
+    if (budget) *budget = c->budget;
+    return SNAPS_OK;
+}
+
+snaps_status snaps_index(snaps_ctx *ctx, const float *feat, int64_t n, int f, uint32_t flags,
+                         void *stream, snaps_pop **out)
+{
+    clear_error();
+    if (!ctx || !feat || !out) FAIL(SNAPS_EINVAL, "ctx, feat and out must be non-NULL");
+    *out = nullptr;
+    if (n < 2 || n > (int64_t(1) << 24)) FAIL(SNAPS_EINVAL, "n must be in 2..2^24 (got %lld)", (long long)n);
+    if (f < 1 || f > SNAPS_MAX_FEATURES) FAIL(SNAPS_EINVAL, "f must be in 1..15 (got %d)", f);
+    if (flags & ~(SNAPS_NORM_MINMAX | SNAPS_NAN_TO_MEAN)) FAIL(SNAPS_EINVAL, "unknown flags 0x%x", flags);
+    SNAPS_TRY(device_guard(ctx));
+    cudaStream_t st = (cudaStream_t)stream;
+    snaps_pop *p = new snaps_pop();
+    p->ctx = ctx;
+    p->n = n;
+    p->f = f;
+    p->n_pad = padded_rows(n);
+    p->bytes = (size_t)p->n_pad * kRowFloats * sizeof(float);
+    void *xp = nullptr;
+    snaps_status s = ctx_alloc(ctx, p->bytes, &xp);
+    if (s != SNAPS_OK) {
+        delete p;
+        return s;
+    }
+    p->x = (float4 *)xp;
+    // staging: input copy (when on the host) + column statistics + flag
+    const size_t in_bytes = (size_t)n * f * sizeof(float);
+    const bool dev_in = is_device_ptr(feat);
+    const size_t aux = 256 + sizeof(ColStats) * 16 + 256;
+    void *stage = nullptr;
+    s = ctx_alloc(ctx, (dev_in ? 0 : in_bytes) + aux, &stage);
+    if (s != SNAPS_OK) {
+        ctx_free(ctx, p->x, p->bytes);
+        delete p;
+        return s;
+    }
+    char *sb = (char *)stage;
+    unsigned *bad = (unsigned *)sb;
+    ColStats *stats = (ColStats *)(sb + 256);
+    const float *in = dev_in ? feat : (const float *)(sb + aux);
+    auto fail = [&](snaps_status code) {
+        cudaStreamSynchronize(st);
+        ctx_free(ctx, stage, (dev_in ? 0 : in_bytes) + aux);
+        ctx_free(ctx, p->x, p->bytes);
+        delete p;
+        return code;
+    };
+    if (!dev_in && cudaMemcpyAsync((void *)in, feat, in_bytes, cudaMemcpyHostToDevice, st) != cudaSuccess) {
+        set_error("copying the features to the device failed");
+        return fail(SNAPS_ECUDA);
+    }
+    {
+        TraceScope ts(ctx, SNAPS_PHASE_INDEX, st, 2);
+        s = launch_normalise(in, n, p->n_pad, f, flags, stats, bad, p->x, st);
+    }
+    if (s != SNAPS_OK) return fail(s);
+    unsigned hbad = 0;
+    if (cudaMemcpyAsync(&hbad, bad, sizeof(unsigned), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess) {
+        set_error("normalisation failed: %s", cudaGetErrorString(cudaGetLastError()));
+        return fail(SNAPS_ECUDA);
+    }
+    if (hbad) {
+        set_error("features must be finite (NaN is allowed only with SNAPS_NAN_TO_MEAN)");
+        return fail(SNAPS_EINVAL);
+    }
+    ctx_free(ctx, stage, (dev_in ? 0 : in_bytes) + aux);
+    ctx->n_pops.fetch_add(1);
+    *out = p;
+    return SNAPS_OK;
+}
+
+snaps_status snaps_release(snaps_pop *pop)
+{
+    clear_error();
+    if (!pop) return SNAPS_OK;
+    if (pop->inflight.load() > 0) FAIL(SNAPS_EBUSY, "population has %d requests in flight", pop->inflight.load());
+    snaps_ctx *ctx = pop->ctx;
+    cudaSetDevice(ctx->device);
+    cudaDeviceSynchronize();
+    ctx_free(ctx, pop->x, pop->bytes);
+    ctx->n_pops.fetch_sub(1);
+    delete pop;
+    return SNAPS_OK;
+}
+
+snaps_status snaps_pop_shape(const snaps_pop *pop, int64_t *n, int *f)
+{
+    clear_error();
+    if (!pop) FAIL(SNAPS_EINVAL, "pop is NULL");
+    if (n) *n = pop->n;
+    if (f) *f = pop->f;
+    return SNAPS_OK;
+}
+
+snaps_status snaps_pop_features(const snaps_pop *pop, float *out, void *stream)
+{
+    clear_error();
+    if (!pop || !out) FAIL(SNAPS_EINVAL, "pop and out must be non-NULL");
+    snaps_ctx *ctx = pop->ctx;
+    SNAPS_TRY(device_guard(ctx));
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t bytes = (size_t)pop->n * pop->f * sizeof(float);
+    if (is_device_ptr(out)) return launch_unpack(pop->x, pop->n, pop->f, out, st);
+    void *tmp = nullptr;
+    SNAPS_TRY(ctx_alloc(ctx, bytes, &tmp));
+    snaps_status s = launch_unpack(pop->x, pop->n, pop->f, (float *)tmp, st);
+    if (s == SNAPS_OK) {
+        if (cudaMemcpyAsync(out, tmp, bytes, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess) {
+            set_error("copying the features out failed");
+            s = SNAPS_ECUDA;
+        }
+    }
+    ctx_free(ctx, tmp, bytes);
+    return s;
+}
+
+snaps_status snaps_knn_selfjoin(snaps_pop *pop, const uint16_t *masks, int n_masks, int k,
+                                int32_t *idx, float *dist, void *stream)
+{
+    clear_error();
+    if (!pop) FAIL(SNAPS_EINVAL, "pop is NULL");
+    if (!idx) FAIL(SNAPS_EINVAL, "idx is NULL");
+    if (k < 1) FAIL(SNAPS_EINVAL, "k must be >= 1 (got %d)", k);
+    SNAPS_TRY(device_guard(pop->ctx));
+    JobSpec j;
+    j.pop = pop;
+    j.masks = masks;
+    j.n_masks = n_masks;
+    j.k = k;
+    j.want_eps = false;
+    j.knn_idx = idx;
+    j.knn_dist = dist;
+    std::lock_guard<std::mutex> g(pop->ctx->sync_mu);
+    return run_job(pop->ctx, j, (cudaStream_t)stream, pop->ctx->scratch, pop->ctx->ctrl, false);
+}
+
+snaps_status snaps_eps_selfjoin(snaps_pop *pop, const uint16_t *masks, int n_masks,
+                                const float *eps, int32_t *count, float *mean_dist, void *stream)
+{
+    clear_error();
+    if (!pop) FAIL(SNAPS_EINVAL, "pop is NULL");
+    SNAPS_TRY(device_guard(pop->ctx));
+    JobSpec j;
+    j.pop = pop;
+    j.masks = masks;
+    j.n_masks = n_masks;
+    j.k = 0;
+    j.eps = eps;
+    j.want_eps = true;
+    j.eps_count = count;
+    j.eps_mean = mean_dist;
+    std::lock_guard<std::mutex> g(pop->ctx->sync_mu);
+    return run_job(pop->ctx, j, (cudaStream_t)stream, pop->ctx->scratch, pop->ctx->ctrl, false);
+}
+
+snaps_status snaps_scores(snaps_pop *pop, const uint16_t *masks, int n_masks, int k,
+                          const float *eps, uint32_t precision, float *scores, float *norm,
+                          int32_t *top, int top_n, void *stream)
+{
+    clear_error();
+    if (!pop) FAIL(SNAPS_EINVAL, "pop is NULL");
+    if (k < 1) FAIL(SNAPS_EINVAL, "k must be >= 1 (got %d)", k);
+    SNAPS_TRY(device_guard(pop->ctx));
+    JobSpec j;
+    j.pop = pop;
+    j.masks = masks;
+    j.n_masks = n_masks;
+    j.k = k;
+    j.eps = eps;
+    j.want_eps = true;
+    j.precision = precision;
+    j.scores = scores;
+    j.norm = norm;
+    j.top = (top && top_n > 0) ? top : nullptr;
+    j.top_n = j.top ? top_n : 0;
+    std::lock_guard<std::mutex> g(pop->ctx->sync_mu);
+    return run_job(pop->ctx, j, (cudaStream_t)stream, pop->ctx->scratch, pop->ctx->ctrl, false);
+}
+
+snaps_status snaps_set_slots(snaps_ctx *ctx, int slots)
+{
+    clear_error();
+    if (!ctx) FAIL(SNAPS_EINVAL, "ctx is NULL");
+    if (slots < 1 || slots > 64) FAIL(SNAPS_EINVAL, "slots must be in 1..64 (got %d)", slots);
+    std::lock_guard<std::mutex> lk(ctx->q_mu);
+    if (!ctx->slots.empty() && slots < (int)ctx->slots.size())
+        FAIL(SNAPS_EBUSY, "slots can only grow once serving has started");
+    ctx->n_slots = slots;
+    return SNAPS_OK;
+}
+
+snaps_status snaps_submit(snaps_ctx *ctx, const snaps_request *req, uint64_t *ticket)
+{
+    clear_error();
+    if (!ctx || !req || !ticket) FAIL(SNAPS_EINVAL, "ctx, req and ticket must be non-NULL");
+    if (!req->pop || req->pop->ctx != ctx) FAIL(SNAPS_EINVAL, "request population does not belong to this context");
+    if (req->k < 1) FAIL(SNAPS_EINVAL, "k must be >= 1 (got %d)", req->k);
+    SNAPS_TRY(device_guard(ctx));
+    Request *r = new Request();
+    r->req = *req;
+    if (req->n_masks < 1 || !req->masks) {
+        delete r;
+        FAIL(SNAPS_EINVAL, "a request needs at least one mask");
+    }
+    r->masks.assign(req->masks, req->masks + req->n_masks);
+    if (req->eps) r->eps.assign(req->eps, req->eps + req->n_masks);
+    r->req.masks = nullptr;
+    r->req.eps = nullptr;
+    JobSpec j = spec_of(r);
+    snaps_status s = validate(j);
+    if (s != SNAPS_OK) {
+        delete r;
+        return s;
+    }
+    r->footprint = job_footprint(j);
+    if (r->footprint > ctx->budget) {
+        const size_t need = r->footprint;
+        delete r;
+        FAIL(SNAPS_ENOMEM, "request needs %zu bytes, over the budget of %zu", need, ctx->budget);
+    }
+    {
+        std::lock_guard<std::mutex> lk(ctx->q_mu);
+        s = start_slots(ctx);
+        if (s != SNAPS_OK) {
+            delete r;
+            return s;
+        }
+        r->ticket = ctx->next_ticket++;
+        r->t_submit = Clock::now();
+        r->req.pop->inflight.fetch_add(1);
+        ctx->tickets[r->ticket] = r;
+        ctx->queue.push_back(r);
+        *ticket = r->ticket;
+    }
+    ctx->q_cv.notify_all();
+    return SNAPS_OK;
+}
+
+snaps_status snaps_poll(snaps_ctx *ctx, uint64_t ticket, int64_t timeout_us, snaps_result *out)
+{
+    clear_error();
+    if (!ctx) FAIL(SNAPS_EINVAL, "ctx is NULL");
+    std::unique_lock<std::mutex> lk(ctx->q_mu);
+    auto it = ctx->tickets.find(ticket);
+    if (it == ctx->tickets.end()) FAIL(SNAPS_EINVAL, "unknown ticket %llu", (unsigned long long)ticket);
+    Request *r = it->second;
+    if (!r->done) {
+        if (timeout_us == 0) return SNAPS_EAGAIN;
+        if (timeout_us < 0)
+            ctx->done_cv.wait(lk, [&] { return r->done; });
+        else if (!ctx->done_cv.wait_for(lk, std::chrono::microseconds(timeout_us), [&] { return r->done; }))
+            return SNAPS_EAGAIN;
+    }
+    if (out) {
+        out->status = r->status;
+        const auto us = [](Clock::duration d) { return std::chrono::duration<double, std::micro>(d).count(); };
+        out->queue_us = r->status == SNAPS_ECANCELED ? us(r->t_done - r->t_submit) : us(r->t_admit - r->t_submit);
+        out->latency_us = us(r->t_done - r->t_submit);
+        out->objects_x_subspaces = r->req.pop ? r->req.pop->n * (int64_t)r->masks.size() : 0;
+    }
+    ctx->tickets.erase(it);
+    delete r;
+    return SNAPS_OK;
+}
+
+snaps_status snaps_cancel(snaps_ctx *ctx, uint64_t ticket)
+{
+    clear_error();
+    if (!ctx) FAIL(SNAPS_EINVAL, "ctx is NULL");
+    std::lock_guard<std::mutex> lk(ctx->q_mu);
+    auto it = ctx->tickets.find(ticket);
+    if (it == ctx->tickets.end()) FAIL(SNAPS_EINVAL, "unknown ticket %llu", (unsigned long long)ticket);
+    Request *r = it->second;
+    if (r->done || r->running) FAIL(SNAPS_EBUSY, "request %llu is already running or finished", (unsigned long long)ticket);
+    for (auto q = ctx->queue.begin(); q != ctx->queue.end(); ++q) {
+        if (*q == r) {
+            ctx->queue.erase(q);
+            break;
+        }
+    }
+    r->status = SNAPS_ECANCELED;
+    r->done = true;
+    r->t_done = Clock::now();
+    r->req.pop->inflight.fetch_sub(1);
+    ctx->done_cv.notify_all();
+    return SNAPS_OK;
+}
+
+snaps_status snaps_trace(snaps_ctx *ctx, int enable)
+{
+    clear_error();
+    if (!ctx) FAIL(SNAPS_EINVAL, "ctx is NULL");
+    SNAPS_TRY(device_guard(ctx));
+    std::lock_guard<std::mutex> g(ctx->tr_mu);
+    if (enable) {
+        for (auto &m : ctx->marks) {
+            ctx->spare.push_back(m.a);
+            ctx->spare.push_back(m.b);
+        }
+        ctx->marks.clear();
+    }
+    ctx->tracing = enable != 0;
+    return SNAPS_OK;
+}
+
+snaps_status snaps_trace_read(snaps_ctx *ctx, double *ms, int64_t *launches)
+{
+    clear_error();
+    if (!ctx) FAIL(SNAPS_EINVAL, "ctx is NULL");
+    SNAPS_TRY(device_guard(ctx));
+    std::vector<snaps_ctx::Mark> marks;
+    {
+        std::lock_guard<std::mutex> g(ctx->tr_mu);
+        marks.swap(ctx->marks);
+    }
+    double acc[SNAPS_N_PHASES] = {0};
+    int64_t cnt[SNAPS_N_PHASES] = {0};
+    snaps_status st = SNAPS_OK;
+    for (auto &m : marks) {
+        if (cudaEventSynchronize(m.b) != cudaSuccess) st = SNAPS_ECUDA;
+        float t = 0.f;
+        if (cudaEventElapsedTime(&t, m.a, m.b) == cudaSuccess) {
+            acc[m.phase] += t;
+            cnt[m.phase] += m.kernels;
+        } else {
+            cudaGetLastError();
+        }
+    }
+    {
+        std::lock_guard<std::mutex> g(ctx->tr_mu);
+        for (auto &m : marks) {
+            ctx->spare.push_back(m.a);
+            ctx->spare.push_back(m.b);
+        }
+    }
+    for (int p = 0; p < SNAPS_N_PHASES; ++p) {
+        if (ms) ms[p] = acc[p];
+        if (launches) launches[p] = cnt[p];
+    }
+    if (st != SNAPS_OK) FAIL(st, "waiting for trace events failed");
+    return SNAPS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,57 @@
+// Host-visible description of one join launch, shared by the join kernels and
+// the C-ABI layer.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "common.cuh"
+
+namespace snaps {
+
+// Up to 32 subspaces handled together by the lane-per-subspace kernel.  An
+// unused entry has mask 0.
+struct MaskGroup {
+    uint32_t mask[32];
+    float eps2[32];   // squared radius; < 0 disables the eps join for that subspace
+    int32_t slot[32]; // output slot (index into the request's mask list)
+};
+
+// The 2^kTreeLowBits subspaces (H << kTreeLowBits) | L, L = 0..2^kTreeLowBits-1,
+// of one high part H, as scheduled for the subspace-batched tree kernel.
+constexpr int kTreeLowBits = 5;
+constexpr int kTreeWidth = 1 << kTreeLowBits;
+struct TreeChunk {
+    uint32_t high;                 // H
+    uint32_t active;               // bit L set when subspace (H << 5) | L is requested
+    float eps2[kTreeWidth];        // per L, as in MaskGroup
+    int32_t slot[kTreeWidth];
+};
+
+// Outputs of a join.  `scores` is always present: n_slots x 4 x n floats; the
+// join writes rows 0 (eps count), 1 (eps mean distance) and 3 (kNN mean
+// distance) and adds 1 to row 2 (in-degree) of every kNN list member, so row 2
+// must be zero before the launch.
+struct JoinOut {
+    float *scores;
+    int32_t *knn_idx;   // n_slots x n x k, or null
+    float *knn_dist;    // n_slots x n x k, or null
+    int32_t *eps_count; // n_slots x n, or null
+};
+
+struct JoinShape {
+    const float4 *x;    // n_pad rows of 16 floats (4 float4)
+    int64_t n;
+    int64_t n_pad;
+    int k;              // 0 disables the kNN join
+};
+
+// Launch the lane-per-subspace join over `n_groups` groups (device array).
+snaps_status launch_join_lanemask(const JoinShape &s, const MaskGroup *groups, int n_groups,
+                                  const JoinOut &o, DeviceControl *ctrl, cudaStream_t st);
+
+// Launch the subspace-batched tree join over `n_chunks` chunks (device array).
+snaps_status launch_join_tree(const JoinShape &s, const TreeChunk *chunks, int n_chunks,
+                              const JoinOut &o, DeviceControl *ctrl, cudaStream_t st);
+
+}  // namespace snaps

@@ -1,0 +1,501 @@
+// Subspace-batched self-join: DSSJ (Sec. 3.5) and kNNSJ (Sec. 3.6) for the 32
+// subspaces (H << 5) | L, L = 0..31, that share one high part H.
+//
+// Why batching pays: in the fixed order the library uses, the squared
+// distance of subspace S is the FMA fold of the squared feature differences
+// from the highest feature index down.  The subspaces H|L therefore form a
+// tree rooted at the fold over H's features, and node L is one FMA away from
+// node L minus its lowest bit.  A warp evaluates all 32 subspaces of a
+// (query, candidate) pair with 15 subtractions, <= 10 root FMAs and 31 tree
+// FMAs -- about one FMA per subspace instead of one per feature.
+//
+// Mapping: a consumer warp owns one query; each lane owns two candidates
+// (rows c+lane and c+32+lane of the staged tile), packed so that the f32x2
+// instructions (FADD2/FFMA2) process both.  The per-subspace thresholds are
+// warp-uniform.  The unrolled tree walk spends, per subspace, one FFMA2, two
+// compares and a warp vote on whether any lane's distance fell below
+// max(current k-th distance, eps).  Only the lanes that passed then append a
+// (squared distance, subspace, candidate) tuple to the warp's buffer in
+// shared memory (a ballot prefix sum gives each its slot).  At the end of
+// every step (or when the buffer fills), a flush processes 32 tuples at a
+// time with every lane busy: eps counts and exact fixed-point distance sums
+// by shared-memory atomics, then warp-cooperative insertion of the few
+// tuples still below their subspace's k-th distance into its sorted list.
+//
+// A producer warp streams candidate tiles with 1-D bulk copies (TMA) into a
+// ring of stages guarded by full / empty mbarriers, so consumer warps move at
+// their own pace; it also hands out work items (chunk x query block) from an
+// atomic counter, tagging every stage with the work item it belongs to.
+//
+// The first 64 candidates are handled lane-per-subspace (each lane folds its
+// own subspace and keeps a private list) so the lists start full and the
+// thresholds tight instead of sending every early candidate to the handler.
+
+#include <math_constants.h>
+
+#include <algorithm>
+
+#include "device.cuh"
+#include "join.cuh"
+
+namespace snaps {
+namespace {
+
+constexpr int kLB = kTreeLowBits;  // 5
+constexpr int kW = kTreeWidth;     // 32 subspaces per chunk
+constexpr int kTile = 256;
+constexpr int kStages = 3;
+constexpr int kInit = 64;          // candidates handled lane-per-subspace first
+constexpr int kTBuf = 512;         // event tuples buffered per warp
+constexpr int kTFlushAt = kTBuf - 64;  // a node appends at most 64 tuples
+
+// Depth-first order of the subset tree over the low kLB bits: node L's parent
+// is L with its lowest set bit cleared, and its children add a bit below that.
+struct DfsTable {
+    int node[kW];    // L at DFS position p
+    int parent[kW];  // DFS position of the parent (p = 0 is the root)
+    int bit[kW];     // feature (low-bit index) the node adds to its parent
+};
+
+constexpr DfsTable make_dfs() {
+    DfsTable t{};
+    int stack_node[kW] = {};
+    int stack_pos[kW] = {};
+    int cursor[kW] = {};
+    int top = 1, pos = 1;
+    t.node[0] = 0;
+    t.parent[0] = 0;
+    t.bit[0] = 0;
+    stack_node[0] = 0;
+    stack_pos[0] = 0;
+    cursor[0] = kLB - 1;
+    while (top > 0) {
+        const int s = top - 1;
+        if (cursor[s] < 0) {
+            --top;
+            continue;
+        }
+        const int b = cursor[s]--;
+        const int child = stack_node[s] | (1 << b);
+        t.node[pos] = child;
+        t.parent[pos] = stack_pos[s];
+        t.bit[pos] = b;
+        stack_node[top] = child;
+        stack_pos[top] = pos;
+        cursor[top] = b - 1;
+        ++top;
+        ++pos;
+    }
+    return t;
+}
+constexpr DfsTable kDfs = make_dfs();
+static_assert(kDfs.node[1] == 16 && kDfs.parent[kW / 2] > 0, "DFS order as expected");
+
+// Per consumer warp: the state of its query across the chunk's 32 subspaces.
+template <int KMAX>
+struct WarpState {
+    uint2 tbuf[512];                // pending events: (d2 bits, L << 24 | candidate)
+    float ld[kW][KMAX + 1];         // kNN lists by L; +1 keeps both access patterns
+    int lj[kW][KMAX + 1];           // free of bank conflicts
+    unsigned long long esum[kW];    // exact quantised eps distance sums
+    float T[kW];                    // current k-th squared distance
+    float tc[kW];                   // pass threshold max(T, eps) by L
+    int cnt[kW];                    // eps-neighbour counts
+    float eps2[kW];                 // radii of this chunk
+    float escale[kW];               // 2^20 / eps
+};
+
+template <int KMAX, int CW>
+struct TreeSmem {
+    float4 tile[kStages][kTile * 4];
+    long long stage_work[kStages];  // work item of the tile in each stage (-1: no more work)
+    int stage_tile[kStages];        // tile index within the work item
+    uint64_t full[kStages];
+    uint64_t empty[kStages];
+    WarpState<KMAX> ws[CW];
+};
+
+__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
+
+__device__ __forceinline__ float eps_up(float e2) {
+    // d2 < eps_up(e2)  <=>  d2 <= e2 for finite e2 >= 0; disabled radii never pass
+    return e2 >= 0.f ? __uint_as_float(__float_as_uint(e2) + 1u) : -CUDART_INF_F;
+}
+
+// Process the buffered event tuples: eps counts and exact distance sums for
+// the tuples within eps (all lanes, shared-memory atomics), then the tuples
+// still below their subspace's current k-th distance are inserted one by one
+// (warp-cooperative sorted insertion).  Tuples of one subspace sit in the
+// buffer in ascending candidate order.  Returns true when a kNN list changed.
+template <int KMAX>
+__device__ __noinline__ bool flush_tuples(WarpState<KMAX> &ws, int count, int k)
+{
+    const unsigned lane = dev::lane_id();
+    bool changed = false;
+    __syncwarp();
+    for (int b = 0; b < count; b += 32) {
+        const int idx = b + (int)lane;
+        const bool ok = idx < count;
+        const uint2 t = ok ? ws.tbuf[idx] : make_uint2(0x7f800000u, 0u);
+        const int L = (int)(t.y >> 24);
+        const int j = (int)(t.y & 0xffffffu);
+        const float d2 = __uint_as_float(t.x);
+        if (ok && d2 <= ws.eps2[L]) {
+            atomicAdd(&ws.cnt[L], 1);
+            atomicAdd(&ws.esum[L], (unsigned long long)dev::eps_quant(d2, ws.escale[L]));
+        }
+        unsigned kb = __ballot_sync(dev::kFull, ok && d2 < ws.T[L]);
+        while (kb) {
+            const int src = __ffs(kb) - 1;
+            kb &= kb - 1;
+            const int Ls = __shfl_sync(dev::kFull, L, src);
+            const float ds = __shfl_sync(dev::kFull, d2, src);
+            const int js = __shfl_sync(dev::kFull, j, src);
+            float T = ws.T[Ls];
+            if (!(ds < T)) continue;
+            float my_d = lane < (unsigned)k ? ws.ld[Ls][lane] : CUDART_INF_F;
+            int my_j = lane < (unsigned)k ? ws.lj[Ls][lane] : 0x7fffffff;
+            const bool before = lane < (unsigned)k && (my_d < ds || (my_d == ds && my_j < js));
+            const int pos = __popc(__ballot_sync(dev::kFull, before));
+            const float up_d = __shfl_up_sync(dev::kFull, my_d, 1);
+            const int up_j = __shfl_up_sync(dev::kFull, my_j, 1);
+            if (lane == (unsigned)pos) {
+                my_d = ds;
+                my_j = js;
+            } else if (lane > (unsigned)pos && lane < (unsigned)k) {
+                my_d = up_d;
+                my_j = up_j;
+            }
+            T = __shfl_sync(dev::kFull, my_d, k - 1);
+            if (lane < (unsigned)k) {
+                ws.ld[Ls][lane] = my_d;
+                ws.lj[Ls][lane] = my_j;
+            }
+            if (lane == 0) {
+                ws.T[Ls] = T;
+                ws.tc[Ls] = fmaxf(T, eps_up(ws.eps2[Ls]));
+            }
+            __syncwarp();
+            changed = true;
+        }
+    }
+    __syncwarp();
+    return changed;
+}
+
+// Pass thresholds into registers, by DFS position.
+template <int P, int KMAX>
+__device__ __forceinline__ void load_thresholds(const WarpState<KMAX> &ws, float (&Tc)[kW])
+{
+    if constexpr (P < kW) {
+        constexpr int L = kDfs.node[P];
+        Tc[P] = ws.tc[L];
+        load_thresholds<P + 1>(ws, Tc);
+    }
+}
+
+// Walk DFS nodes P .. END-1: one FFMA2 per node, the pass test against the
+// node's threshold, and a warp vote; when some lane passed, the passing lanes
+// append their tuples, and a nearly full buffer is flushed.
+template <int P, int END, int KMAX>
+__device__ __forceinline__ void tree_walk(WarpState<KMAX> &ws, float2 (&v)[kW],
+                                          const float2 (&d)[15], float (&Tc)[kW], int &count,
+                                          int ja, int jb, int k)
+{
+    if constexpr (P < END) {
+        if constexpr (P > 0) {
+            constexpr int b = kDfs.bit[P];
+            constexpr int par = kDfs.parent[P];
+            v[P] = __ffma2_rn(d[b], d[b], v[par]);
+        }
+        constexpr int L = kDfs.node[P];
+        const bool pa = v[P].x < Tc[P], pb = v[P].y < Tc[P];
+        if (__any_sync(dev::kFull, pa | pb)) {
+            const unsigned lt = (1u << dev::lane_id()) - 1u;
+            const unsigned ba = __ballot_sync(dev::kFull, pa);
+            const unsigned bb = __ballot_sync(dev::kFull, pb);
+            if (pa) ws.tbuf[count + __popc(ba & lt)] = make_uint2(__float_as_uint(v[P].x), (L << 24) | ja);
+            count += __popc(ba);
+            if (pb) ws.tbuf[count + __popc(bb & lt)] = make_uint2(__float_as_uint(v[P].y), (L << 24) | jb);
+            count += __popc(bb);
+            if (count > kTFlushAt) {
+                if (flush_tuples<KMAX>(ws, count, k)) load_thresholds<0>(ws, Tc);
+                count = 0;
+            }
+        }
+        tree_walk<P + 1, END>(ws, v, d, Tc, count, ja, jb, k);
+    }
+}
+
+template <int KMAX, int CW>
+__global__ void __launch_bounds__((CW + 1) * 32, 1)
+    join_tree_kernel(JoinShape s, const TreeChunk *__restrict__ chunks, int n_chunks, JoinOut o,
+                     DeviceControl *ctrl)
+{
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    TreeSmem<KMAX, CW> &sm = *reinterpret_cast<TreeSmem<KMAX, CW> *>(smem_raw);
+    const int warp = threadIdx.x >> 5;
+    const unsigned lane = threadIdx.x & 31u;
+    const int64_t n = s.n;
+    const int k = s.k;
+    const long long n_qb = (n + CW - 1) / CW;
+    const long long total = n_qb * (long long)n_chunks;
+    const int n_tiles = (int)(s.n_pad / kTile);
+    const float4 *x = s.x;
+
+    if (threadIdx.x == 0) {
+        for (int st = 0; st < kStages; ++st) {
+            dev::mbar_init(&sm.full[st], 1);
+            dev::mbar_init(&sm.empty[st], CW);
+        }
+        dev::fence_barrier_init();
+    }
+    __syncthreads();
+
+    if (warp == CW) {
+        // ---- producer: work items and candidate tiles ------------------------------
+        if (lane != 0) return;
+        uint32_t g = 0;  // tiles issued so far
+        for (;;) {
+            const long long w = (long long)atomicAdd(&ctrl->next_work, 1ull);
+            const bool end = w >= total;
+            const int count = end ? 1 : n_tiles;
+            for (int t = 0; t < count; ++t, ++g) {
+                const uint32_t st = g % kStages;
+                if (g >= (uint32_t)kStages &&
+                    !dev::mbar_wait(&sm.empty[st], ((g / kStages) - 1) & 1u)) {
+                    atomicOr(&ctrl->error, kErrTimeout);
+                    return;
+                }
+                sm.stage_work[st] = end ? -1 : w;
+                sm.stage_tile[st] = t;
+                if (end)
+                    dev::mbar_arrive(&sm.full[st]);
+                else
+                    dev::bulk_load(sm.tile[st], x + (int64_t)t * kTile * 4, kTile * 64, &sm.full[st]);
+            }
+            if (end) return;
+        }
+    }
+
+    // ---- consumers -------------------------------------------------------------------
+    WarpState<KMAX> &ws = sm.ws[warp];
+    uint32_t g = 0;
+    float Tc[kW];
+    float2 nxq[15];
+    float xq[16];
+    int64_t i = 0;
+    bool valid = false;
+    uint32_t active = 0, high = 0;
+    int tcount = 0;  // buffered event tuples (warp-uniform)
+    const TreeChunk *ch = nullptr;
+    for (;; ++g) {
+        const uint32_t st = g % kStages;
+        if (!dev::mbar_wait(&sm.full[st], (g / kStages) & 1u)) {
+            if (lane == 0) atomicOr(&ctrl->error, kErrTimeout);
+            return;
+        }
+        const long long w = sm.stage_work[st];
+        if (w < 0) return;
+        const int t = sm.stage_tile[st];
+        const float4 *tile = sm.tile[st];
+
+        if (t == 0) {
+            // ---- new work item: this warp's query and the chunk's subspaces ------------
+            ch = &chunks[w / n_qb];
+            i = (w % n_qb) * CW + warp;
+            valid = i < n;
+            high = ch->high;
+            active = valid ? ch->active : 0u;
+            if (valid) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const float4 v = x[row_quad(i, q)];
+                    xq[4 * q + 0] = v.x;
+                    xq[4 * q + 1] = v.y;
+                    xq[4 * q + 2] = v.z;
+                    xq[4 * q + 3] = v.w;
+                }
+            } else {
+#pragma unroll
+                for (int f = 0; f < 16; ++f) xq[f] = 0.f;
+            }
+#pragma unroll
+            for (int f = 0; f < 15; ++f) nxq[f] = f2(-xq[f], -xq[f]);
+            {
+                const uint32_t L = lane;
+                const float e2 = ch->eps2[L];
+                ws.eps2[L] = e2;
+                ws.escale[L] = dev::eps_scale(e2).scale;
+                for (int p = 0; p < KMAX; ++p) {
+                    ws.ld[L][p] = CUDART_INF_F;
+                    ws.lj[L][p] = 0x7fffffff;
+                }
+                ws.esum[L] = 0ull;
+                ws.cnt[L] = 0;
+                ws.T[L] = (((active >> L) & 1u) && k > 0) ? CUDART_INF_F : -CUDART_INF_F;
+            }
+            __syncwarp();
+            // ---- set-up phase: lane L folds subspace L over the first candidates and
+            // keeps a private sorted list ---------------------------------------------
+            if (valid) {
+                const uint32_t L = lane;
+                const bool mine = (active >> L) & 1u;
+                const uint32_t mask = (high << kLB) | L;
+                const float e2 = ws.eps2[L];
+                const float sc = ws.escale[L];
+                float T = ws.T[L];
+                int cnt = 0;
+                unsigned long long qs = 0;
+                float wgt[15];
+#pragma unroll
+                for (int f = 0; f < 15; ++f) wgt[f] = ((mask >> f) & 1u) ? 1.f : 0.f;
+                const int c_end = (int)std::min<int64_t>(kInit, n);
+                for (int c = 0; c < c_end; ++c) {
+                    if ((int64_t)c == i) continue;
+                    float xc[16];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const float4 v = tile[q * kTile + c];
+                        xc[4 * q + 0] = v.x;
+                        xc[4 * q + 1] = v.y;
+                        xc[4 * q + 2] = v.z;
+                        xc[4 * q + 3] = v.w;
+                    }
+                    float acc = 0.f;
+#pragma unroll
+                    for (int f = 14; f >= 0; --f) {
+                        const float dd = xc[f] - xq[f];
+                        acc = fmaf(dd * wgt[f], dd, acc);
+                    }
+                    if (mine && acc <= e2) {
+                        ++cnt;
+                        qs += dev::eps_quant(acc, sc);
+                    }
+                    if (mine && acc < T) T = dev::private_insert(ws.ld[L], ws.lj[L], k, acc, c);
+                }
+                ws.T[L] = T;
+                ws.cnt[L] = cnt;
+                ws.esum[L] = qs;
+            }
+            {
+                const uint32_t L = lane;
+                ws.tc[L] = ((active >> L) & 1u) ? fmaxf(ws.T[L], eps_up(ws.eps2[L])) : -CUDART_INF_F;
+            }
+            __syncwarp();
+            load_thresholds<0>(ws, Tc);
+        }
+
+        // ---- main loop over the tile -----------------------------------------------------
+        if (valid) {
+            const int64_t base = (int64_t)t * kTile;
+            for (int c = (t == 0 ? kInit : 0); c < kTile; c += 64) {
+                const int64_t ja = base + c + lane;
+                const int64_t jb = ja + 32;
+                float2 d[15];
+                {
+                    float xa[16], xb[16];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const float4 va = tile[q * kTile + c + lane];
+                        const float4 vb = tile[q * kTile + c + 32 + lane];
+                        xa[4 * q + 0] = va.x; xa[4 * q + 1] = va.y;
+                        xa[4 * q + 2] = va.z; xa[4 * q + 3] = va.w;
+                        xb[4 * q + 0] = vb.x; xb[4 * q + 1] = vb.y;
+                        xb[4 * q + 2] = vb.z; xb[4 * q + 3] = vb.w;
+                    }
+                    if (i >= base + c && i < base + c + 64) {
+                        // the query itself is in this step: make it infinitely far
+                        if (ja == i) {
+#pragma unroll
+                            for (int f = 0; f < 16; ++f) xa[f] = CUDART_INF_F;
+                        }
+                        if (jb == i) {
+#pragma unroll
+                            for (int f = 0; f < 16; ++f) xb[f] = CUDART_INF_F;
+                        }
+                    }
+#pragma unroll
+                    for (int f = 0; f < 15; ++f) d[f] = __fadd2_rn(f2(xa[f], xb[f]), nxq[f]);
+                }
+                float2 v[kW];
+                v[0] = f2(0.f, 0.f);
+#pragma unroll
+                for (int f = 14; f >= kLB; --f)
+                    if ((high >> (f - kLB)) & 1u) v[0] = __ffma2_rn(d[f], d[f], v[0]);
+                tree_walk<0, kW, KMAX>(ws, v, d, Tc, tcount, (int)ja, (int)jb, k);
+                // flushing every step keeps the kNN thresholds at most one step stale
+                if (tcount > 0) {
+                    if (flush_tuples<KMAX>(ws, tcount, k)) load_thresholds<0>(ws, Tc);
+                    tcount = 0;
+                }
+            }
+        }
+        __syncwarp();
+        if (lane == 0) dev::mbar_arrive(&sm.empty[st]);
+
+        // ---- end of the work item: lane L reports subspace L ---------------------------
+        if (t == n_tiles - 1) {
+            if (tcount > 0) flush_tuples<KMAX>(ws, tcount, k);
+            tcount = 0;
+            const uint32_t L = lane;
+            if ((active >> L) & 1u) {
+                const int slot = ch->slot[L];
+                float *sc = o.scores + (int64_t)slot * 4 * n;
+                const int cnt = ws.cnt[L];
+                sc[i] = (float)cnt;
+                sc[n + i] = dev::eps_mean(ws.esum[L], cnt, ws.escale[L]);
+                if (o.eps_count) o.eps_count[(int64_t)slot * n + i] = cnt;
+                if (k > 0) {
+                    float msum = 0.f;
+                    for (int p = 0; p < k; ++p) {
+                        const float dd = sqrtf(ws.ld[L][p]);
+                        const int j = ws.lj[L][p];
+                        msum += dd;
+                        if (j >= 0 && j < n) atomicAdd(&sc[2 * n + j], 1.f);
+                        if (o.knn_idx) o.knn_idx[((int64_t)slot * n + i) * k + p] = j;
+                        if (o.knn_dist) o.knn_dist[((int64_t)slot * n + i) * k + p] = dd;
+                    }
+                    sc[3 * n + i] = msum / (float)k;
+                }
+            }
+            __syncwarp();
+        }
+    }
+}
+
+template <int KMAX, int CW>
+snaps_status launch_tree(const JoinShape &s, const TreeChunk *chunks, int n_chunks,
+                         const JoinOut &o, DeviceControl *ctrl, cudaStream_t st)
+{
+    const size_t smem = sizeof(TreeSmem<KMAX, CW>);
+    auto kern = join_tree_kernel<KMAX, CW>;
+    SNAPS_CHECK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int dev = 0, sms = 0, per_sm = 0;
+    SNAPS_CHECK_CUDA(cudaGetDevice(&dev));
+    SNAPS_CHECK_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    SNAPS_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, (CW + 1) * 32, smem));
+    if (per_sm < 1) {
+        set_error("subspace-batched join does not fit on an SM (smem %zu)", smem);
+        return SNAPS_ECUDA;
+    }
+    const long long n_qb = (s.n + CW - 1) / CW;
+    const long long total = n_qb * (long long)n_chunks;
+    const long long grid = std::min<long long>(total, (long long)sms * per_sm);
+    SNAPS_CHECK_CUDA(cudaMemsetAsync(&ctrl->next_work, 0, sizeof(unsigned long long), st));
+    kern<<<(unsigned)grid, (CW + 1) * 32, smem, st>>>(s, chunks, n_chunks, o, ctrl);
+    SNAPS_CHECK_CUDA(cudaGetLastError());
+    return SNAPS_OK;
+}
+
+}  // namespace
+
+snaps_status launch_join_tree(const JoinShape &s, const TreeChunk *chunks, int n_chunks,
+                              const JoinOut &o, DeviceControl *ctrl, cudaStream_t st)
+{
+    if (n_chunks <= 0) return SNAPS_OK;
+    if (s.k <= 16) return launch_tree<16, 15>(s, chunks, n_chunks, o, ctrl, st);
+    return launch_tree<32, 8>(s, chunks, n_chunks, o, ctrl, st);
+}
+
+}  // namespace snaps
