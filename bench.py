@@ -50,7 +50,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--n", type=int, default=N_DEFAULT)
-    ap.add_argument("--masks", default="all", help="'all' or a count of seeded sample subspaces")
+    ap.add_argument("--masks", default="all",
+                    help="'all', a count of seeded sample subspaces, or 'chunk:H' (H = 10 binary "
+                         "digits: the 32 subspaces (H << 5) | L sharing that high part)")
     ap.add_argument("--k", type=int, default=K_DEFAULT)
     ap.add_argument("--precision", choices=["fp32", "tc_f16"], default="fp32")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -61,11 +63,19 @@ def parse():
 def workload_masks(spec: str) -> np.ndarray:
     if spec == "all":
         return snaps_inputs.all_masks()
+    if spec.startswith("chunk:"):
+        allm = snaps_inputs.all_masks()
+        return allm[(allm >> 5) == int(spec[6:], 2)]
     return snaps_inputs.mask_sample(int(spec), SAMPLE_SEED)
 
 
 def workload_name(args, n_masks):
-    sub = "all 32,752 subspaces" if args.masks == "all" else f"{n_masks} sampled subspaces"
+    if args.masks == "all":
+        sub = "all 32,752 subspaces"
+    elif args.masks.startswith("chunk:"):
+        sub = f"the {n_masks} subspaces with high features {args.masks[6:]}"
+    else:
+        sub = f"{n_masks} sampled subspaces"
     return (f"batched scoring: N={args.n} objects x {sub} of 2-15 of 15 features, "
             f"k={args.k}, eps=0.05*sqrt(d), seed 0")
 
@@ -201,6 +211,7 @@ def run_ours(args, rank, world, dist):
     dom_launches = trace[dominant][1]
     achieved = evals_per_step * args.steps / (dom_ms / 1e3) / 1e12 if dom_ms > 0 else None
     launches = int(sum(v[1] for v in trace.values()))
+    measured_alu = snaps.snaps_calibrate_alu(local) / 1e12
 
     # end to end through the C ABI with host buffers
     e2e = None
@@ -254,7 +265,9 @@ def run_ours(args, rank, world, dist):
                      "peak_basis": f"{props.multi_processor_count} SMs x {COMPARES_PER_SM_CLK} "
                                    f"FP32 compares/clk x {max_mhz:.0f} MHz (one compare per "
                                    f"pair-subspace evaluation)",
-                     "kernel_ms_per_launch": dom_ms / max(dom_launches, 1)},
+                     "kernel_ms_per_launch": dom_ms / max(dom_launches, 1),
+                     "measured_alu_peak": measured_alu,
+                     "frac_of_measured_alu": (achieved / measured_alu) if achieved else None},
         "phase_ms_per_step": {kname: v[0] / args.steps for kname, v in trace.items()},
         "clocks": clocks,
         "e2e": e2e,

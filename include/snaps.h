@@ -203,6 +203,15 @@ snaps_status snaps_cancel(snaps_ctx *ctx, uint64_t ticket);
 /* Number of requests the scheduler may run at once (default 4, 1..64). */
 snaps_status snaps_set_slots(snaps_ctx *ctx, int slots);
 
+/* ---- calibration ---- */
+
+/* Measure on `device` the rate of FP32 (add, compare) pairs -- one pair per
+ * (pair, subspace) evaluation is the plain join's algorithmic minimum -- with
+ * a dependency-free kernel occupying every SM; writes pairs per second.  The
+ * paper has no counterpart: this backs the ALU roofline denominator.
+ * Errors: EINVAL (NULL output), ECUDA. */
+snaps_status snaps_calibrate_alu(int device, double *evals_per_s);
+
 /* ---- tracing: device time per phase ---- */
 
 #define SNAPS_PHASE_INDEX 0      /* normalisation kernels of snaps_index */

@@ -87,6 +87,7 @@ def lib():
             "snaps_cancel": ([p, ctypes.c_uint64], i32),
             "snaps_set_slots": ([p, i32], i32),
             "snaps_trace": ([p, i32], i32),
+            "snaps_calibrate_alu": ([i32, p], i32),
             "snaps_trace_read": ([p, p, p], i32),
         }
         for name, (args, res) in sig.items():
@@ -222,6 +223,13 @@ def snaps_scores(pop: int, masks, k: int, eps=None, precision: int = SNAPS_FP32,
 
 def snaps_set_slots(ctx: int, slots: int) -> None:
     _check(lib().snaps_set_slots(ctx, slots), "snaps_set_slots")
+
+
+def snaps_calibrate_alu(device: int = 0) -> float:
+    """Measured FP32 (add, compare) pairs per second on `device`."""
+    v = ctypes.c_double()
+    _check(lib().snaps_calibrate_alu(device, ctypes.byref(v)), "snaps_calibrate_alu")
+    return v.value
 
 
 def snaps_trace(ctx: int, enable: bool = True) -> None:

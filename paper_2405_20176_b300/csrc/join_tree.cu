@@ -14,7 +14,8 @@
 // instructions (FADD2/FFMA2) process both.  The per-subspace thresholds are
 // warp-uniform.  The unrolled tree walk spends, per subspace, one FFMA2, two
 // compares and a warp vote on whether any lane's distance fell below
-// max(current k-th distance, eps).  Only the lanes that passed then append a
+// max(current k-th distance, eps); it votes on 8 subspaces before branching,
+// so their latencies overlap.  Only the lanes that passed then append a
 // (squared distance, subspace, candidate) tuple to the warp's buffer in
 // shared memory (a ballot prefix sum gives each its slot).  At the end of
 // every step (or when the buffer fills), a flush processes 32 tuples at a
@@ -27,7 +28,7 @@
 // their own pace; it also hands out work items (chunk x query block) from an
 // atomic counter, tagging every stage with the work item it belongs to.
 //
-// The first 64 candidates are handled lane-per-subspace (each lane folds its
+// The first 256 candidates are handled lane-per-subspace (each lane folds its
 // own subspace and keeps a private list) so the lists start full and the
 // thresholds tight instead of sending every early candidate to the handler.
 
@@ -45,9 +46,10 @@ constexpr int kLB = kTreeLowBits;  // 5
 constexpr int kW = kTreeWidth;     // 32 subspaces per chunk
 constexpr int kTile = 256;
 constexpr int kStages = 3;
-constexpr int kInit = 64;          // candidates handled lane-per-subspace first
+constexpr int kInit = 256;         // candidates handled lane-per-subspace first (one tile)
 constexpr int kTBuf = 512;         // event tuples buffered per warp
 constexpr int kTFlushAt = kTBuf - 64;  // a node appends at most 64 tuples
+constexpr int kGroup = 8;          // nodes voted on before any of them appends
 
 // Depth-first order of the subset tree over the low kLB bits: node L's parent
 // is L with its lowest set bit cleared, and its children add a bit below that.
@@ -194,13 +196,11 @@ __device__ __forceinline__ void load_thresholds(const WarpState<KMAX> &ws, float
     }
 }
 
-// Walk DFS nodes P .. END-1: one FFMA2 per node, the pass test against the
-// node's threshold, and a warp vote; when some lane passed, the passing lanes
-// append their tuples, and a nearly full buffer is flushed.
-template <int P, int END, int KMAX>
-__device__ __forceinline__ void tree_walk(WarpState<KMAX> &ws, float2 (&v)[kW],
-                                          const float2 (&d)[15], float (&Tc)[kW], int &count,
-                                          int ja, int jb, int k)
+// Nodes P .. END-1 of one group: the FFMA2s and the warp votes, with no
+// branch in between so the scheduler can overlap the nodes' latencies.
+template <int P, int END>
+__device__ __forceinline__ void group_votes(float2 (&v)[kW], const float2 (&d)[15],
+                                            const float (&Tc)[kW], unsigned &gvote)
 {
     if constexpr (P < END) {
         if constexpr (P > 0) {
@@ -208,9 +208,23 @@ __device__ __forceinline__ void tree_walk(WarpState<KMAX> &ws, float2 (&v)[kW],
             constexpr int par = kDfs.parent[P];
             v[P] = __ffma2_rn(d[b], d[b], v[par]);
         }
-        constexpr int L = kDfs.node[P];
-        const bool pa = v[P].x < Tc[P], pb = v[P].y < Tc[P];
-        if (__any_sync(dev::kFull, pa | pb)) {
+        const bool pass = (v[P].x < Tc[P]) | (v[P].y < Tc[P]);
+        gvote |= __any_sync(dev::kFull, pass) ? (1u << (P % kGroup)) : 0u;
+        group_votes<P + 1, END>(v, d, Tc, gvote);
+    }
+}
+
+// The triggered nodes of one group: the lanes that passed append their
+// tuples; a nearly full buffer is flushed.
+template <int P, int END, int KMAX>
+__device__ __forceinline__ void group_appends(WarpState<KMAX> &ws, const float2 (&v)[kW],
+                                              float (&Tc)[kW], unsigned gvote, int &count,
+                                              int ja, int jb, int k)
+{
+    if constexpr (P < END) {
+        if (gvote & (1u << (P % kGroup))) {
+            constexpr int L = kDfs.node[P];
+            const bool pa = v[P].x < Tc[P], pb = v[P].y < Tc[P];
             const unsigned lt = (1u << dev::lane_id()) - 1u;
             const unsigned ba = __ballot_sync(dev::kFull, pa);
             const unsigned bb = __ballot_sync(dev::kFull, pb);
@@ -223,7 +237,22 @@ __device__ __forceinline__ void tree_walk(WarpState<KMAX> &ws, float2 (&v)[kW],
                 count = 0;
             }
         }
-        tree_walk<P + 1, END>(ws, v, d, Tc, count, ja, jb, k);
+        group_appends<P + 1, END, KMAX>(ws, v, Tc, gvote, count, ja, jb, k);
+    }
+}
+
+// Walk the DFS in groups of kGroup nodes: votes first, then appends.
+template <int G, int KMAX>
+__device__ __forceinline__ void tree_walk(WarpState<KMAX> &ws, float2 (&v)[kW],
+                                          const float2 (&d)[15], float (&Tc)[kW], int &count,
+                                          int ja, int jb, int k)
+{
+    if constexpr (G * kGroup < kW) {
+        unsigned gvote = 0;
+        group_votes<G * kGroup, (G + 1) * kGroup>(v, d, Tc, gvote);
+        if (gvote)
+            group_appends<G * kGroup, (G + 1) * kGroup, KMAX>(ws, v, Tc, gvote, count, ja, jb, k);
+        tree_walk<G + 1, KMAX>(ws, v, d, Tc, count, ja, jb, k);
     }
 }
 
@@ -423,7 +452,7 @@ __global__ void __launch_bounds__((CW + 1) * 32, 1)
 #pragma unroll
                 for (int f = 14; f >= kLB; --f)
                     if ((high >> (f - kLB)) & 1u) v[0] = __ffma2_rn(d[f], d[f], v[0]);
-                tree_walk<0, kW, KMAX>(ws, v, d, Tc, tcount, (int)ja, (int)jb, k);
+                tree_walk<0, KMAX>(ws, v, d, Tc, tcount, (int)ja, (int)jb, k);
                 // flushing every step keeps the kNN thresholds at most one step stale
                 if (tcount > 0) {
                     if (flush_tuples<KMAX>(ws, tcount, k)) load_thresholds<0>(ws, Tc);
