@@ -203,6 +203,39 @@ snaps_status snaps_cancel(snaps_ctx *ctx, uint64_t ticket);
 /* Number of requests the scheduler may run at once (default 4, 1..64). */
 snaps_status snaps_set_slots(snaps_ctx *ctx, int slots);
 
+/* ---- scoring without device allocation ---- */
+
+#define SNAPS_STATIC_MAX_N 32768       /* objects per allocation-free call */
+#define SNAPS_STATIC_MAX_MASKS 32768   /* subspaces per allocation-free call */
+
+/* snaps_scores for callers that cannot let a library allocate device memory
+ * -- a process holding a fixed, pre-planned share of a GPU, or code that must
+ * not call cudaMalloc / cudaFree because they can synchronise the device.  The
+ * paper has no counterpart; this is a deployment convenience.
+ * It allocates nothing.  Its working memory -- the normalised population,
+ * statistics, the kernels' control block and the subspace plan, about 2.7 MB
+ * -- is one static device array inside the library that every GPU which loads
+ * the library keeps until the process exits.  The first call on a device looks
+ * up that array's device address; make that first call before any stream
+ * capture.
+ * device: CUDA device to run on (made current by the call).
+ * feat: n x f float32 row-major in device memory, normalised as flags say
+ *   (SNAPS_NORM_MINMAX / SNAPS_NAN_TO_MEAN), 2 <= n <= SNAPS_STATIC_MAX_N.
+ * masks, n_masks (<= SNAPS_STATIC_MAX_MASKS), k, eps: as for snaps_scores.
+ * scores: n_masks x 4 x n float32, device memory (required).
+ * top: n_masks x 4 x top_n int32, device memory, or NULL.
+ * The call synchronises `stream` before returning.  Every call shares the one
+ * array and it keeps the last call's contents (the call clears what must start
+ * at zero), so calls whose GPU work overlaps -- on different streams or
+ * threads -- race; issue them one after another.  Results equal those of
+ * snaps_index + snaps_scores.
+ * Errors: EINVAL (sizes beyond the limits, host pointers, bad masks / k / eps,
+ * non-finite features), ETIMEOUT, ECUDA. */
+snaps_status snaps_scores_static(int device, const float *feat, int64_t n, int f,
+                                 uint32_t flags, const uint16_t *masks, int n_masks, int k,
+                                 const float *eps, float *scores, int32_t *top, int top_n,
+                                 void *stream);
+
 /* ---- calibration ---- */
 
 /* Measure on `device` the rate of FP32 (add, compare) pairs -- one pair per

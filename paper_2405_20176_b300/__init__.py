@@ -32,6 +32,8 @@ SNAPS_NORM_MINMAX = 0x1
 SNAPS_NAN_TO_MEAN = 0x2
 SNAPS_FP32 = 0
 SNAPS_TC_F16 = 1
+SNAPS_STATIC_MAX_N = 32768
+SNAPS_STATIC_MAX_MASKS = 32768
 SNAPS_PHASE_INDEX, SNAPS_PHASE_JOIN_TREE, SNAPS_PHASE_JOIN_LANE, SNAPS_PHASE_NORM, SNAPS_PHASE_TOP = range(5)
 SNAPS_N_PHASES = 5
 PHASE_NAMES = ["index", "join_tree", "join_lane", "norm", "top"]
@@ -88,6 +90,7 @@ def lib():
             "snaps_set_slots": ([p, i32], i32),
             "snaps_trace": ([p, i32], i32),
             "snaps_calibrate_alu": ([i32, p], i32),
+            "snaps_scores_static": ([i32, p, i64, i32, u32, p, i32, i32, p, p, p, i32, p], i32),
             "snaps_trace_read": ([p, p, p], i32),
         }
         for name, (args, res) in sig.items():
@@ -219,6 +222,22 @@ def snaps_scores(pop: int, masks, k: int, eps=None, precision: int = SNAPS_FP32,
     _check(lib().snaps_scores(pop, m.ctypes.data, m.size, k, None if e is None else e.ctypes.data,
                               precision, _ptr(scores), _ptr(norm), _ptr(top),
                               top_n if top is not None else 0, _stream(stream)), "snaps_scores")
+
+
+def snaps_scores_static(device: int, feat, masks, k: int, eps=None, flags: int = SNAPS_NORM_MINMAX,
+                        scores=None, top=None, top_n: int = 100, stream=None) -> None:
+    """Allocation-free scoring: ``feat`` (n, f), ``scores`` and ``top`` are
+    device arrays owned by the caller; the library uses only its fixed static
+    working array."""
+    if len(feat.shape) != 2:
+        raise ValueError("feat must be 2-D (n, f)")
+    m = _masks(masks)
+    e = _eps(eps, m.size)
+    _check(lib().snaps_scores_static(device, _ptr(feat), int(feat.shape[0]), int(feat.shape[1]),
+                                     flags, m.ctypes.data, m.size, k,
+                                     None if e is None else e.ctypes.data, _ptr(scores), _ptr(top),
+                                     top_n if top is not None else 0, _stream(stream)),
+           "snaps_scores_static")
 
 
 def snaps_set_slots(ctx: int, slots: int) -> None:
