@@ -57,6 +57,13 @@ def parse():
     ap.add_argument("--precision", choices=["fp32", "tc_f16"], default="fp32")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--serving", type=int, default=0, metavar="R",
+                    help="instead of the batching workload, run a Poisson stream of R scoring "
+                         "requests through snaps_submit/snaps_poll and report p50/p99 latency")
+    ap.add_argument("--serving-max-n", type=int, default=100000)
+    ap.add_argument("--serving-max-masks", type=int, default=64)
+    ap.add_argument("--serving-slots", type=int, default=4)
+    ap.add_argument("--serving-load", type=float, default=0.7)
     return ap.parse_args()
 
 
@@ -276,6 +283,97 @@ def run_ours(args, rank, world, dist):
     return result
 
 
+# ---- serving: a Poisson stream of mixed requests ----------------------------------------------
+
+def serving_requests(args, rng):
+    """Populations N ~ LogUniform(1e3, max_n) (seeded per population), requests
+    with 1..max_masks subspaces (d uniform in 2..15, then a uniform subset),
+    k in {5, 10, 20}, eps = 0.05 sqrt(d)."""
+    n_pops = 12
+    pops = []
+    for p in range(n_pops):
+        n = int(np.exp(rng.uniform(np.log(1e3), np.log(args.serving_max_n))))
+        pops.append((n, int(rng.integers(0, 1 << 30))))
+    reqs = []
+    for _ in range(args.serving):
+        pi = int(rng.integers(0, n_pops))
+        nm = int(rng.integers(1, args.serving_max_masks + 1))
+        masks = []
+        for _ in range(nm):
+            d = int(rng.integers(2, 16))
+            feats = rng.choice(15, size=d, replace=False)
+            masks.append(int(sum(1 << int(f) for f in feats)))
+        reqs.append((pi, np.array(masks, dtype=np.uint16), int(rng.choice([5, 10, 20]))))
+    return pops, reqs
+
+
+def run_serving(args):
+    import torch
+
+    import paper_2405_20176_b300 as snaps
+
+    torch.cuda.set_device(0)
+    rng = np.random.default_rng(20240530)
+    pops, reqs = serving_requests(args, rng)
+    ctx = snaps.snaps_create(0)
+    snaps.snaps_set_slots(ctx, args.serving_slots)
+    handles = [snaps.snaps_index(ctx, snaps_inputs.population(n, seed)) for n, seed in pops]
+    tops = [torch.empty((m.size, 4, 100), dtype=torch.int32, device="cuda") for _, m, _ in reqs]
+    torch.cuda.synchronize()
+    # service time of one request alone, to set the arrival rate
+    t0 = time.perf_counter()
+    n_cal = min(8, len(reqs))
+    for (pi, m, k), tp in zip(reqs[:n_cal], tops[:n_cal]):
+        snaps.snaps_scores(handles[pi], m, k, top=tp, top_n=100)
+    torch.cuda.synchronize()
+    mean_service = (time.perf_counter() - t0) / n_cal
+    rate = args.serving_load / mean_service
+    gaps = rng.exponential(1.0 / rate, size=len(reqs))
+    arrivals = np.cumsum(gaps)
+    with ClockSampler(0) as clk:
+        start = time.perf_counter()
+        tickets = []
+        for (pi, m, k), tp, at in zip(reqs, tops, arrivals):
+            wait = start + at - time.perf_counter()
+            if wait > 0:
+                time.sleep(wait)
+            tickets.append(snaps.snaps_submit(ctx, handles[pi], m, k, top=tp, top_n=100))
+        results = [snaps.snaps_poll(ctx, t, -1) for t in tickets]
+        makespan = time.perf_counter() - start
+    lat = np.array([r.latency_us for r in results]) / 1e3
+    queue = np.array([r.queue_us for r in results]) / 1e3
+    work = float(sum(r.objects_x_subspaces for r in results))
+    bad = [r.status for r in results if r.status != snaps.SNAPS_OK]
+    for h in handles:
+        snaps.snaps_release(h)
+    snaps.snaps_destroy(ctx)
+    return {
+        "metric": "objects*subspaces/s (serving stream)",
+        "value": work / makespan,
+        "unit": "objects*subspaces/s",
+        "n_gpus": 1,
+        "higher_is_better": True,
+        "p50_latency_ms": float(np.percentile(lat, 50)),
+        "p99_latency_ms": float(np.percentile(lat, 99)),
+        "p50_queue_ms": float(np.percentile(queue, 50)),
+        "p99_queue_ms": float(np.percentile(queue, 99)),
+        "requests": len(results),
+        "failed": len(bad),
+        "makespan_s": makespan,
+        "arrival_rate_per_s": rate,
+        "mean_service_alone_s": mean_service,
+        "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": f"Poisson stream of {len(reqs)} scoring requests at load "
+                               f"{args.serving_load} of one request's service rate; 12 resident "
+                               f"populations N ~ LogUniform(1e3, {args.serving_max_n}); 1-"
+                               f"{args.serving_max_masks} subspaces (d uniform 2..15); "
+                               f"k in {{5,10,20}}; eps = 0.05*sqrt(d); top-100 outputs",
+                   "slots": args.serving_slots, "precision": args.precision},
+        "clocks": clk.summary(),
+    }
+
+
 # ---- CPU oracle legs -------------------------------------------------------------------------
 
 def oracle_rate(x, masks, budget_s, k):
@@ -353,6 +451,9 @@ def main():
     if args.impl == "reference":
         if rank == 0:
             print(json.dumps(run_reference(args)))
+        return 0
+    if args.serving:
+        print(json.dumps(run_serving(args)))
         return 0
     dist = None
     if world > 1:
