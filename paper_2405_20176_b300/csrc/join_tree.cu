@@ -50,6 +50,7 @@ constexpr int kInit = 256;         // candidates handled lane-per-subspace first
 constexpr int kTBuf = 512;         // event tuples buffered per warp
 constexpr int kTFlushAt = kTBuf - 64;  // a node appends at most 64 tuples
 constexpr int kGroup = 8;          // nodes voted on before any of them appends
+constexpr int kFlushMin = 16;      // tuples that trigger an end-of-step flush
 
 // Depth-first order of the subset tree over the low kLB bits: node L's parent
 // is L with its lowest set bit cleared, and its children add a bit below that.
@@ -100,6 +101,7 @@ struct WarpState {
     float ld[kW][KMAX + 1];         // kNN lists by L; +1 keeps both access patterns
     int lj[kW][KMAX + 1];           // free of bank conflicts
     unsigned long long esum[kW];    // exact quantised eps distance sums
+    unsigned epart[kW];             // this flush's partial sums (<= 512 terms of <= 2^20 + 1)
     float T[kW];                    // current k-th squared distance
     float tc[kW];                   // pass threshold max(T, eps) by L
     int cnt[kW];                    // eps-neighbour counts
@@ -144,7 +146,7 @@ __device__ __noinline__ bool flush_tuples(WarpState<KMAX> &ws, int count, int k)
         const float d2 = __uint_as_float(t.x);
         if (ok && d2 <= ws.eps2[L]) {
             atomicAdd(&ws.cnt[L], 1);
-            atomicAdd(&ws.esum[L], (unsigned long long)dev::eps_quant(d2, ws.escale[L]));
+            atomicAdd(&ws.epart[L], dev::eps_quant(d2, ws.escale[L]));
         }
         unsigned kb = __ballot_sync(dev::kFull, ok && d2 < ws.T[L]);
         while (kb) {
@@ -181,6 +183,9 @@ __device__ __noinline__ bool flush_tuples(WarpState<KMAX> &ws, int count, int k)
             changed = true;
         }
     }
+    __syncwarp();
+    ws.esum[lane] += ws.epart[lane];
+    ws.epart[lane] = 0u;
     __syncwarp();
     return changed;
 }
@@ -361,6 +366,7 @@ __global__ void __launch_bounds__((CW + 1) * 32, 1)
                     ws.lj[L][p] = 0x7fffffff;
                 }
                 ws.esum[L] = 0ull;
+                ws.epart[L] = 0u;
                 ws.cnt[L] = 0;
                 ws.T[L] = (((active >> L) & 1u) && k > 0) ? CUDART_INF_F : -CUDART_INF_F;
             }
@@ -453,8 +459,9 @@ __global__ void __launch_bounds__((CW + 1) * 32, 1)
                 for (int f = 14; f >= kLB; --f)
                     if ((high >> (f - kLB)) & 1u) v[0] = __ffma2_rn(d[f], d[f], v[0]);
                 tree_walk<0, KMAX>(ws, v, d, Tc, tcount, (int)ja, (int)jb, k);
-                // flushing every step keeps the kNN thresholds at most one step stale
-                if (tcount > 0) {
+                // flushing once a batch is waiting keeps the kNN thresholds fresh
+                // without paying a flush per step
+                if (tcount >= kFlushMin) {
                     if (flush_tuples<KMAX>(ws, tcount, k)) load_thresholds<0>(ws, Tc);
                     tcount = 0;
                 }
