@@ -140,7 +140,11 @@ snaps_status snaps_eps_selfjoin(snaps_pop *pop, const uint16_t *masks, int n_mas
                                 void *stream);
 
 /* Both joins and the four outlier metrics per object and subspace (Table 2).
- * k, eps: as above.  precision: SNAPS_FP32 or SNAPS_TC_F16 (same results).
+ * k, eps: as above.  precision: SNAPS_FP32 (plain FP32 joins) or SNAPS_TC_F16
+ *   (the squared-difference x subspace-mask contraction on the tensor cores
+ *   as a conservative FP16 filter, survivors recomputed exactly in FP32: the
+ *   same results).  SNAPS_TC_F16 needs every feature to span at most 1, which
+ *   SNAPS_NORM_MINMAX guarantees (EINVAL otherwise).
  * scores: n_masks x 4 x n float32 raw metrics (rows SNAPS_SCORE_*), or NULL.
  *   Counts and in-degrees are exact integers stored as float.
  * norm:   n_masks x 4 x n float32, each metric mapped onto [0, 1] with
@@ -252,7 +256,8 @@ snaps_status snaps_calibrate_alu(int device, double *evals_per_s);
 #define SNAPS_PHASE_JOIN_LANE 2  /* lane-per-subspace join kernel */
 #define SNAPS_PHASE_NORM 3       /* normalised-metric kernel */
 #define SNAPS_PHASE_TOP 4        /* top-n ranking kernel */
-#define SNAPS_N_PHASES 5
+#define SNAPS_PHASE_JOIN_TC 5    /* tensor-core filtered join kernel */
+#define SNAPS_N_PHASES 6
 
 /* enable != 0: clear the counters and start recording, around every kernel
  * launch of every later call on this context, a pair of CUDA events on the

@@ -34,9 +34,10 @@ SNAPS_FP32 = 0
 SNAPS_TC_F16 = 1
 SNAPS_STATIC_MAX_N = 32768
 SNAPS_STATIC_MAX_MASKS = 32768
-SNAPS_PHASE_INDEX, SNAPS_PHASE_JOIN_TREE, SNAPS_PHASE_JOIN_LANE, SNAPS_PHASE_NORM, SNAPS_PHASE_TOP = range(5)
-SNAPS_N_PHASES = 5
-PHASE_NAMES = ["index", "join_tree", "join_lane", "norm", "top"]
+SNAPS_PHASE_INDEX, SNAPS_PHASE_JOIN_TREE, SNAPS_PHASE_JOIN_LANE, SNAPS_PHASE_NORM, SNAPS_PHASE_TOP, \
+    SNAPS_PHASE_JOIN_TC = range(6)
+SNAPS_N_PHASES = 6
+PHASE_NAMES = ["index", "join_tree", "join_lane", "norm", "top", "join_tc"]
 
 
 class SnapsError(RuntimeError):

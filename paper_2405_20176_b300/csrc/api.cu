@@ -104,6 +104,7 @@ struct snaps_pop {
     snaps_ctx *ctx = nullptr;
     int64_t n = 0, n_pad = 0;
     int f = 0;
+    bool unit_range = false;  // every stored feature spans <= 1 (tensor-core filter allowed)
     float4 *x = nullptr;
     size_t bytes = 0;
     std::atomic<int> inflight{0};
@@ -231,8 +232,9 @@ snaps_status validate(const JobSpec &j)
         FAIL(SNAPS_EINVAL, "top_n must be in 1..min(1024, n) (got %d)", j.top_n);
     if (j.precision != SNAPS_FP32 && j.precision != SNAPS_TC_F16)
         FAIL(SNAPS_EINVAL, "unknown precision %u", j.precision);
-    if (j.precision == SNAPS_TC_F16)
-        FAIL(SNAPS_EINVAL, "precision SNAPS_TC_F16 is not available in this build");
+    if (j.precision == SNAPS_TC_F16 && !p->unit_range)
+        FAIL(SNAPS_EINVAL, "SNAPS_TC_F16 needs every feature to span at most 1 "
+                           "(index the population with SNAPS_NORM_MINMAX)");
     return SNAPS_OK;
 }
 
@@ -241,11 +243,34 @@ snaps_status validate(const JobSpec &j)
 struct Plan {
     std::vector<TreeChunk> chunks;
     std::vector<MaskGroup> groups;
+    std::vector<TcBlock> blocks;
 };
 
 Plan make_plan(const JobSpec &j)
 {
     Plan pl;
+    if (j.precision == SNAPS_TC_F16) {
+        // the tensor-core join takes any subspaces, 64 at a time
+        for (int b = 0; b < j.n_masks; b += kTcBlockWidth) {
+            TcBlock blk{};
+            for (int c = 0; c < kTcBlockWidth; ++c) {
+                const int m = b + c;
+                if (m < j.n_masks) {
+                    blk.mask[c] = j.masks[m];
+                    blk.eps2[c] = !j.want_eps ? -1.f
+                                  : j.eps ? j.eps[m] * j.eps[m]
+                                          : default_eps2(popc16(j.masks[m]));
+                    blk.slot[c] = m;
+                } else {
+                    blk.mask[c] = 0;
+                    blk.eps2[c] = -1.f;
+                    blk.slot[c] = -1;
+                }
+            }
+            pl.blocks.push_back(blk);
+        }
+        return pl;
+    }
     const int f = j.pop->f;
     const int n_chunk = f > kTreeLowBits ? 1 << (f - kTreeLowBits) : 1;
     std::vector<int> first(size_t(n_chunk) * kTreeWidth, -1);
@@ -317,6 +342,7 @@ struct Layout {
     int32_t *eps_count = nullptr;
     TreeChunk *chunks = nullptr;
     MaskGroup *groups = nullptr;
+    TcBlock *blocks = nullptr;
     size_t bytes = 0;
 };
 
@@ -335,6 +361,7 @@ Layout layout_job(const JobSpec &j, const Plan &pl, char *base, bool dev_scores,
     if (j.eps_count) L.eps_count = dev_cnt ? j.eps_count : cv.take<int32_t>(nm * n);
     L.chunks = cv.take<TreeChunk>(pl.chunks.size());
     L.groups = cv.take<MaskGroup>(pl.groups.size());
+    L.blocks = cv.take<TcBlock>(pl.blocks.size());
     L.bytes = cv.off + 256;
     return L;
 }
@@ -413,6 +440,10 @@ snaps_status run_job(snaps_ctx *ctx, const JobSpec &j, cudaStream_t st, Scratch 
         SNAPS_CHECK_CUDA(cudaMemcpyAsync(L.groups, pl.groups.data(),
                                          pl.groups.size() * sizeof(MaskGroup),
                                          cudaMemcpyHostToDevice, st));
+    if (!pl.blocks.empty())
+        SNAPS_CHECK_CUDA(cudaMemcpyAsync(L.blocks, pl.blocks.data(),
+                                         pl.blocks.size() * sizeof(TcBlock),
+                                         cudaMemcpyHostToDevice, st));
     SNAPS_CHECK_CUDA(cudaMemsetAsync(L.scores, 0, nm * 4 * (size_t)n * sizeof(float), st));
     SNAPS_CHECK_CUDA(cudaMemsetAsync(&ctrl->error, 0, sizeof(unsigned), st));
 
@@ -425,6 +456,10 @@ snaps_status run_job(snaps_ctx *ctx, const JobSpec &j, cudaStream_t st, Scratch 
     if (!pl.groups.empty()) {
         TraceScope ts(ctx, SNAPS_PHASE_JOIN_LANE, st);
         SNAPS_TRY(launch_join_lanemask(shape, L.groups, (int)pl.groups.size(), out, ctrl, st));
+    }
+    if (!pl.blocks.empty()) {
+        TraceScope ts(ctx, SNAPS_PHASE_JOIN_TC, st);
+        SNAPS_TRY(launch_join_tc(shape, L.blocks, (int)pl.blocks.size(), out, ctrl, st));
     }
     if (j.norm) {
         TraceScope ts(ctx, SNAPS_PHASE_NORM, st);
@@ -682,7 +717,9 @@ snaps_status snaps_index(snaps_ctx *ctx, const float *feat, int64_t n, int f, ui
     }
     if (s != SNAPS_OK) return fail(s);
     unsigned hbad = 0;
+    ColStats hstats[SNAPS_MAX_FEATURES];
     if (cudaMemcpyAsync(&hbad, bad, sizeof(unsigned), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaMemcpyAsync(hstats, stats, sizeof(ColStats) * f, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
         cudaStreamSynchronize(st) != cudaSuccess) {
         set_error("normalisation failed: %s", cudaGetErrorString(cudaGetLastError()));
         return fail(SNAPS_ECUDA);
@@ -692,6 +729,10 @@ snaps_status snaps_index(snaps_ctx *ctx, const float *feat, int64_t n, int f, ui
         return fail(SNAPS_EINVAL);
     }
     ctx_free(ctx, stage, (dev_in ? 0 : in_bytes) + aux);
+    p->unit_range = true;
+    if (!(flags & SNAPS_NORM_MINMAX))
+        for (int c = 0; c < f; ++c)
+            if (!(hstats[c].hi - hstats[c].lo <= 1.0)) p->unit_range = false;
     ctx->n_pops.fetch_add(1);
     *out = p;
     return SNAPS_OK;

@@ -28,6 +28,15 @@ struct TreeChunk {
     int32_t slot[kTreeWidth];
 };
 
+// Up to 64 subspaces of any kind, as scheduled for the tensor-core join.  An
+// unused entry has mask 0.
+constexpr int kTcBlockWidth = 64;
+struct TcBlock {
+    uint32_t mask[kTcBlockWidth];
+    float eps2[kTcBlockWidth];
+    int32_t slot[kTcBlockWidth];
+};
+
 // Outputs of a join.  `scores` is always present: n_slots x 4 x n floats; the
 // join writes rows 0 (eps count), 1 (eps mean distance) and 3 (kNN mean
 // distance) and adds 1 to row 2 (in-degree) of every kNN list member, so row 2
@@ -49,6 +58,11 @@ struct JoinShape {
 // Launch the lane-per-subspace join over `n_groups` groups (device array).
 snaps_status launch_join_lanemask(const JoinShape &s, const MaskGroup *groups, int n_groups,
                                   const JoinOut &o, DeviceControl *ctrl, cudaStream_t st);
+
+// Launch the tensor-core filtered join over `n_blocks` blocks (device array).
+// Requires every feature of the population to span at most 1.
+snaps_status launch_join_tc(const JoinShape &s, const TcBlock *blocks, int n_blocks,
+                            const JoinOut &o, DeviceControl *ctrl, cudaStream_t st);
 
 // Launch the subspace-batched tree join over `n_chunks` chunks (device array).
 snaps_status launch_join_tree(const JoinShape &s, const TreeChunk *chunks, int n_chunks,

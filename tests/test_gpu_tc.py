@@ -1,0 +1,113 @@
+"""The tensor-core filtered join (SNAPS_TC_F16) returns exactly the plain FP32
+path's results -- same canonical distances, exact decisions on every
+survivor of the FP16 filter -- across block fills, subspace mixes, k, ragged
+N and extreme radii (every candidate passing stresses the event buffers),
+and matches the FP64 oracle under the same rules."""
+import numpy as np
+import pytest
+
+import oracle
+import paper_2405_20176_b300 as snaps
+import snaps_inputs
+from parity import check_eps, check_knn, check_top
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = snaps.snaps_create(0)
+    yield c
+    snaps.snaps_destroy(c)
+
+
+def run_both(ctx, x, masks, k, eps=None, top_n=100):
+    masks = np.asarray(masks, dtype=np.uint16)
+    pop = snaps.snaps_index(ctx, x)
+    try:
+        n = x.shape[0]
+        top_n = min(top_n, n)
+        out = {}
+        for prec in (snaps.SNAPS_FP32, snaps.SNAPS_TC_F16):
+            sc = np.zeros((masks.size, 4, n), dtype=np.float32)
+            nz = np.zeros_like(sc)
+            tp = np.zeros((masks.size, 4, top_n), dtype=np.int32)
+            snaps.snaps_scores(pop, masks, k, eps=eps, precision=prec, scores=sc, norm=nz,
+                               top=tp, top_n=top_n)
+            out[prec] = (sc, nz, tp)
+        return out
+    finally:
+        snaps.snaps_release(pop)
+
+
+def assert_same(out):
+    a, b = out[snaps.SNAPS_FP32], out[snaps.SNAPS_TC_F16]
+    for u, v, name in zip(a, b, ("scores", "norm", "top")):
+        np.testing.assert_array_equal(v, u, err_msg=name)
+
+
+@pytest.mark.parametrize("n,seed", [(2000, 0), (257, 1), (513, 2), (1100, 3)])
+def test_tc_equals_plain_on_mixed_subspaces(ctx, n, seed):
+    allm = snaps_inputs.all_masks()
+    masks = np.concatenate([allm[(allm >> 5) == 0b1111111111], snaps_inputs.mask_sample(50, seed),
+                            [0b11, (1 << 15) - 1]])
+    assert_same(run_both(ctx, snaps_inputs.population(n, seed), masks, 10))
+
+
+@pytest.mark.parametrize("k", [1, 5, 16, 17, 32])
+def test_tc_k_range(ctx, k):
+    masks = snaps_inputs.mask_sample(70, 10 + k)
+    assert_same(run_both(ctx, snaps_inputs.population(700, 20 + k), masks, k))
+
+
+def test_tc_extreme_radii_and_large_k(ctx):
+    # eps beyond the diameter: every candidate passes the filter and the kNN
+    # buffers overflow mid-tile; tiny eps: only duplicates
+    x = snaps_inputs.population(900, 31)
+    x[5] = x[17]
+    masks = np.array([0b11, 0b111, 0b1010101010101, (1 << 15) - 1, 0b110000000000011], dtype=np.uint16)
+    assert_same(run_both(ctx, x, masks, 32, eps=[4.0, 4.0, 4.0, 4.0, 4.0]))
+    assert_same(run_both(ctx, x, masks, 10, eps=[0.0, 1e-9, 0.0, 1e-9, 0.0]))
+
+
+def test_tc_matches_oracle(ctx):
+    x = snaps_inputs.population(1500, 41)
+    masks = snaps_inputs.mask_sample(12, 41)
+    pop = snaps.snaps_index(ctx, x)
+    try:
+        n, m = 1500, masks.size
+        idx = torch.empty((m, n, 10), dtype=torch.int32, device="cuda")
+        dist = torch.empty((m, n, 10), device="cuda")
+        sc = np.zeros((m, 4, n), dtype=np.float32)
+        tp = np.zeros((m, 4, 100), dtype=np.int32)
+        snaps.snaps_scores(pop, masks, 10, precision=snaps.SNAPS_TC_F16, scores=sc, top=tp, top_n=100)
+        snaps.snaps_knn_selfjoin(pop, masks, 10, idx, dist)
+        torch.cuda.synchronize()
+    finally:
+        snaps.snaps_release(pop)
+    xn = oracle.normalise(x)
+    x64 = xn.astype(np.float64)
+    for s, mask in enumerate(masks):
+        r = oracle.subspace(xn, int(mask), 10)
+        check_knn(x64, int(mask), idx[s].cpu().numpy(), dist[s].cpu().numpy(),
+                  r.join.knn_idx, r.join.knn_d2)
+        e2 = oracle.default_eps2(int(mask))
+        lo = oracle.join(x64, int(mask), 0, e2 * (1 - 2e-6)).eps_count
+        hi = oracle.join(x64, int(mask), 0, e2 * (1 + 2e-6)).eps_count
+        check_eps(sc[s][0].astype(np.int64), sc[s][1], oracle.join(x64, int(mask), 0, e2), lo, hi)
+        np.testing.assert_allclose(sc[s][3], r.scores[oracle.KNN_MEAN], rtol=1e-5)
+        for mm in (oracle.EPS_MEAN, oracle.KNN_MEAN):
+            check_top(tp[s][mm], r.scores, r.top[mm], mm)
+
+
+def test_tc_rejects_wide_features(ctx):
+    x = (snaps_inputs.population(300, 3) * 10).astype(np.float32)
+    pop = snaps.snaps_index(ctx, x, flags=0)
+    try:
+        with pytest.raises(snaps.SnapsError) as ei:
+            snaps.snaps_scores(pop, [0b11], 5, precision=snaps.SNAPS_TC_F16,
+                               scores=np.zeros((1, 4, 300), np.float32))
+        assert ei.value.status == snaps.SNAPS_EINVAL
+    finally:
+        snaps.snaps_release(pop)
