@@ -105,6 +105,11 @@ snaps_status snaps_mem_info(const snaps_ctx *ctx, size_t *held, size_t *budget);
  *   Without SNAPS_NORM_MINMAX the values are used unchanged.
  * Requirements: n >= 2, 1 <= f <= 15, every value finite (NaN allowed only
  *   with SNAPS_NAN_TO_MEAN).
+ * Requirements: n <= 2^24 as well.
+ * The stored rows are kept in cell order (sorted by a Morton key over the
+ * features) so that neighbouring rows are near in feature space; every output
+ * of the joins and scores is still indexed by the caller's row order, and the
+ * results do not depend on the stored order.
  * The population lives in device memory until snaps_release.
  * Errors: EINVAL, ENOMEM (over budget), ECUDA. */
 snaps_status snaps_index(snaps_ctx *ctx, const float *feat, int64_t n, int f,

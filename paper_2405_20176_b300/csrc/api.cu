@@ -3,6 +3,8 @@
 
 #include <cuda_runtime.h>
 
+#include <cub/device/device_radix_sort.cuh>
+
 #include <algorithm>
 #include <atomic>
 #include <chrono>
@@ -91,6 +93,12 @@ struct snaps_ctx {
     std::vector<Slot *> slots;
     bool stopping = false;
     std::atomic<int> n_pops{0};
+
+    // kernels one radix sort launches, by n (counted from a stream capture
+    // that records the sort without running it; only while tracing)
+    std::mutex cap_mu;
+    cudaStream_t cap_stream = nullptr;
+    std::unordered_map<int64_t, int> sort_kernels;
 
     // tracing
     std::mutex tr_mu;
@@ -644,6 +652,7 @@ snaps_status snaps_destroy(snaps_ctx *ctx)
         cudaEventDestroy(m.b);
     }
     for (cudaEvent_t e : ctx->spare) cudaEventDestroy(e);
+    if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
     ctx_free(ctx, ctx->scratch.ptr, ctx->scratch.cap);
     ctx_free(ctx, ctx->ctrl, sizeof(DeviceControl));
     delete ctx;
@@ -660,6 +669,56 @@ snaps_status snaps_mem_info(const snaps_ctx *ctx, size_t *held, size_t *budget)
     if (budget) *budget = c->budget;
     return SNAPS_OK;
 }
+
+namespace {
+
+// How many kernels cub::DeviceRadixSort::SortPairs launches for n pairs of
+// 30-bit keys: the sort is recorded by a stream capture on a private stream
+// (recording runs nothing) and its kernel nodes are counted; cached per n.
+// Used only to report launch counts while tracing.
+snaps_status sort_kernel_count(snaps_ctx *ctx, int64_t n, void *tmp, size_t tmp_bytes,
+                               const uint32_t *k_in, uint32_t *k_out, const int32_t *i_in,
+                               int32_t *i_out, int *count)
+{
+    std::lock_guard<std::mutex> g(ctx->cap_mu);
+    auto it = ctx->sort_kernels.find(n);
+    if (it != ctx->sort_kernels.end()) {
+        *count = it->second;
+        return SNAPS_OK;
+    }
+    if (!ctx->cap_stream)
+        SNAPS_CHECK_CUDA(cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
+    SNAPS_CHECK_CUDA(cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal));
+    const cudaError_t ce = cub::DeviceRadixSort::SortPairs(tmp, tmp_bytes, k_in, k_out, i_in, i_out, (int)n, 0,
+                                                           30, ctx->cap_stream);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ee = cudaStreamEndCapture(ctx->cap_stream, &graph);
+    if (ce != cudaSuccess || ee != cudaSuccess || !graph) {
+        if (graph) cudaGraphDestroy(graph);
+        set_error("recording the cell sort failed: %s", cudaGetErrorString(ce != cudaSuccess ? ce : ee));
+        return SNAPS_ECUDA;
+    }
+    size_t nn = 0;
+    cudaError_t ge = cudaGraphGetNodes(graph, nullptr, &nn);
+    std::vector<cudaGraphNode_t> nodes(nn);
+    if (ge == cudaSuccess && nn) ge = cudaGraphGetNodes(graph, nodes.data(), &nn);
+    int kernels = 0;
+    for (size_t q = 0; ge == cudaSuccess && q < nn; ++q) {
+        cudaGraphNodeType t;
+        ge = cudaGraphNodeGetType(nodes[q], &t);
+        if (ge == cudaSuccess && t == cudaGraphNodeTypeKernel) ++kernels;
+    }
+    cudaGraphDestroy(graph);
+    if (ge != cudaSuccess) {
+        set_error("reading the recorded cell sort failed: %s", cudaGetErrorString(ge));
+        return SNAPS_ECUDA;
+    }
+    ctx->sort_kernels[n] = kernels;
+    *count = kernels;
+    return SNAPS_OK;
+}
+
+}  // namespace
 
 snaps_status snaps_index(snaps_ctx *ctx, const float *feat, int64_t n, int f, uint32_t flags,
                          void *stream, snaps_pop **out)
@@ -729,6 +788,56 @@ snaps_status snaps_index(snaps_ctx *ctx, const float *feat, int64_t n, int f, ui
         return fail(SNAPS_EINVAL);
     }
     ctx_free(ctx, stage, (dev_in ? 0 : in_bytes) + aux);
+    // ---- sort-by-cell index: rows reordered by their 15-feature cell key, so
+    // a tile of consecutive rows is a spatial neighbourhood.  Stored rows keep
+    // their original index in float 15.
+    {
+        size_t cub_bytes = 0;
+        cub::DeviceRadixSort::SortPairs(nullptr, cub_bytes, (const uint32_t *)nullptr, (uint32_t *)nullptr,
+                                        (const int32_t *)nullptr, (int32_t *)nullptr, (int)n, 0, 30, st);
+        const size_t rows_bytes = p->bytes;
+        const size_t arr = ((size_t)n * 4 + 255) & ~size_t(255);
+        const size_t sort_bytes = rows_bytes + 4 * arr + cub_bytes + 256;
+        void *sb2 = nullptr;
+        s = ctx_alloc(ctx, sort_bytes, &sb2);
+        if (s != SNAPS_OK) {
+            ctx_free(ctx, p->x, p->bytes);
+            delete p;
+            return s;
+        }
+        char *b2 = (char *)sb2;
+        float4 *rows = (float4 *)b2;
+        uint32_t *k_in = (uint32_t *)(b2 + rows_bytes);
+        uint32_t *k_out = (uint32_t *)(b2 + rows_bytes + arr);
+        int32_t *i_in = (int32_t *)(b2 + rows_bytes + 2 * arr);
+        int32_t *i_out = (int32_t *)(b2 + rows_bytes + 3 * arr);
+        void *tmp = b2 + rows_bytes + 4 * arr;
+        int sort_kernels = 0;
+        snaps_status ss = SNAPS_OK;
+        bool tracing = false;
+        {
+            std::lock_guard<std::mutex> g(ctx->tr_mu);
+            tracing = ctx->tracing;
+        }
+        if (tracing) ss = sort_kernel_count(ctx, n, tmp, cub_bytes, k_in, k_out, i_in, i_out, &sort_kernels);
+        cudaError_t ce = cudaSuccess;
+        if (ss == SNAPS_OK) {
+            TraceScope ts(ctx, SNAPS_PHASE_INDEX, st, 2 + sort_kernels);
+            ce = cudaMemcpyAsync(rows, p->x, rows_bytes, cudaMemcpyDeviceToDevice, st);
+            if (ce == cudaSuccess) ss = launch_cell_keys(rows, n, k_in, i_in, st);
+            if (ss == SNAPS_OK && ce == cudaSuccess)
+                ce = cub::DeviceRadixSort::SortPairs(tmp, cub_bytes, k_in, k_out, i_in, i_out, (int)n, 0, 30, st);
+            if (ss == SNAPS_OK && ce == cudaSuccess) ss = launch_gather_rows(rows, i_out, n, p->n_pad, p->x, st);
+        }
+        if (ss == SNAPS_OK && ce == cudaSuccess) ce = cudaStreamSynchronize(st);
+        ctx_free(ctx, sb2, sort_bytes);
+        if (ss != SNAPS_OK || ce != cudaSuccess) {
+            if (ce != cudaSuccess) set_error("sort-by-cell index failed: %s", cudaGetErrorString(ce));
+            ctx_free(ctx, p->x, p->bytes);
+            delete p;
+            return ss != SNAPS_OK ? ss : SNAPS_ECUDA;
+        }
+    }
     p->unit_range = true;
     if (!(flags & SNAPS_NORM_MINMAX))
         for (int c = 0; c < f; ++c)

@@ -80,6 +80,7 @@ __global__ void __launch_bounds__(kLmWarps * 32)
 #pragma unroll
         for (int f = 0; f < 15; ++f) wgt[f] = ((mask >> f) & 1u) ? 1.f : 0.f;
         float xq[16];
+        int orig_i = 0;  // the query's original index (float 15 of its stored row)
         if (valid) {
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
@@ -89,6 +90,7 @@ __global__ void __launch_bounds__(kLmWarps * 32)
                 xq[4 * q + 2] = v.z;
                 xq[4 * q + 3] = v.w;
             }
+            orig_i = __float_as_int(xq[15]);
         }
         float T = (active && k > 0) ? CUDART_INF_F : -CUDART_INF_F;
         for (int p = 0; p < KMAX; ++p) {
@@ -142,21 +144,23 @@ __global__ void __launch_bounds__(kLmWarps * 32)
                         ++cnt;
                         qsum += dev::eps_quant(acc, escale);
                     }
-                    if (acc < T) {
-                        // sorted insertion into this lane's list (entries strided by 32)
+                    const int oc = __float_as_int(xc[15]);  // candidate's original index
+                    if (acc < T || (acc == T && k > 0 && oc < sm.lj[warp][k - 1][lane])) {
+                        // sorted insertion into this lane's list (entries strided by 32),
+                        // by (distance, original index)
                         float *ld = &sm.ld[warp][0][lane];
                         int *lj = &sm.lj[warp][0][lane];
                         int p = k - 1;
                         while (p > 0) {
                             const float pd = ld[(p - 1) * 32];
                             const int pj = lj[(p - 1) * 32];
-                            if (!(acc < pd || (acc == pd && (int)j < pj))) break;
+                            if (!(acc < pd || (acc == pd && oc < pj))) break;
                             ld[p * 32] = pd;
                             lj[p * 32] = pj;
                             --p;
                         }
                         ld[p * 32] = acc;
-                        lj[p * 32] = (int)j;
+                        lj[p * 32] = oc;
                         T = ld[(k - 1) * 32];
                     }
                 }
@@ -171,9 +175,9 @@ __global__ void __launch_bounds__(kLmWarps * 32)
         if (active) {
             const int slot = grp.slot[lane];
             float *sc = o.scores + (int64_t)slot * 4 * n;
-            sc[i] = (float)cnt;
-            sc[n + i] = dev::eps_mean(qsum, cnt, escale);
-            if (o.eps_count) o.eps_count[(int64_t)slot * n + i] = cnt;
+            sc[orig_i] = (float)cnt;
+            sc[n + orig_i] = dev::eps_mean(qsum, cnt, escale);
+            if (o.eps_count) o.eps_count[(int64_t)slot * n + orig_i] = cnt;
             if (k > 0) {
                 float msum = 0.f;
                 for (int p = 0; p < k; ++p) {
@@ -181,10 +185,10 @@ __global__ void __launch_bounds__(kLmWarps * 32)
                     const int j = sm.lj[warp][p][lane];
                     msum += d;
                     if (j >= 0 && j < n) atomicAdd(&sc[2 * n + j], 1.f);
-                    if (o.knn_idx) o.knn_idx[((int64_t)slot * n + i) * k + p] = j;
-                    if (o.knn_dist) o.knn_dist[((int64_t)slot * n + i) * k + p] = d;
+                    if (o.knn_idx) o.knn_idx[((int64_t)slot * n + orig_i) * k + p] = j;
+                    if (o.knn_dist) o.knn_dist[((int64_t)slot * n + orig_i) * k + p] = d;
                 }
-                sc[3 * n + i] = msum / (float)k;
+                sc[3 * n + orig_i] = msum / (float)k;
             }
         }
     }

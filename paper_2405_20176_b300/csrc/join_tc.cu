@@ -292,6 +292,7 @@ __global__ void __launch_bounds__(kTcWarps * 32)
                 xq[4 * q + 2] = v.z;
                 xq[4 * q + 3] = v.w;
             }
+            const int orig_i = __float_as_int(xq[15]);  // the query's original index
             // stream the tiles: prologue
             if (tid == 0) {
                 for (int t = 0; t < kTcStages && t < n_tiles; ++t) {
@@ -343,7 +344,9 @@ __global__ void __launch_bounds__(kTcWarps * 32)
                                 ++cnt;
                                 qs += dev::eps_quant(acc, sc);
                             }
-                            if (act && acc < T) T = dev::private_insert(sm.ld[c], sm.lj[c], k, acc, r);
+                            const int oc = __float_as_int(tile[3 * kTile + r].w);
+                            if (act && (acc < T || (acc == T && oc < sm.lj[c][k - 1])))
+                                T = dev::private_insert(sm.ld[c], sm.lj[c], k, acc, oc);
                         }
                         sm.T[c] = T;
                         sm.cnt[c] = cnt;
@@ -435,7 +438,9 @@ __global__ void __launch_bounds__(kTcWarps * 32)
                     uint2 *buf = sm.tbuf[warp];
                     int count = sm.tcount[warp];
                     const int ra = 32 * warp + (int)lane, rb = ra + 128;
-                    const int ja = (int)(base + ra), jb = (int)(base + rb);
+                    // original indices of this lane's two candidates (float 15 of the rows)
+                    const int ja = __float_as_int(tile[3 * kTile + ra].w);
+                    const int jb = __float_as_int(tile[3 * kTile + rb].w);
 #pragma unroll 1
                     for (int c0 = 0; c0 < kNB; c0 += 32) {
                         uint32_t r0[32], r1[32];
@@ -533,9 +538,9 @@ __global__ void __launch_bounds__(kTcWarps * 32)
                 const int slot = sm.slot[c];
                 float *sc = o.scores + (int64_t)slot * 4 * n;
                 const int cnt = sm.cnt[c];
-                sc[i] = (float)cnt;
-                sc[n + i] = dev::eps_mean(sm.esum[c], cnt, sm.escale[c]);
-                if (o.eps_count) o.eps_count[(int64_t)slot * n + i] = cnt;
+                sc[orig_i] = (float)cnt;
+                sc[n + orig_i] = dev::eps_mean(sm.esum[c], cnt, sm.escale[c]);
+                if (o.eps_count) o.eps_count[(int64_t)slot * n + orig_i] = cnt;
                 if (k > 0) {
                     float msum = 0.f;
                     for (int p = 0; p < k; ++p) {
@@ -543,10 +548,10 @@ __global__ void __launch_bounds__(kTcWarps * 32)
                         const int j = sm.lj[c][p];
                         msum += dd;
                         if (j >= 0 && j < n) atomicAdd(&sc[2 * n + j], 1.f);
-                        if (o.knn_idx) o.knn_idx[((int64_t)slot * n + i) * k + p] = j;
-                        if (o.knn_dist) o.knn_dist[((int64_t)slot * n + i) * k + p] = dd;
+                        if (o.knn_idx) o.knn_idx[((int64_t)slot * n + orig_i) * k + p] = j;
+                        if (o.knn_dist) o.knn_dist[((int64_t)slot * n + orig_i) * k + p] = dd;
                     }
-                    sc[3 * n + i] = msum / (float)k;
+                    sc[3 * n + orig_i] = msum / (float)k;
                 }
             }
             __syncthreads();

@@ -17,20 +17,26 @@
 // max(current k-th distance, eps); it votes on 8 subspaces before branching,
 // so their latencies overlap.  Only the lanes that passed then append a
 // (squared distance, subspace, candidate) tuple to the warp's buffer in
-// shared memory (a ballot prefix sum gives each its slot).  At the end of
-// every step (or when the buffer fills), a flush processes 32 tuples at a
-// time with every lane busy: eps counts and exact fixed-point distance sums
-// by shared-memory atomics, then warp-cooperative insertion of the few
-// tuples still below their subspace's k-th distance into its sorted list.
+// shared memory (a ballot prefix sum gives each its slot).  Once enough
+// tuples wait (or the buffer fills), a flush processes 32 tuples at a time
+// with every lane busy: eps counts and exact fixed-point distance sums by
+// shared-memory atomics, then kNN insertions, lanes holding different
+// subspaces inserting into their lists at the same time.
+//
+// Rows are stored in cell order (sorted by a 15-feature Morton key when the
+// population is indexed) and carry their original index in float 15; lists,
+// ties and outputs use original indices, so results do not depend on the
+// order.  A work item's candidate stream starts at the tile holding its
+// queries and wraps around: its first 256 candidates are the queries' own
+// neighbourhood, handled lane-per-subspace (each lane folds its own subspace
+// and keeps a private list), so the lists start full and the thresholds tight
+// instead of sending every early candidate to the flush.
 //
 // A producer warp streams candidate tiles with 1-D bulk copies (TMA) into a
 // ring of stages guarded by full / empty mbarriers, so consumer warps move at
 // their own pace; it also hands out work items (chunk x query block) from an
-// atomic counter, tagging every stage with the work item it belongs to.
-//
-// The first 256 candidates are handled lane-per-subspace (each lane folds its
-// own subspace and keeps a private list) so the lists start full and the
-// thresholds tight instead of sending every early candidate to the handler.
+// atomic counter, tagging every stage with the work item it belongs to.  Two
+// CTAs share an SM (k <= 16), each with its own stream and work items.
 
 #include <math_constants.h>
 
@@ -109,6 +115,12 @@ struct WarpState {
     float escale[kW];               // 2^20 / eps
 };
 
+// Two CTAs share an SM when their consumer warps fit (CW <= 6 with k <= 16):
+// each CTA streams its own tiles, so one CTA's event-heavy stretch of the
+// candidate stream overlaps the other's event-free stretch.
+template <int CW>
+constexpr int kCtasPerSm = CW <= 6 ? 2 : 1;
+
 template <int KMAX, int CW>
 struct TreeSmem {
     float4 tile[kStages][kTile * 4];
@@ -126,16 +138,26 @@ __device__ __forceinline__ float eps_up(float e2) {
     return e2 >= 0.f ? __uint_as_float(__float_as_uint(e2) + 1u) : -CUDART_INF_F;
 }
 
-// Process the buffered event tuples: eps counts and exact distance sums for
-// the tuples within eps (all lanes, shared-memory atomics), then the tuples
-// still below their subspace's current k-th distance are inserted one by one
-// (warp-cooperative sorted insertion).  Tuples of one subspace sit in the
-// buffer in ascending candidate order.  Returns true when a kNN list changed.
+__device__ __forceinline__ float next_up(float t) {
+    // d2 < next_up(t)  <=>  d2 <= t for finite t >= 0 (a tie with the k-th
+    // distance may still enter through a smaller original index); +-inf stay as they are
+    return (t >= 0.f && t < CUDART_INF_F) ? __uint_as_float(__float_as_uint(t) + 1u) : t;
+}
+
+// Process the buffered event tuples, 32 at a time with every lane busy: eps
+// counts and exact distance sums for the tuples within eps (shared-memory
+// atomics), then the tuples at or below their subspace's current k-th
+// distance enter its sorted list.  Lanes holding tuples of different
+// subspaces insert at the same time (each into its own list); lanes that share
+// a subspace take turns in lane order.  The k smallest (distance, original
+// index) pairs do not depend on the order of insertion.  Returns true when a
+// kNN list changed.
 template <int KMAX>
 __device__ __noinline__ bool flush_tuples(WarpState<KMAX> &ws, int count, int k)
 {
     const unsigned lane = dev::lane_id();
-    bool changed = false;
+    const unsigned lower = (1u << lane) - 1u;
+    unsigned changed = 0;  // bit L: list L changed
     __syncwarp();
     for (int b = 0; b < count; b += 32) {
         const int idx = b + (int)lane;
@@ -148,46 +170,44 @@ __device__ __noinline__ bool flush_tuples(WarpState<KMAX> &ws, int count, int k)
             atomicAdd(&ws.cnt[L], 1);
             atomicAdd(&ws.epart[L], dev::eps_quant(d2, ws.escale[L]));
         }
-        unsigned kb = __ballot_sync(dev::kFull, ok && d2 < ws.T[L]);
-        while (kb) {
-            const int src = __ffs(kb) - 1;
-            kb &= kb - 1;
-            const int Ls = __shfl_sync(dev::kFull, L, src);
-            const float ds = __shfl_sync(dev::kFull, d2, src);
-            const int js = __shfl_sync(dev::kFull, j, src);
-            float T = ws.T[Ls];
-            if (!(ds < T)) continue;
-            float my_d = lane < (unsigned)k ? ws.ld[Ls][lane] : CUDART_INF_F;
-            int my_j = lane < (unsigned)k ? ws.lj[Ls][lane] : 0x7fffffff;
-            const bool before = lane < (unsigned)k && (my_d < ds || (my_d == ds && my_j < js));
-            const int pos = __popc(__ballot_sync(dev::kFull, before));
-            const float up_d = __shfl_up_sync(dev::kFull, my_d, 1);
-            const int up_j = __shfl_up_sync(dev::kFull, my_j, 1);
-            if (lane == (unsigned)pos) {
-                my_d = ds;
-                my_j = js;
-            } else if (lane > (unsigned)pos && lane < (unsigned)k) {
-                my_d = up_d;
-                my_j = up_j;
+        const bool want = ok && d2 <= ws.T[L];  // T is -inf for inactive subspaces and k = 0
+        unsigned pend = __ballot_sync(dev::kFull, want);
+        if (!pend) continue;
+        // rank among the pending lanes of the same subspace
+        const unsigned same = __match_any_sync(dev::kFull, want ? L : 32 + (int)lane);
+        const int rank = __popc(same & pend & lower);
+        for (int r = 0; pend; ++r) {
+            if (want && rank == r) {
+                float *ld = ws.ld[L];
+                int *lj = ws.lj[L];
+                const float T = ld[k - 1];
+                if (d2 < T || (d2 == T && j < lj[k - 1])) {
+                    int p = k - 1;
+                    while (p > 0) {
+                        const float pd = ld[p - 1];
+                        const int pj = lj[p - 1];
+                        if (!(d2 < pd || (d2 == pd && j < pj))) break;
+                        ld[p] = pd;
+                        lj[p] = pj;
+                        --p;
+                    }
+                    ld[p] = d2;
+                    lj[p] = j;
+                    ws.T[L] = ld[k - 1];
+                }
             }
-            T = __shfl_sync(dev::kFull, my_d, k - 1);
-            if (lane < (unsigned)k) {
-                ws.ld[Ls][lane] = my_d;
-                ws.lj[Ls][lane] = my_j;
-            }
-            if (lane == 0) {
-                ws.T[Ls] = T;
-                ws.tc[Ls] = fmaxf(T, eps_up(ws.eps2[Ls]));
-            }
+            const bool mine = want && rank == r;
+            pend &= ~__ballot_sync(dev::kFull, mine);
+            changed |= __reduce_or_sync(dev::kFull, mine ? (1u << L) : 0u);
             __syncwarp();
-            changed = true;
         }
     }
     __syncwarp();
     ws.esum[lane] += ws.epart[lane];
     ws.epart[lane] = 0u;
+    if ((changed >> lane) & 1u) ws.tc[lane] = fmaxf(next_up(ws.T[lane]), eps_up(ws.eps2[lane]));
     __syncwarp();
-    return changed;
+    return changed != 0u;
 }
 
 // Pass thresholds into registers, by DFS position.
@@ -262,7 +282,7 @@ __device__ __forceinline__ void tree_walk(WarpState<KMAX> &ws, float2 (&v)[kW],
 }
 
 template <int KMAX, int CW>
-__global__ void __launch_bounds__((CW + 1) * 32, 1)
+__global__ void __launch_bounds__((CW + 1) * 32, kCtasPerSm<CW>)
     join_tree_kernel(JoinShape s, const TreeChunk *__restrict__ chunks, int n_chunks, JoinOut o,
                      DeviceControl *ctrl)
 {
@@ -294,6 +314,9 @@ __global__ void __launch_bounds__((CW + 1) * 32, 1)
             const long long w = (long long)atomicAdd(&ctrl->next_work, 1ull);
             const bool end = w >= total;
             const int count = end ? 1 : n_tiles;
+            // the stream starts at the query block's own tile: in cell order that
+            // tile is the queries' neighbourhood, which tightens the thresholds early
+            const int t0 = end ? 0 : (int)(((w % n_qb) * CW) / kTile);
             for (int t = 0; t < count; ++t, ++g) {
                 const uint32_t st = g % kStages;
                 if (g >= (uint32_t)kStages &&
@@ -301,12 +324,13 @@ __global__ void __launch_bounds__((CW + 1) * 32, 1)
                     atomicOr(&ctrl->error, kErrTimeout);
                     return;
                 }
+                const int phys = (t0 + t) % n_tiles;
                 sm.stage_work[st] = end ? -1 : w;
                 sm.stage_tile[st] = t;
                 if (end)
                     dev::mbar_arrive(&sm.full[st]);
                 else
-                    dev::bulk_load(sm.tile[st], x + (int64_t)t * kTile * 4, kTile * 64, &sm.full[st]);
+                    dev::bulk_load(sm.tile[st], x + (int64_t)phys * kTile * 4, kTile * 64, &sm.full[st]);
             }
             if (end) return;
         }
@@ -319,6 +343,7 @@ __global__ void __launch_bounds__((CW + 1) * 32, 1)
     float2 nxq[15];
     float xq[16];
     int64_t i = 0;
+    int orig_i = 0;  // the query's original index (float 15 of its stored row)
     bool valid = false;
     uint32_t active = 0, high = 0;
     int tcount = 0;  // buffered event tuples (warp-uniform)
@@ -332,6 +357,7 @@ __global__ void __launch_bounds__((CW + 1) * 32, 1)
         const long long w = sm.stage_work[st];
         if (w < 0) return;
         const int t = sm.stage_tile[st];
+        const int phys = (int)((((w % n_qb) * CW) / kTile + t) % n_tiles);
         const float4 *tile = sm.tile[st];
 
         if (t == 0) {
@@ -350,6 +376,7 @@ __global__ void __launch_bounds__((CW + 1) * 32, 1)
                     xq[4 * q + 2] = v.z;
                     xq[4 * q + 3] = v.w;
                 }
+                orig_i = __float_as_int(xq[15]);
             } else {
 #pragma unroll
                 for (int f = 0; f < 16; ++f) xq[f] = 0.f;
@@ -385,9 +412,10 @@ __global__ void __launch_bounds__((CW + 1) * 32, 1)
                 float wgt[15];
 #pragma unroll
                 for (int f = 0; f < 15; ++f) wgt[f] = ((mask >> f) & 1u) ? 1.f : 0.f;
-                const int c_end = (int)std::min<int64_t>(kInit, n);
+                const int64_t tbase = (int64_t)phys * kTile;
+                const int c_end = (int)std::min<int64_t>(kInit, n - tbase);
                 for (int c = 0; c < c_end; ++c) {
-                    if ((int64_t)c == i) continue;
+                    if (tbase + c == i) continue;
                     float xc[16];
 #pragma unroll
                     for (int q = 0; q < 4; ++q) {
@@ -407,7 +435,9 @@ __global__ void __launch_bounds__((CW + 1) * 32, 1)
                         ++cnt;
                         qs += dev::eps_quant(acc, sc);
                     }
-                    if (mine && acc < T) T = dev::private_insert(ws.ld[L], ws.lj[L], k, acc, c);
+                    const int oc = __float_as_int(xc[15]);
+                    if (mine && (acc < T || (acc == T && oc < ws.lj[L][k - 1])))
+                        T = dev::private_insert(ws.ld[L], ws.lj[L], k, acc, oc);
                 }
                 ws.T[L] = T;
                 ws.cnt[L] = cnt;
@@ -415,7 +445,7 @@ __global__ void __launch_bounds__((CW + 1) * 32, 1)
             }
             {
                 const uint32_t L = lane;
-                ws.tc[L] = ((active >> L) & 1u) ? fmaxf(ws.T[L], eps_up(ws.eps2[L])) : -CUDART_INF_F;
+                ws.tc[L] = ((active >> L) & 1u) ? fmaxf(next_up(ws.T[L]), eps_up(ws.eps2[L])) : -CUDART_INF_F;
             }
             __syncwarp();
             load_thresholds<0>(ws, Tc);
@@ -423,10 +453,11 @@ __global__ void __launch_bounds__((CW + 1) * 32, 1)
 
         // ---- main loop over the tile -----------------------------------------------------
         if (valid) {
-            const int64_t base = (int64_t)t * kTile;
+            const int64_t base = (int64_t)phys * kTile;
             for (int c = (t == 0 ? kInit : 0); c < kTile; c += 64) {
                 const int64_t ja = base + c + lane;
                 const int64_t jb = ja + 32;
+                int oa = 0, ob = 0;  // original indices of the two candidates
                 float2 d[15];
                 {
                     float xa[16], xb[16];
@@ -439,6 +470,8 @@ __global__ void __launch_bounds__((CW + 1) * 32, 1)
                         xb[4 * q + 0] = vb.x; xb[4 * q + 1] = vb.y;
                         xb[4 * q + 2] = vb.z; xb[4 * q + 3] = vb.w;
                     }
+                    oa = __float_as_int(xa[15]);
+                    ob = __float_as_int(xb[15]);
                     if (i >= base + c && i < base + c + 64) {
                         // the query itself is in this step: make it infinitely far
                         if (ja == i) {
@@ -458,7 +491,7 @@ __global__ void __launch_bounds__((CW + 1) * 32, 1)
 #pragma unroll
                 for (int f = 14; f >= kLB; --f)
                     if ((high >> (f - kLB)) & 1u) v[0] = __ffma2_rn(d[f], d[f], v[0]);
-                tree_walk<0, KMAX>(ws, v, d, Tc, tcount, (int)ja, (int)jb, k);
+                tree_walk<0, KMAX>(ws, v, d, Tc, tcount, oa, ob, k);
                 // flushing once a batch is waiting keeps the kNN thresholds fresh
                 // without paying a flush per step
                 if (tcount >= kFlushMin) {
@@ -479,9 +512,9 @@ __global__ void __launch_bounds__((CW + 1) * 32, 1)
                 const int slot = ch->slot[L];
                 float *sc = o.scores + (int64_t)slot * 4 * n;
                 const int cnt = ws.cnt[L];
-                sc[i] = (float)cnt;
-                sc[n + i] = dev::eps_mean(ws.esum[L], cnt, ws.escale[L]);
-                if (o.eps_count) o.eps_count[(int64_t)slot * n + i] = cnt;
+                sc[orig_i] = (float)cnt;
+                sc[n + orig_i] = dev::eps_mean(ws.esum[L], cnt, ws.escale[L]);
+                if (o.eps_count) o.eps_count[(int64_t)slot * n + orig_i] = cnt;
                 if (k > 0) {
                     float msum = 0.f;
                     for (int p = 0; p < k; ++p) {
@@ -489,10 +522,10 @@ __global__ void __launch_bounds__((CW + 1) * 32, 1)
                         const int j = ws.lj[L][p];
                         msum += dd;
                         if (j >= 0 && j < n) atomicAdd(&sc[2 * n + j], 1.f);
-                        if (o.knn_idx) o.knn_idx[((int64_t)slot * n + i) * k + p] = j;
-                        if (o.knn_dist) o.knn_dist[((int64_t)slot * n + i) * k + p] = dd;
+                        if (o.knn_idx) o.knn_idx[((int64_t)slot * n + orig_i) * k + p] = j;
+                        if (o.knn_dist) o.knn_dist[((int64_t)slot * n + orig_i) * k + p] = dd;
                     }
-                    sc[3 * n + i] = msum / (float)k;
+                    sc[3 * n + orig_i] = msum / (float)k;
                 }
             }
             __syncwarp();
@@ -530,7 +563,7 @@ snaps_status launch_join_tree(const JoinShape &s, const TreeChunk *chunks, int n
                               const JoinOut &o, DeviceControl *ctrl, cudaStream_t st)
 {
     if (n_chunks <= 0) return SNAPS_OK;
-    if (s.k <= 16) return launch_tree<16, 15>(s, chunks, n_chunks, o, ctrl, st);
+    if (s.k <= 16) return launch_tree<16, 6>(s, chunks, n_chunks, o, ctrl, st);
     return launch_tree<32, 8>(s, chunks, n_chunks, o, ctrl, st);
 }
 

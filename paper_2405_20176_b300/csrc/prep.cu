@@ -104,6 +104,7 @@ __global__ void normalise_rows_kernel(const float *__restrict__ in, int64_t n, i
                 }
                 v[c] = y;
             }
+            v[15] = __int_as_float((int)r);  // the object's original index (features are 0..14)
         } else {
 #pragma unroll
             for (int c = 0; c < 16; ++c) v[c] = CUDART_INF_F;
@@ -114,15 +115,66 @@ __global__ void normalise_rows_kernel(const float *__restrict__ in, int64_t n, i
     }
 }
 
+// Rows come out in their original order: float 15 of a stored row holds the
+// object's original index.
 __global__ void unpack_rows_kernel(const float4 *__restrict__ x, int64_t n, int f,
                                    float *__restrict__ out)
 {
     for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n;
          r += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t o = __float_as_int(x[row_quad(r, 3)].w);
         for (int c = 0; c < f; ++c) {
             const float4 v = x[row_quad(r, c / 4)];
             const int e = c % 4;
-            out[r * f + c] = e == 0 ? v.x : e == 1 ? v.y : e == 2 ? v.z : v.w;
+            out[o * f + c] = e == 0 ? v.x : e == 1 ? v.y : e == 2 ? v.z : v.w;
+        }
+    }
+}
+
+// Cell key of every row for the sort-by-cell index: each of the 15 features
+// quantised to 2 bits (4 cells per unit range), bits interleaved from the most
+// significant level down, so rows sharing a key prefix are close in every
+// feature.
+__global__ void cell_key_kernel(const float4 *__restrict__ x, int64_t n,
+                                uint32_t *__restrict__ keys, int32_t *__restrict__ idx)
+{
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n;
+         r += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t q[15];
+#pragma unroll
+        for (int qq = 0; qq < 4; ++qq) {
+            const float4 v = x[row_quad(r, qq)];
+            const float e[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int f = 4 * qq + u;
+                if (f < 15) q[f] = (uint32_t)fminf(fmaxf(e[u] * 4.f, 0.f), 3.f);
+            }
+        }
+        uint32_t key = 0;
+#pragma unroll
+        for (int b = 1; b >= 0; --b)
+#pragma unroll
+            for (int f = 0; f < 15; ++f) key = (key << 1) | ((q[f] >> b) & 1u);
+        keys[r] = key;
+        idx[r] = (int32_t)r;
+    }
+}
+
+// Sorted row p <- original row perm[p]; padding rows are +inf.
+__global__ void gather_rows_kernel(const float4 *__restrict__ src, const int32_t *__restrict__ perm,
+                                   int64_t n, int64_t n_pad, float4 *__restrict__ dst)
+{
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n_pad;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        if (p < n) {
+            const int64_t o = perm[p];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) dst[row_quad(p, q)] = src[row_quad(o, q)];
+        } else {
+            const float inf = CUDART_INF_F;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) dst[row_quad(p, q)] = make_float4(inf, inf, inf, inf);
         }
     }
 }
@@ -331,6 +383,23 @@ snaps_status launch_normalise(const float *in_dev, int64_t n, int64_t n_pad, int
     SNAPS_CHECK_CUDA(cudaGetLastError());
     const int64_t blocks = std::min<int64_t>((n_pad + 255) / 256, 148 * 16);
     normalise_rows_kernel<<<(unsigned)blocks, 256, 0, st>>>(in_dev, n, n_pad, f, flags, stats, out);
+    SNAPS_CHECK_CUDA(cudaGetLastError());
+    return SNAPS_OK;
+}
+
+snaps_status launch_cell_keys(const float4 *x, int64_t n, uint32_t *keys, int32_t *idx, cudaStream_t st)
+{
+    const int64_t blocks = std::min<int64_t>((n + 255) / 256, 148 * 16);
+    cell_key_kernel<<<(unsigned)blocks, 256, 0, st>>>(x, n, keys, idx);
+    SNAPS_CHECK_CUDA(cudaGetLastError());
+    return SNAPS_OK;
+}
+
+snaps_status launch_gather_rows(const float4 *src, const int32_t *perm, int64_t n, int64_t n_pad,
+                                float4 *dst, cudaStream_t st)
+{
+    const int64_t blocks = std::min<int64_t>((n_pad + 255) / 256, 148 * 16);
+    gather_rows_kernel<<<(unsigned)blocks, 256, 0, st>>>(src, perm, n, n_pad, dst);
     SNAPS_CHECK_CUDA(cudaGetLastError());
     return SNAPS_OK;
 }

@@ -15,12 +15,20 @@ struct ColStats {
 
 // in_dev: n x f row-major floats on the device.  stats: f entries.  bad: one
 // word set non-zero when a value is NaN (without SNAPS_NAN_TO_MEAN) or +-inf.
-// out: the padded quad-planar population (n_pad rows).
+// out: the padded quad-planar population (n_pad rows) in the input's order;
+// float 15 of every real row holds its original index.
 snaps_status launch_normalise(const float *in_dev, int64_t n, int64_t n_pad, int f,
                               uint32_t flags, ColStats *stats, unsigned *bad, float4 *out,
                               cudaStream_t st);
 
-// Copy the first f features of the n population rows out as n x f row-major.
+// Sort-by-cell index: 30-bit cell keys (2 bits per feature, interleaved) and
+// the identity permutation, then the rows gathered into sorted order.
+snaps_status launch_cell_keys(const float4 *x, int64_t n, uint32_t *keys, int32_t *idx, cudaStream_t st);
+snaps_status launch_gather_rows(const float4 *src, const int32_t *perm, int64_t n, int64_t n_pad,
+                                float4 *dst, cudaStream_t st);
+
+// Copy the first f features of the n population rows out as n x f row-major,
+// in the objects' original order.
 snaps_status launch_unpack(const float4 *x, int64_t n, int f, float *out, cudaStream_t st);
 
 // norm[slot][m][i] from scores[slot][m][i] (n_slots x 4 x n each).
