@@ -55,7 +55,6 @@ constexpr int kStages = 3;
 constexpr int kInit = 256;         // candidates handled lane-per-subspace first (one tile)
 constexpr int kTBuf = 512;         // event tuples buffered per warp
 constexpr int kTFlushAt = kTBuf - 64;  // a node appends at most 64 tuples
-constexpr int kGroup = 8;          // nodes voted on before any of them appends
 constexpr int kFlushMin = 16;      // tuples that trigger an end-of-step flush
 
 // Depth-first order of the subset tree over the low kLB bits: node L's parent
@@ -131,6 +130,10 @@ struct TreeSmem {
     WarpState<KMAX> ws[CW];
 };
 
+// The kernel's dynamic shared memory, declared here so that device functions
+// outside the kernel address it as shared memory.
+extern __shared__ __align__(128) unsigned char tree_smem[];
+
 __device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
 
 __device__ __forceinline__ float eps_up(float e2) {
@@ -153,8 +156,9 @@ __device__ __forceinline__ float next_up(float t) {
 // index) pairs do not depend on the order of insertion.  Returns true when a
 // kNN list changed.
 template <int KMAX>
-__device__ __noinline__ bool flush_tuples(WarpState<KMAX> &ws, int count, int k)
+__device__ __noinline__ bool flush_tuples(int ws_off, int count, int k)
 {
+    WarpState<KMAX> &ws = *reinterpret_cast<WarpState<KMAX> *>(tree_smem + ws_off);
     const unsigned lane = dev::lane_id();
     const unsigned lower = (1u << lane) - 1u;
     unsigned changed = 0;  // bit L: list L changed
@@ -221,64 +225,59 @@ __device__ __forceinline__ void load_thresholds(const WarpState<KMAX> &ws, float
     }
 }
 
-// Nodes P .. END-1 of one group: the FFMA2s and the warp votes, with no
-// branch in between so the scheduler can overlap the nodes' latencies.
-template <int P, int END>
-__device__ __forceinline__ void group_votes(float2 (&v)[kW], const float2 (&d)[15],
-                                            const float (&Tc)[kW], unsigned &gvote)
+// The walk: the 32 subspace distances of this lane's two candidates in DFS
+// order (one FFMA2 per node), and the set of subspaces L in which either
+// candidate fell below its pass threshold (bit L of `bits`).  No branches.
+template <int P>
+__device__ __forceinline__ void walk(float2 (&v)[kW], const float2 (&d)[15], const float (&Tc)[kW],
+                                     unsigned &bits)
 {
-    if constexpr (P < END) {
+    if constexpr (P < kW) {
         if constexpr (P > 0) {
             constexpr int b = kDfs.bit[P];
             constexpr int par = kDfs.parent[P];
             v[P] = __ffma2_rn(d[b], d[b], v[par]);
         }
-        const bool pass = (v[P].x < Tc[P]) | (v[P].y < Tc[P]);
-        gvote |= __any_sync(dev::kFull, pass) ? (1u << (P % kGroup)) : 0u;
-        group_votes<P + 1, END>(v, d, Tc, gvote);
+        constexpr int L = kDfs.node[P];
+        bits |= ((v[P].x < Tc[P]) | (v[P].y < Tc[P])) ? (1u << L) : 0u;
+        walk<P + 1>(v, d, Tc, bits);
     }
 }
 
-// The triggered nodes of one group: the lanes that passed append their
-// tuples; a nearly full buffer is flushed.
-template <int P, int END, int KMAX>
-__device__ __forceinline__ void group_appends(WarpState<KMAX> &ws, const float2 (&v)[kW],
-                                              float (&Tc)[kW], unsigned gvote, int &count,
-                                              int ja, int jb, int k)
+// Append the tuples of the subspaces in `hit` (a warp-uniform mask): each
+// node's distances are recomputed from the root with the walk's own FFMA2
+// chain (the low features of L folded from the highest down), so they are
+// bit-identical to the walk's.  A nearly full buffer is flushed; returns true
+// when a flush changed a kNN list.
+template <int KMAX>
+__device__ __forceinline__ bool append_hits(WarpState<KMAX> &ws, int ws_off, unsigned hit, float2 root,
+                                            const float2 (&d)[15], int &count, int ja, int jb, int k)
 {
-    if constexpr (P < END) {
-        if (gvote & (1u << (P % kGroup))) {
-            constexpr int L = kDfs.node[P];
-            const bool pa = v[P].x < Tc[P], pb = v[P].y < Tc[P];
-            const unsigned lt = (1u << dev::lane_id()) - 1u;
-            const unsigned ba = __ballot_sync(dev::kFull, pa);
-            const unsigned bb = __ballot_sync(dev::kFull, pb);
-            if (pa) ws.tbuf[count + __popc(ba & lt)] = make_uint2(__float_as_uint(v[P].x), (L << 24) | ja);
-            count += __popc(ba);
-            if (pb) ws.tbuf[count + __popc(bb & lt)] = make_uint2(__float_as_uint(v[P].y), (L << 24) | jb);
-            count += __popc(bb);
-            if (count > kTFlushAt) {
-                if (flush_tuples<KMAX>(ws, count, k)) load_thresholds<0>(ws, Tc);
-                count = 0;
-            }
+    const unsigned lower = (1u << dev::lane_id()) - 1u;
+    bool changed = false;
+    while (hit) {
+        const int L = __ffs(hit) - 1;
+        hit &= hit - 1;
+        float2 v = root;
+        if (L & 16) v = __ffma2_rn(d[4], d[4], v);
+        if (L & 8) v = __ffma2_rn(d[3], d[3], v);
+        if (L & 4) v = __ffma2_rn(d[2], d[2], v);
+        if (L & 2) v = __ffma2_rn(d[1], d[1], v);
+        if (L & 1) v = __ffma2_rn(d[0], d[0], v);
+        const float tc = ws.tc[L];
+        const bool pa = v.x < tc, pb = v.y < tc;
+        const unsigned ba = __ballot_sync(dev::kFull, pa);
+        const unsigned bb = __ballot_sync(dev::kFull, pb);
+        if (pa) ws.tbuf[count + __popc(ba & lower)] = make_uint2(__float_as_uint(v.x), (L << 24) | ja);
+        count += __popc(ba);
+        if (pb) ws.tbuf[count + __popc(bb & lower)] = make_uint2(__float_as_uint(v.y), (L << 24) | jb);
+        count += __popc(bb);
+        if (count > kTFlushAt) {
+            changed |= flush_tuples<KMAX>(ws_off, count, k);
+            count = 0;
         }
-        group_appends<P + 1, END, KMAX>(ws, v, Tc, gvote, count, ja, jb, k);
     }
-}
-
-// Walk the DFS in groups of kGroup nodes: votes first, then appends.
-template <int G, int KMAX>
-__device__ __forceinline__ void tree_walk(WarpState<KMAX> &ws, float2 (&v)[kW],
-                                          const float2 (&d)[15], float (&Tc)[kW], int &count,
-                                          int ja, int jb, int k)
-{
-    if constexpr (G * kGroup < kW) {
-        unsigned gvote = 0;
-        group_votes<G * kGroup, (G + 1) * kGroup>(v, d, Tc, gvote);
-        if (gvote)
-            group_appends<G * kGroup, (G + 1) * kGroup, KMAX>(ws, v, Tc, gvote, count, ja, jb, k);
-        tree_walk<G + 1, KMAX>(ws, v, d, Tc, count, ja, jb, k);
-    }
+    return changed;
 }
 
 template <int KMAX, int CW>
@@ -286,8 +285,7 @@ __global__ void __launch_bounds__((CW + 1) * 32, kCtasPerSm<CW>)
     join_tree_kernel(JoinShape s, const TreeChunk *__restrict__ chunks, int n_chunks, JoinOut o,
                      DeviceControl *ctrl)
 {
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    TreeSmem<KMAX, CW> &sm = *reinterpret_cast<TreeSmem<KMAX, CW> *>(smem_raw);
+    TreeSmem<KMAX, CW> &sm = *reinterpret_cast<TreeSmem<KMAX, CW> *>(tree_smem);
     const int warp = threadIdx.x >> 5;
     const unsigned lane = threadIdx.x & 31u;
     const int64_t n = s.n;
@@ -338,6 +336,7 @@ __global__ void __launch_bounds__((CW + 1) * 32, kCtasPerSm<CW>)
 
     // ---- consumers -------------------------------------------------------------------
     WarpState<KMAX> &ws = sm.ws[warp];
+    const int ws_off = (int)((const unsigned char *)&sm.ws[warp] - tree_smem);
     uint32_t g = 0;
     float Tc[kW];
     float2 nxq[15];
@@ -491,12 +490,18 @@ __global__ void __launch_bounds__((CW + 1) * 32, kCtasPerSm<CW>)
 #pragma unroll
                 for (int f = 14; f >= kLB; --f)
                     if ((high >> (f - kLB)) & 1u) v[0] = __ffma2_rn(d[f], d[f], v[0]);
-                tree_walk<0, KMAX>(ws, v, d, Tc, tcount, oa, ob, k);
-                // flushing once a batch is waiting keeps the kNN thresholds fresh
-                // without paying a flush per step
-                if (tcount >= kFlushMin) {
-                    if (flush_tuples<KMAX>(ws, tcount, k)) load_thresholds<0>(ws, Tc);
-                    tcount = 0;
+                unsigned bits = 0u;
+                walk<0>(v, d, Tc, bits);
+                const unsigned hit = __reduce_or_sync(dev::kFull, bits);
+                if (hit) {
+                    bool changed = append_hits<KMAX>(ws, ws_off, hit, v[0], d, tcount, oa, ob, k);
+                    // flushing once a batch is waiting keeps the kNN thresholds fresh
+                    // without paying a flush per step
+                    if (tcount >= kFlushMin) {
+                        changed |= flush_tuples<KMAX>(ws_off, tcount, k);
+                        tcount = 0;
+                    }
+                    if (changed) load_thresholds<0>(ws, Tc);
                 }
             }
         }
@@ -505,7 +510,7 @@ __global__ void __launch_bounds__((CW + 1) * 32, kCtasPerSm<CW>)
 
         // ---- end of the work item: lane L reports subspace L ---------------------------
         if (t == n_tiles - 1) {
-            if (tcount > 0) flush_tuples<KMAX>(ws, tcount, k);
+            if (tcount > 0) flush_tuples<KMAX>(ws_off, tcount, k);
             tcount = 0;
             const uint32_t L = lane;
             if ((active >> L) & 1u) {
