@@ -262,7 +262,8 @@ snaps_status snaps_calibrate_alu(int device, double *evals_per_s);
 #define SNAPS_PHASE_NORM 3       /* normalised-metric kernel */
 #define SNAPS_PHASE_TOP 4        /* top-n ranking kernel */
 #define SNAPS_PHASE_JOIN_TC 5    /* tensor-core filtered join kernel */
-#define SNAPS_N_PHASES 6
+#define SNAPS_PHASE_ORDER 6      /* per-chunk row orders for the subspace-batched join */
+#define SNAPS_N_PHASES 7
 
 /* enable != 0: clear the counters and start recording, around every kernel
  * launch of every later call on this context, a pair of CUDA events on the

@@ -35,9 +35,9 @@ SNAPS_TC_F16 = 1
 SNAPS_STATIC_MAX_N = 32768
 SNAPS_STATIC_MAX_MASKS = 32768
 SNAPS_PHASE_INDEX, SNAPS_PHASE_JOIN_TREE, SNAPS_PHASE_JOIN_LANE, SNAPS_PHASE_NORM, SNAPS_PHASE_TOP, \
-    SNAPS_PHASE_JOIN_TC = range(6)
-SNAPS_N_PHASES = 6
-PHASE_NAMES = ["index", "join_tree", "join_lane", "norm", "top", "join_tc"]
+    SNAPS_PHASE_JOIN_TC, SNAPS_PHASE_ORDER = range(7)
+SNAPS_N_PHASES = 7
+PHASE_NAMES = ["index", "join_tree", "join_lane", "norm", "top", "join_tc", "order"]
 
 
 class SnapsError(RuntimeError):

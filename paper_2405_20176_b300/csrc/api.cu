@@ -115,6 +115,7 @@ struct snaps_pop {
     bool unit_range = false;  // every stored feature spans <= 1 (tensor-core filter allowed)
     float4 *x = nullptr;
     size_t bytes = 0;
+    KeyRange kr{};           // maps stored features onto [0, 1] for cell keys
     std::atomic<int> inflight{0};
 };
 
@@ -252,7 +253,33 @@ struct Plan {
     std::vector<TreeChunk> chunks;
     std::vector<MaskGroup> groups;
     std::vector<TcBlock> blocks;
+    int order_batch = 0;  // chunks whose row orders are built at a time
 };
+
+// Device bytes for the per-chunk row orders of one batch of chunks: the row
+// copies, sort keys and values (double-buffered) and the sort's temporary
+// storage.
+constexpr size_t kOrderBytes = size_t(4) << 30;
+
+size_t order_chunk_bytes(const snaps_pop *p)
+{
+    return (size_t)p->n_pad * kRowFloats * sizeof(float) + (size_t)p->n * 2 * (sizeof(uint64_t) + sizeof(int32_t));
+}
+
+int order_end_bit(int batch)
+{
+    int hb = 0;
+    while ((1 << hb) < batch) ++hb;
+    return 32 + hb;
+}
+
+size_t order_sort_temp(int64_t items, int end_bit)
+{
+    size_t bytes = 0;
+    cub::DeviceRadixSort::SortPairs(nullptr, bytes, (const uint64_t *)nullptr, (uint64_t *)nullptr,
+                                    (const int32_t *)nullptr, (int32_t *)nullptr, (int)items, 0, end_bit);
+    return bytes;
+}
 
 Plan make_plan(const JobSpec &j)
 {
@@ -337,6 +364,10 @@ Plan make_plan(const JobSpec &j)
         }
         pl.groups.push_back(g);
     }
+    if (!pl.chunks.empty()) {
+        const size_t per = order_chunk_bytes(j.pop);
+        pl.order_batch = (int)std::max<size_t>(1, std::min<size_t>(pl.chunks.size(), kOrderBytes / per));
+    }
     return pl;
 }
 
@@ -351,6 +382,12 @@ struct Layout {
     TreeChunk *chunks = nullptr;
     MaskGroup *groups = nullptr;
     TcBlock *blocks = nullptr;
+    // per-chunk row orders (one batch)
+    float4 *ocopy = nullptr;
+    uint64_t *okeys = nullptr, *okeys2 = nullptr;
+    int32_t *ovals = nullptr, *ovals2 = nullptr;
+    void *otmp = nullptr;
+    size_t otmp_bytes = 0;
     size_t bytes = 0;
 };
 
@@ -370,6 +407,17 @@ Layout layout_job(const JobSpec &j, const Plan &pl, char *base, bool dev_scores,
     L.chunks = cv.take<TreeChunk>(pl.chunks.size());
     L.groups = cv.take<MaskGroup>(pl.groups.size());
     L.blocks = cv.take<TcBlock>(pl.blocks.size());
+    if (pl.order_batch > 0) {
+        const size_t g = (size_t)pl.order_batch;
+        const int64_t items = (int64_t)g * j.pop->n;
+        L.ocopy = cv.take<float4>(g * (size_t)j.pop->n_pad * 4);
+        L.okeys = cv.take<uint64_t>((size_t)items);
+        L.okeys2 = cv.take<uint64_t>((size_t)items);
+        L.ovals = cv.take<int32_t>((size_t)items);
+        L.ovals2 = cv.take<int32_t>((size_t)items);
+        L.otmp_bytes = order_sort_temp(items, order_end_bit(pl.order_batch));
+        L.otmp = cv.take<char>(L.otmp_bytes);
+    }
     L.bytes = cv.off + 256;
     return L;
 }
@@ -421,6 +469,60 @@ struct TraceScope {
     }
 };
 
+// How many kernels cub::DeviceRadixSort::SortPairs launches for `items`
+// (key, value) pairs over key bits [0, end_bit): the sort is recorded by a
+// stream capture on a private stream (recording runs nothing) and its kernel
+// nodes are counted; cached per shape.  Used only to report launch counts
+// while tracing.
+template <class K>
+snaps_status sort_kernel_count(snaps_ctx *ctx, int64_t items, int end_bit, void *tmp, size_t tmp_bytes,
+                               const K *k_in, K *k_out, const int32_t *i_in, int32_t *i_out, int *count)
+{
+    std::lock_guard<std::mutex> g(ctx->cap_mu);
+    const int64_t key = (items << 8) | ((int64_t)sizeof(K) << 6) | end_bit;
+    auto it = ctx->sort_kernels.find(key);
+    if (it != ctx->sort_kernels.end()) {
+        *count = it->second;
+        return SNAPS_OK;
+    }
+    if (!ctx->cap_stream)
+        SNAPS_CHECK_CUDA(cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
+    SNAPS_CHECK_CUDA(cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal));
+    const cudaError_t ce = cub::DeviceRadixSort::SortPairs(tmp, tmp_bytes, k_in, k_out, i_in, i_out, (int)items,
+                                                           0, end_bit, ctx->cap_stream);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ee = cudaStreamEndCapture(ctx->cap_stream, &graph);
+    if (ce != cudaSuccess || ee != cudaSuccess || !graph) {
+        if (graph) cudaGraphDestroy(graph);
+        set_error("recording a radix sort failed: %s", cudaGetErrorString(ce != cudaSuccess ? ce : ee));
+        return SNAPS_ECUDA;
+    }
+    size_t nn = 0;
+    cudaError_t ge = cudaGraphGetNodes(graph, nullptr, &nn);
+    std::vector<cudaGraphNode_t> nodes(nn);
+    if (ge == cudaSuccess && nn) ge = cudaGraphGetNodes(graph, nodes.data(), &nn);
+    int kernels = 0;
+    for (size_t q = 0; ge == cudaSuccess && q < nn; ++q) {
+        cudaGraphNodeType t;
+        ge = cudaGraphNodeGetType(nodes[q], &t);
+        if (ge == cudaSuccess && t == cudaGraphNodeTypeKernel) ++kernels;
+    }
+    cudaGraphDestroy(graph);
+    if (ge != cudaSuccess) {
+        set_error("reading a recorded radix sort failed: %s", cudaGetErrorString(ge));
+        return SNAPS_ECUDA;
+    }
+    ctx->sort_kernels[key] = kernels;
+    *count = kernels;
+    return SNAPS_OK;
+}
+
+bool tracing_on(snaps_ctx *ctx)
+{
+    std::lock_guard<std::mutex> g(ctx->tr_mu);
+    return ctx->tracing;
+}
+
 // Run one job on `st` with `scratch`.  Returns after host outputs are written
 // (it synchronises the stream when any output is host memory, or when
 // `sync` is set).
@@ -457,9 +559,31 @@ snaps_status run_job(snaps_ctx *ctx, const JobSpec &j, cudaStream_t st, Scratch 
 
     JoinShape shape{p->x, n, p->n_pad, j.k};
     JoinOut out{L.scores, L.knn_idx, L.knn_dist, L.eps_count};
-    if (!pl.chunks.empty()) {
+    const int n_chunks = (int)pl.chunks.size();
+    for (int b0 = 0; b0 < n_chunks; b0 += pl.order_batch) {
+        // every chunk gets its rows in its own order (Morton over its high
+        // features), so that a query's stream starts among its neighbours in
+        // the features all 32 of the chunk's subspaces share
+        const int g = std::min(pl.order_batch, n_chunks - b0);
+        const int64_t items = (int64_t)g * n;
+        const int end_bit = order_end_bit(g);
+        int sort_kernels = 0;
+        if (tracing_on(ctx))
+            SNAPS_TRY(sort_kernel_count<uint64_t>(ctx, items, end_bit, L.otmp, L.otmp_bytes, L.okeys, L.okeys2,
+                                                  L.ovals, L.ovals2, &sort_kernels));
+        {
+            TraceScope ts(ctx, SNAPS_PHASE_ORDER, st, 2 + sort_kernels);
+            SNAPS_TRY(launch_chunk_keys(p->x, n, p->f, L.chunks + b0, g, p->kr, L.okeys, L.ovals, st));
+            size_t tb = L.otmp_bytes;
+            SNAPS_CHECK_CUDA(cub::DeviceRadixSort::SortPairs(L.otmp, tb, L.okeys, L.okeys2, L.ovals, L.ovals2,
+                                                             (int)items, 0, end_bit, st));
+            SNAPS_TRY(launch_gather_chunks(p->x, L.ovals2, n, p->n_pad, g, L.ocopy, st));
+        }
+        JoinShape cs = shape;
+        cs.x = L.ocopy;
+        cs.chunk_stride = p->n_pad * 4;
         TraceScope ts(ctx, SNAPS_PHASE_JOIN_TREE, st);
-        SNAPS_TRY(launch_join_tree(shape, L.chunks, (int)pl.chunks.size(), out, ctrl, st));
+        SNAPS_TRY(launch_join_tree(cs, L.chunks + b0, g, out, ctrl, st));
     }
     if (!pl.groups.empty()) {
         TraceScope ts(ctx, SNAPS_PHASE_JOIN_LANE, st);
@@ -670,55 +794,6 @@ snaps_status snaps_mem_info(const snaps_ctx *ctx, size_t *held, size_t *budget)
     return SNAPS_OK;
 }
 
-namespace {
-
-// How many kernels cub::DeviceRadixSort::SortPairs launches for n pairs of
-// 30-bit keys: the sort is recorded by a stream capture on a private stream
-// (recording runs nothing) and its kernel nodes are counted; cached per n.
-// Used only to report launch counts while tracing.
-snaps_status sort_kernel_count(snaps_ctx *ctx, int64_t n, void *tmp, size_t tmp_bytes,
-                               const uint32_t *k_in, uint32_t *k_out, const int32_t *i_in,
-                               int32_t *i_out, int *count)
-{
-    std::lock_guard<std::mutex> g(ctx->cap_mu);
-    auto it = ctx->sort_kernels.find(n);
-    if (it != ctx->sort_kernels.end()) {
-        *count = it->second;
-        return SNAPS_OK;
-    }
-    if (!ctx->cap_stream)
-        SNAPS_CHECK_CUDA(cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
-    SNAPS_CHECK_CUDA(cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal));
-    const cudaError_t ce = cub::DeviceRadixSort::SortPairs(tmp, tmp_bytes, k_in, k_out, i_in, i_out, (int)n, 0,
-                                                           30, ctx->cap_stream);
-    cudaGraph_t graph = nullptr;
-    const cudaError_t ee = cudaStreamEndCapture(ctx->cap_stream, &graph);
-    if (ce != cudaSuccess || ee != cudaSuccess || !graph) {
-        if (graph) cudaGraphDestroy(graph);
-        set_error("recording the cell sort failed: %s", cudaGetErrorString(ce != cudaSuccess ? ce : ee));
-        return SNAPS_ECUDA;
-    }
-    size_t nn = 0;
-    cudaError_t ge = cudaGraphGetNodes(graph, nullptr, &nn);
-    std::vector<cudaGraphNode_t> nodes(nn);
-    if (ge == cudaSuccess && nn) ge = cudaGraphGetNodes(graph, nodes.data(), &nn);
-    int kernels = 0;
-    for (size_t q = 0; ge == cudaSuccess && q < nn; ++q) {
-        cudaGraphNodeType t;
-        ge = cudaGraphNodeGetType(nodes[q], &t);
-        if (ge == cudaSuccess && t == cudaGraphNodeTypeKernel) ++kernels;
-    }
-    cudaGraphDestroy(graph);
-    if (ge != cudaSuccess) {
-        set_error("reading the recorded cell sort failed: %s", cudaGetErrorString(ge));
-        return SNAPS_ECUDA;
-    }
-    ctx->sort_kernels[n] = kernels;
-    *count = kernels;
-    return SNAPS_OK;
-}
-
-}  // namespace
 
 snaps_status snaps_index(snaps_ctx *ctx, const float *feat, int64_t n, int f, uint32_t flags,
                          void *stream, snaps_pop **out)
@@ -788,6 +863,16 @@ snaps_status snaps_index(snaps_ctx *ctx, const float *feat, int64_t n, int f, ui
         return fail(SNAPS_EINVAL);
     }
     ctx_free(ctx, stage, (dev_in ? 0 : in_bytes) + aux);
+    for (int c = 0; c < 16; ++c) {
+        p->kr.lo[c] = 0.f;
+        p->kr.scale[c] = c < f ? 1.f : 0.f;
+    }
+    if (!(flags & SNAPS_NORM_MINMAX))
+        for (int c = 0; c < f; ++c) {
+            const double span = hstats[c].hi - hstats[c].lo;
+            p->kr.lo[c] = (float)hstats[c].lo;
+            p->kr.scale[c] = span > 0.0 ? (float)(1.0 / span) : 0.f;
+        }
     // ---- sort-by-cell index: rows reordered by their 15-feature cell key, so
     // a tile of consecutive rows is a spatial neighbourhood.  Stored rows keep
     // their original index in float 15.
@@ -814,17 +899,13 @@ snaps_status snaps_index(snaps_ctx *ctx, const float *feat, int64_t n, int f, ui
         void *tmp = b2 + rows_bytes + 4 * arr;
         int sort_kernels = 0;
         snaps_status ss = SNAPS_OK;
-        bool tracing = false;
-        {
-            std::lock_guard<std::mutex> g(ctx->tr_mu);
-            tracing = ctx->tracing;
-        }
-        if (tracing) ss = sort_kernel_count(ctx, n, tmp, cub_bytes, k_in, k_out, i_in, i_out, &sort_kernels);
+        if (tracing_on(ctx))
+            ss = sort_kernel_count<uint32_t>(ctx, n, 30, tmp, cub_bytes, k_in, k_out, i_in, i_out, &sort_kernels);
         cudaError_t ce = cudaSuccess;
         if (ss == SNAPS_OK) {
             TraceScope ts(ctx, SNAPS_PHASE_INDEX, st, 2 + sort_kernels);
             ce = cudaMemcpyAsync(rows, p->x, rows_bytes, cudaMemcpyDeviceToDevice, st);
-            if (ce == cudaSuccess) ss = launch_cell_keys(rows, n, k_in, i_in, st);
+            if (ce == cudaSuccess) ss = launch_cell_keys(rows, n, p->kr, k_in, i_in, st);
             if (ss == SNAPS_OK && ce == cudaSuccess)
                 ce = cub::DeviceRadixSort::SortPairs(tmp, cub_bytes, k_in, k_out, i_in, i_out, (int)n, 0, 30, st);
             if (ss == SNAPS_OK && ce == cudaSuccess) ss = launch_gather_rows(rows, i_out, n, p->n_pad, p->x, st);

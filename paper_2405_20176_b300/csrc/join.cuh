@@ -53,6 +53,9 @@ struct JoinShape {
     int64_t n;
     int64_t n_pad;
     int k;              // 0 disables the kNN join
+    // subspace-batched join only: float4 offset between the row copies of
+    // consecutive chunks (each chunk's rows in its own order); 0 = one shared copy
+    int64_t chunk_stride = 0;
 };
 
 // Launch the lane-per-subspace join over `n_groups` groups (device array).

@@ -51,7 +51,6 @@ namespace {
 constexpr int kLB = kTreeLowBits;  // 5
 constexpr int kW = kTreeWidth;     // 32 subspaces per chunk
 constexpr int kTile = 256;
-constexpr int kStages = 3;
 constexpr int kInit = 256;         // candidates handled lane-per-subspace first (one tile)
 constexpr int kTBuf = 512;         // event tuples buffered per warp
 constexpr int kTFlushAt = kTBuf - 64;  // a node appends at most 64 tuples
@@ -114,19 +113,12 @@ struct WarpState {
     float escale[kW];               // 2^20 / eps
 };
 
-// Two CTAs share an SM when their consumer warps fit (CW <= 6 with k <= 16):
-// each CTA streams its own tiles, so one CTA's event-heavy stretch of the
-// candidate stream overlaps the other's event-free stretch.
+// Two CTAs of six warps share an SM: 12 warps, each with up to 170 registers.
 template <int CW>
-constexpr int kCtasPerSm = CW <= 6 ? 2 : 1;
+constexpr int kCtasPerSm = 2;
 
 template <int KMAX, int CW>
 struct TreeSmem {
-    float4 tile[kStages][kTile * 4];
-    long long stage_work[kStages];  // work item of the tile in each stage (-1: no more work)
-    int stage_tile[kStages];        // tile index within the work item
-    uint64_t full[kStages];
-    uint64_t empty[kStages];
     WarpState<KMAX> ws[CW];
 };
 
@@ -280,8 +272,24 @@ __device__ __forceinline__ bool append_hits(WarpState<KMAX> &ws, int ws_off, uns
     return changed;
 }
 
+// One step's candidates: rows c + lane and c + 32 + lane of a tile, four
+// float4 each, loaded straight from global memory (the population stays in L2).
+struct StepRows {
+    float4 a[4], b[4];
+};
+
+__device__ __forceinline__ void load_step(const float4 *__restrict__ x, int64_t base, int c, unsigned lane,
+                                          StepRows &r)
+{
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        r.a[q] = __ldg(&x[(base / kTile * 4 + q) * kTile + c + lane]);
+        r.b[q] = __ldg(&x[(base / kTile * 4 + q) * kTile + c + 32 + lane]);
+    }
+}
+
 template <int KMAX, int CW>
-__global__ void __launch_bounds__((CW + 1) * 32, kCtasPerSm<CW>)
+__global__ void __launch_bounds__(CW * 32, kCtasPerSm<CW>)
     join_tree_kernel(JoinShape s, const TreeChunk *__restrict__ chunks, int n_chunks, JoinOut o,
                      DeviceControl *ctrl)
 {
@@ -290,228 +298,171 @@ __global__ void __launch_bounds__((CW + 1) * 32, kCtasPerSm<CW>)
     const unsigned lane = threadIdx.x & 31u;
     const int64_t n = s.n;
     const int k = s.k;
-    const long long n_qb = (n + CW - 1) / CW;
-    const long long total = n_qb * (long long)n_chunks;
+    const long long total = n * (long long)n_chunks;
     const int n_tiles = (int)(s.n_pad / kTile);
-    const float4 *x = s.x;
-
-    if (threadIdx.x == 0) {
-        for (int st = 0; st < kStages; ++st) {
-            dev::mbar_init(&sm.full[st], 1);
-            dev::mbar_init(&sm.empty[st], CW);
-        }
-        dev::fence_barrier_init();
-    }
-    __syncthreads();
-
-    if (warp == CW) {
-        // ---- producer: work items and candidate tiles ------------------------------
-        if (lane != 0) return;
-        uint32_t g = 0;  // tiles issued so far
-        for (;;) {
-            const long long w = (long long)atomicAdd(&ctrl->next_work, 1ull);
-            const bool end = w >= total;
-            const int count = end ? 1 : n_tiles;
-            // the stream starts at the query block's own tile: in cell order that
-            // tile is the queries' neighbourhood, which tightens the thresholds early
-            const int t0 = end ? 0 : (int)(((w % n_qb) * CW) / kTile);
-            for (int t = 0; t < count; ++t, ++g) {
-                const uint32_t st = g % kStages;
-                if (g >= (uint32_t)kStages &&
-                    !dev::mbar_wait(&sm.empty[st], ((g / kStages) - 1) & 1u)) {
-                    atomicOr(&ctrl->error, kErrTimeout);
-                    return;
-                }
-                const int phys = (t0 + t) % n_tiles;
-                sm.stage_work[st] = end ? -1 : w;
-                sm.stage_tile[st] = t;
-                if (end)
-                    dev::mbar_arrive(&sm.full[st]);
-                else
-                    dev::bulk_load(sm.tile[st], x + (int64_t)phys * kTile * 4, kTile * 64, &sm.full[st]);
-            }
-            if (end) return;
-        }
-    }
-
-    // ---- consumers -------------------------------------------------------------------
     WarpState<KMAX> &ws = sm.ws[warp];
     const int ws_off = (int)((const unsigned char *)&sm.ws[warp] - tree_smem);
-    uint32_t g = 0;
-    float Tc[kW];
-    float2 nxq[15];
-    float xq[16];
-    int64_t i = 0;
-    int orig_i = 0;  // the query's original index (float 15 of its stored row)
-    bool valid = false;
-    uint32_t active = 0, high = 0;
-    int tcount = 0;  // buffered event tuples (warp-uniform)
-    const TreeChunk *ch = nullptr;
-    for (;; ++g) {
-        const uint32_t st = g % kStages;
-        if (!dev::mbar_wait(&sm.full[st], (g / kStages) & 1u)) {
-            if (lane == 0) atomicOr(&ctrl->error, kErrTimeout);
-            return;
-        }
-        const long long w = sm.stage_work[st];
-        if (w < 0) return;
-        const int t = sm.stage_tile[st];
-        const int phys = (int)((((w % n_qb) * CW) / kTile + t) % n_tiles);
-        const float4 *tile = sm.tile[st];
 
-        if (t == 0) {
-            // ---- new work item: this warp's query and the chunk's subspaces ------------
-            ch = &chunks[w / n_qb];
-            i = (w % n_qb) * CW + warp;
-            valid = i < n;
-            high = ch->high;
-            active = valid ? ch->active : 0u;
-            if (valid) {
+    for (;;) {
+        // ---- next work item (one query of one chunk), claimed by the warp -----------
+        unsigned long long wc = 0;
+        if (lane == 0) wc = atomicAdd(&ctrl->next_work, 1ull);
+        const long long w = (long long)__shfl_sync(dev::kFull, wc, 0);
+        if (w >= total) return;
+        const TreeChunk *ch = &chunks[w / n];
+        // the chunk's rows (in the chunk's own order when each chunk has a copy)
+        const float4 *__restrict__ x = s.x + (w / n) * s.chunk_stride;
+        const int64_t i = w % n;  // the query's row in that order
+        const uint32_t high = ch->high;
+        const uint32_t active = ch->active;
+        float xq[16];
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const float4 v = x[row_quad(i, q)];
-                    xq[4 * q + 0] = v.x;
-                    xq[4 * q + 1] = v.y;
-                    xq[4 * q + 2] = v.z;
-                    xq[4 * q + 3] = v.w;
-                }
-                orig_i = __float_as_int(xq[15]);
-            } else {
-#pragma unroll
-                for (int f = 0; f < 16; ++f) xq[f] = 0.f;
-            }
-#pragma unroll
-            for (int f = 0; f < 15; ++f) nxq[f] = f2(-xq[f], -xq[f]);
-            {
-                const uint32_t L = lane;
-                const float e2 = ch->eps2[L];
-                ws.eps2[L] = e2;
-                ws.escale[L] = dev::eps_scale(e2).scale;
-                for (int p = 0; p < KMAX; ++p) {
-                    ws.ld[L][p] = CUDART_INF_F;
-                    ws.lj[L][p] = 0x7fffffff;
-                }
-                ws.esum[L] = 0ull;
-                ws.epart[L] = 0u;
-                ws.cnt[L] = 0;
-                ws.T[L] = (((active >> L) & 1u) && k > 0) ? CUDART_INF_F : -CUDART_INF_F;
-            }
-            __syncwarp();
-            // ---- set-up phase: lane L folds subspace L over the first candidates and
-            // keeps a private sorted list ---------------------------------------------
-            if (valid) {
-                const uint32_t L = lane;
-                const bool mine = (active >> L) & 1u;
-                const uint32_t mask = (high << kLB) | L;
-                const float e2 = ws.eps2[L];
-                const float sc = ws.escale[L];
-                float T = ws.T[L];
-                int cnt = 0;
-                unsigned long long qs = 0;
-                float wgt[15];
-#pragma unroll
-                for (int f = 0; f < 15; ++f) wgt[f] = ((mask >> f) & 1u) ? 1.f : 0.f;
-                const int64_t tbase = (int64_t)phys * kTile;
-                const int c_end = (int)std::min<int64_t>(kInit, n - tbase);
-                for (int c = 0; c < c_end; ++c) {
-                    if (tbase + c == i) continue;
-                    float xc[16];
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        const float4 v = tile[q * kTile + c];
-                        xc[4 * q + 0] = v.x;
-                        xc[4 * q + 1] = v.y;
-                        xc[4 * q + 2] = v.z;
-                        xc[4 * q + 3] = v.w;
-                    }
-                    float acc = 0.f;
-#pragma unroll
-                    for (int f = 14; f >= 0; --f) {
-                        const float dd = xc[f] - xq[f];
-                        acc = fmaf(dd * wgt[f], dd, acc);
-                    }
-                    if (mine && acc <= e2) {
-                        ++cnt;
-                        qs += dev::eps_quant(acc, sc);
-                    }
-                    const int oc = __float_as_int(xc[15]);
-                    if (mine && (acc < T || (acc == T && oc < ws.lj[L][k - 1])))
-                        T = dev::private_insert(ws.ld[L], ws.lj[L], k, acc, oc);
-                }
-                ws.T[L] = T;
-                ws.cnt[L] = cnt;
-                ws.esum[L] = qs;
-            }
-            {
-                const uint32_t L = lane;
-                ws.tc[L] = ((active >> L) & 1u) ? fmaxf(next_up(ws.T[L]), eps_up(ws.eps2[L])) : -CUDART_INF_F;
-            }
-            __syncwarp();
-            load_thresholds<0>(ws, Tc);
+        for (int q = 0; q < 4; ++q) {
+            const float4 v = x[row_quad(i, q)];
+            xq[4 * q + 0] = v.x;
+            xq[4 * q + 1] = v.y;
+            xq[4 * q + 2] = v.z;
+            xq[4 * q + 3] = v.w;
         }
-
-        // ---- main loop over the tile -----------------------------------------------------
-        if (valid) {
-            const int64_t base = (int64_t)phys * kTile;
-            for (int c = (t == 0 ? kInit : 0); c < kTile; c += 64) {
-                const int64_t ja = base + c + lane;
-                const int64_t jb = ja + 32;
-                int oa = 0, ob = 0;  // original indices of the two candidates
-                float2 d[15];
-                {
-                    float xa[16], xb[16];
+        const int orig_i = __float_as_int(xq[15]);  // the query's original index
+        float2 nxq[15];
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        const float4 va = tile[q * kTile + c + lane];
-                        const float4 vb = tile[q * kTile + c + 32 + lane];
-                        xa[4 * q + 0] = va.x; xa[4 * q + 1] = va.y;
-                        xa[4 * q + 2] = va.z; xa[4 * q + 3] = va.w;
-                        xb[4 * q + 0] = vb.x; xb[4 * q + 1] = vb.y;
-                        xb[4 * q + 2] = vb.z; xb[4 * q + 3] = vb.w;
-                    }
-                    oa = __float_as_int(xa[15]);
-                    ob = __float_as_int(xb[15]);
-                    if (i >= base + c && i < base + c + 64) {
-                        // the query itself is in this step: make it infinitely far
-                        if (ja == i) {
-#pragma unroll
-                            for (int f = 0; f < 16; ++f) xa[f] = CUDART_INF_F;
-                        }
-                        if (jb == i) {
-#pragma unroll
-                            for (int f = 0; f < 16; ++f) xb[f] = CUDART_INF_F;
-                        }
-                    }
-#pragma unroll
-                    for (int f = 0; f < 15; ++f) d[f] = __fadd2_rn(f2(xa[f], xb[f]), nxq[f]);
-                }
-                float2 v[kW];
-                v[0] = f2(0.f, 0.f);
-#pragma unroll
-                for (int f = 14; f >= kLB; --f)
-                    if ((high >> (f - kLB)) & 1u) v[0] = __ffma2_rn(d[f], d[f], v[0]);
-                unsigned bits = 0u;
-                walk<0>(v, d, Tc, bits);
-                const unsigned hit = __reduce_or_sync(dev::kFull, bits);
-                if (hit) {
-                    bool changed = append_hits<KMAX>(ws, ws_off, hit, v[0], d, tcount, oa, ob, k);
-                    // flushing once a batch is waiting keeps the kNN thresholds fresh
-                    // without paying a flush per step
-                    if (tcount >= kFlushMin) {
-                        changed |= flush_tuples<KMAX>(ws_off, tcount, k);
-                        tcount = 0;
-                    }
-                    if (changed) load_thresholds<0>(ws, Tc);
-                }
+        for (int f = 0; f < 15; ++f) nxq[f] = f2(-xq[f], -xq[f]);
+        // the candidate stream starts at the query's own tile (in cell order, its
+        // neighbourhood) and wraps around
+        const int t0 = (int)(i / kTile);
+        {
+            const uint32_t L = lane;
+            const float e2 = ch->eps2[L];
+            ws.eps2[L] = e2;
+            ws.escale[L] = dev::eps_scale(e2).scale;
+            for (int p = 0; p < KMAX; ++p) {
+                ws.ld[L][p] = CUDART_INF_F;
+                ws.lj[L][p] = 0x7fffffff;
             }
+            ws.esum[L] = 0ull;
+            ws.epart[L] = 0u;
+            ws.cnt[L] = 0;
+            ws.T[L] = (((active >> L) & 1u) && k > 0) ? CUDART_INF_F : -CUDART_INF_F;
         }
         __syncwarp();
-        if (lane == 0) dev::mbar_arrive(&sm.empty[st]);
+        // ---- set-up phase: lane L folds subspace L over the query's own tile and
+        // keeps a private sorted list ---------------------------------------------------
+        {
+            const uint32_t L = lane;
+            const bool mine = (active >> L) & 1u;
+            const uint32_t mask = (high << kLB) | L;
+            const float e2 = ws.eps2[L];
+            const float sc = ws.escale[L];
+            float T = ws.T[L];
+            int cnt = 0;
+            unsigned long long qs = 0;
+            float wgt[15];
+#pragma unroll
+            for (int f = 0; f < 15; ++f) wgt[f] = ((mask >> f) & 1u) ? 1.f : 0.f;
+            const int64_t tbase = (int64_t)t0 * kTile;
+            const int c_end = (int)std::min<int64_t>(kInit, n - tbase);
+            for (int c = 0; c < c_end; ++c) {
+                if (tbase + c == i) continue;
+                float xc[16];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const float4 v = __ldg(&x[((int64_t)t0 * 4 + q) * kTile + c]);
+                    xc[4 * q + 0] = v.x;
+                    xc[4 * q + 1] = v.y;
+                    xc[4 * q + 2] = v.z;
+                    xc[4 * q + 3] = v.w;
+                }
+                float acc = 0.f;
+#pragma unroll
+                for (int f = 14; f >= 0; --f) {
+                    const float dd = xc[f] - xq[f];
+                    acc = fmaf(dd * wgt[f], dd, acc);
+                }
+                if (mine && acc <= e2) {
+                    ++cnt;
+                    qs += dev::eps_quant(acc, sc);
+                }
+                const int oc = __float_as_int(xc[15]);
+                if (mine && (acc < T || (acc == T && oc < ws.lj[L][k - 1])))
+                    T = dev::private_insert(ws.ld[L], ws.lj[L], k, acc, oc);
+            }
+            ws.T[L] = T;
+            ws.cnt[L] = cnt;
+            ws.esum[L] = qs;
+            ws.tc[L] = mine ? fmaxf(next_up(T), eps_up(e2)) : -CUDART_INF_F;
+        }
+        __syncwarp();
+        float Tc[kW];
+        load_thresholds<0>(ws, Tc);
+
+        // ---- main loop: the other tiles, 64 candidates a step, the next step's rows
+        // loaded while this one is walked -----------------------------------------------
+        int tcount = 0;  // buffered event tuples (warp-uniform)
+        const int n_steps = (n_tiles - 1) * (kTile / 64);
+        StepRows cur, nxt;
+        if (n_steps > 0) load_step(x, (int64_t)((t0 + 1) % n_tiles) * kTile, 0, lane, cur);
+        for (int sidx = 0; sidx < n_steps; ++sidx) {
+            const int phys = (t0 + 1 + sidx / (kTile / 64)) % n_tiles;
+            const int c = (sidx % (kTile / 64)) * 64;
+            const int64_t base = (int64_t)phys * kTile;
+            if (sidx + 1 < n_steps) {
+                const int nphys = (t0 + 1 + (sidx + 1) / (kTile / 64)) % n_tiles;
+                load_step(x, (int64_t)nphys * kTile, ((sidx + 1) % (kTile / 64)) * 64, lane, nxt);
+            }
+            const int64_t ja = base + c + lane;
+            const int64_t jb = ja + 32;
+            float2 d[15];
+            int oa, ob;  // original indices of the two candidates
+            {
+                float xa[16], xb[16];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    xa[4 * q + 0] = cur.a[q].x; xa[4 * q + 1] = cur.a[q].y;
+                    xa[4 * q + 2] = cur.a[q].z; xa[4 * q + 3] = cur.a[q].w;
+                    xb[4 * q + 0] = cur.b[q].x; xb[4 * q + 1] = cur.b[q].y;
+                    xb[4 * q + 2] = cur.b[q].z; xb[4 * q + 3] = cur.b[q].w;
+                }
+                oa = __float_as_int(xa[15]);
+                ob = __float_as_int(xb[15]);
+                if (i >= base + c && i < base + c + 64) {
+                    // the query itself is in this step: make it infinitely far
+                    if (ja == i) {
+#pragma unroll
+                        for (int f = 0; f < 16; ++f) xa[f] = CUDART_INF_F;
+                    }
+                    if (jb == i) {
+#pragma unroll
+                        for (int f = 0; f < 16; ++f) xb[f] = CUDART_INF_F;
+                    }
+                }
+#pragma unroll
+                for (int f = 0; f < 15; ++f) d[f] = __fadd2_rn(f2(xa[f], xb[f]), nxq[f]);
+            }
+            cur = nxt;
+            float2 v[kW];
+            v[0] = f2(0.f, 0.f);
+#pragma unroll
+            for (int f = 14; f >= kLB; --f)
+                if ((high >> (f - kLB)) & 1u) v[0] = __ffma2_rn(d[f], d[f], v[0]);
+            unsigned bits = 0u;
+            walk<0>(v, d, Tc, bits);
+            const unsigned hit = __reduce_or_sync(dev::kFull, bits);
+            if (hit) {
+                bool changed = append_hits<KMAX>(ws, ws_off, hit, v[0], d, tcount, oa, ob, k);
+                // flushing once a batch is waiting keeps the kNN thresholds fresh
+                // without paying a flush per step
+                if (tcount >= kFlushMin) {
+                    changed |= flush_tuples<KMAX>(ws_off, tcount, k);
+                    tcount = 0;
+                }
+                if (changed) load_thresholds<0>(ws, Tc);
+            }
+        }
+        if (tcount > 0) flush_tuples<KMAX>(ws_off, tcount, k);
 
         // ---- end of the work item: lane L reports subspace L ---------------------------
-        if (t == n_tiles - 1) {
-            if (tcount > 0) flush_tuples<KMAX>(ws_off, tcount, k);
-            tcount = 0;
+        {
             const uint32_t L = lane;
             if ((active >> L) & 1u) {
                 const int slot = ch->slot[L];
@@ -548,16 +499,15 @@ snaps_status launch_tree(const JoinShape &s, const TreeChunk *chunks, int n_chun
     int dev = 0, sms = 0, per_sm = 0;
     SNAPS_CHECK_CUDA(cudaGetDevice(&dev));
     SNAPS_CHECK_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    SNAPS_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, (CW + 1) * 32, smem));
+    SNAPS_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, CW * 32, smem));
     if (per_sm < 1) {
         set_error("subspace-batched join does not fit on an SM (smem %zu)", smem);
         return SNAPS_ECUDA;
     }
-    const long long n_qb = (s.n + CW - 1) / CW;
-    const long long total = n_qb * (long long)n_chunks;
-    const long long grid = std::min<long long>(total, (long long)sms * per_sm);
+    const long long warps = s.n * (long long)n_chunks;
+    const long long grid = std::min<long long>((warps + CW - 1) / CW, (long long)sms * per_sm);
     SNAPS_CHECK_CUDA(cudaMemsetAsync(&ctrl->next_work, 0, sizeof(unsigned long long), st));
-    kern<<<(unsigned)grid, (CW + 1) * 32, smem, st>>>(s, chunks, n_chunks, o, ctrl);
+    kern<<<(unsigned)grid, CW * 32, smem, st>>>(s, chunks, n_chunks, o, ctrl);
     SNAPS_CHECK_CUDA(cudaGetLastError());
     return SNAPS_OK;
 }
@@ -569,7 +519,7 @@ snaps_status launch_join_tree(const JoinShape &s, const TreeChunk *chunks, int n
 {
     if (n_chunks <= 0) return SNAPS_OK;
     if (s.k <= 16) return launch_tree<16, 6>(s, chunks, n_chunks, o, ctrl, st);
-    return launch_tree<32, 8>(s, chunks, n_chunks, o, ctrl, st);
+    return launch_tree<32, 6>(s, chunks, n_chunks, o, ctrl, st);
 }
 
 }  // namespace snaps

@@ -135,7 +135,7 @@ __global__ void unpack_rows_kernel(const float4 *__restrict__ x, int64_t n, int 
 // quantised to 2 bits (4 cells per unit range), bits interleaved from the most
 // significant level down, so rows sharing a key prefix are close in every
 // feature.
-__global__ void cell_key_kernel(const float4 *__restrict__ x, int64_t n,
+__global__ void cell_key_kernel(const float4 *__restrict__ x, int64_t n, KeyRange kr,
                                 uint32_t *__restrict__ keys, int32_t *__restrict__ idx)
 {
     for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n;
@@ -148,7 +148,7 @@ __global__ void cell_key_kernel(const float4 *__restrict__ x, int64_t n,
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
                 const int f = 4 * qq + u;
-                if (f < 15) q[f] = (uint32_t)fminf(fmaxf(e[u] * 4.f, 0.f), 3.f);
+                if (f < 15) q[f] = (uint32_t)fminf(fmaxf((e[u] - kr.lo[f]) * kr.scale[f] * 4.f, 0.f), 3.f);
             }
         }
         uint32_t key = 0;
@@ -158,6 +158,69 @@ __global__ void cell_key_kernel(const float4 *__restrict__ x, int64_t n,
             for (int f = 0; f < 15; ++f) key = (key << 1) | ((q[f] >> b) & 1u);
         keys[r] = key;
         idx[r] = (int32_t)r;
+    }
+}
+
+// Chunk keys: Morton order over the chunk's high features (see prep.cuh).
+__global__ void chunk_key_kernel(const float4 *__restrict__ x, int64_t n, int f,
+                                 const TreeChunk *__restrict__ chunks, int n_chunks, KeyRange kr,
+                                 uint64_t *__restrict__ keys, int32_t *__restrict__ vals)
+{
+    const int64_t total = n * (int64_t)n_chunks;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int g = (int)(e / n);
+        const int64_t r = e - (int64_t)g * n;
+        const uint32_t high = chunks[g].high;
+        float v[16];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const float4 t = x[row_quad(r, q)];
+            v[4 * q + 0] = t.x;
+            v[4 * q + 1] = t.y;
+            v[4 * q + 2] = t.z;
+            v[4 * q + 3] = t.w;
+        }
+        // the key's features: H's, or the low ones when H is empty
+        const uint32_t fmask = high ? (high << kTreeLowBits) : ((1u << min(f, kTreeLowBits)) - 1u);
+        const int nd = __popc(fmask);
+        const int bits = min(10, 30 / nd);
+        uint32_t q[15];
+#pragma unroll
+        for (int c = 0; c < 15; ++c) {
+            const float u = (v[c] - kr.lo[c]) * kr.scale[c];
+            const float top = (float)((1u << bits) - 1u);
+            q[c] = (uint32_t)fminf(fmaxf(u * (float)(1u << bits), 0.f), top);
+        }
+        uint32_t key = 0;
+        for (int b = bits - 1; b >= 0; --b)
+#pragma unroll
+            for (int c = 14; c >= 0; --c)
+                if ((fmask >> c) & 1u) key = (key << 1) | ((q[c] >> b) & 1u);
+        keys[e] = ((uint64_t)g << 32) | key;
+        vals[e] = (int32_t)r;
+    }
+}
+
+// out[g][p] <- x[perm[g * n + p]] (quad-planar, n_pad rows per chunk).
+__global__ void gather_chunks_kernel(const float4 *__restrict__ x, const int32_t *__restrict__ perm,
+                                     int64_t n, int64_t n_pad, int n_chunks, float4 *__restrict__ out)
+{
+    const int64_t total = n_pad * (int64_t)n_chunks;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t g = e / n_pad;
+        const int64_t p = e - g * n_pad;
+        float4 *dst = out + g * n_pad * 4;
+        if (p < n) {
+            const int64_t o = perm[g * n + p];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) dst[row_quad(p, q)] = x[row_quad(o, q)];
+        } else {
+            const float inf = CUDART_INF_F;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) dst[row_quad(p, q)] = make_float4(inf, inf, inf, inf);
+        }
     }
 }
 
@@ -387,10 +450,31 @@ snaps_status launch_normalise(const float *in_dev, int64_t n, int64_t n_pad, int
     return SNAPS_OK;
 }
 
-snaps_status launch_cell_keys(const float4 *x, int64_t n, uint32_t *keys, int32_t *idx, cudaStream_t st)
+snaps_status launch_cell_keys(const float4 *x, int64_t n, const KeyRange &kr, uint32_t *keys,
+                              int32_t *idx, cudaStream_t st)
 {
     const int64_t blocks = std::min<int64_t>((n + 255) / 256, 148 * 16);
-    cell_key_kernel<<<(unsigned)blocks, 256, 0, st>>>(x, n, keys, idx);
+    cell_key_kernel<<<(unsigned)blocks, 256, 0, st>>>(x, n, kr, keys, idx);
+    SNAPS_CHECK_CUDA(cudaGetLastError());
+    return SNAPS_OK;
+}
+
+snaps_status launch_chunk_keys(const float4 *x, int64_t n, int f, const TreeChunk *chunks, int n_chunks,
+                               const KeyRange &kr, uint64_t *keys, int32_t *vals, cudaStream_t st)
+{
+    const int64_t total = n * (int64_t)n_chunks;
+    const int64_t blocks = std::min<int64_t>((total + 255) / 256, 148 * 16);
+    chunk_key_kernel<<<(unsigned)blocks, 256, 0, st>>>(x, n, f, chunks, n_chunks, kr, keys, vals);
+    SNAPS_CHECK_CUDA(cudaGetLastError());
+    return SNAPS_OK;
+}
+
+snaps_status launch_gather_chunks(const float4 *x, const int32_t *perm, int64_t n, int64_t n_pad,
+                                  int n_chunks, float4 *out, cudaStream_t st)
+{
+    const int64_t total = n_pad * (int64_t)n_chunks;
+    const int64_t blocks = std::min<int64_t>((total + 255) / 256, 148 * 16);
+    gather_chunks_kernel<<<(unsigned)blocks, 256, 0, st>>>(x, perm, n, n_pad, n_chunks, out);
     SNAPS_CHECK_CUDA(cudaGetLastError());
     return SNAPS_OK;
 }

@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include "common.cuh"
+#include "join.cuh"
 
 namespace snaps {
 
@@ -21,11 +22,30 @@ snaps_status launch_normalise(const float *in_dev, int64_t n, int64_t n_pad, int
                               uint32_t flags, ColStats *stats, unsigned *bad, float4 *out,
                               cudaStream_t st);
 
+// Maps each stored feature onto [0, 1] for cell keys: (v - lo) * scale.
+struct KeyRange {
+    float lo[16];
+    float scale[16];
+};
+
 // Sort-by-cell index: 30-bit cell keys (2 bits per feature, interleaved) and
 // the identity permutation, then the rows gathered into sorted order.
-snaps_status launch_cell_keys(const float4 *x, int64_t n, uint32_t *keys, int32_t *idx, cudaStream_t st);
+snaps_status launch_cell_keys(const float4 *x, int64_t n, const KeyRange &kr, uint32_t *keys,
+                              int32_t *idx, cudaStream_t st);
 snaps_status launch_gather_rows(const float4 *src, const int32_t *perm, int64_t n, int64_t n_pad,
                                 float4 *dst, cudaStream_t st);
+
+// Per-chunk orders for the subspace-batched join.  For chunk g of `chunks`
+// (high part H), keys[g * n + r] = g << 32 | the Morton key of row r over the
+// features in H (feature 5 + b for bit b of H; features 0..4 when H = 0), each
+// quantised to min(10, 30 / |features|) bits; vals[g * n + r] = r.
+snaps_status launch_chunk_keys(const float4 *x, int64_t n, int f, const TreeChunk *chunks, int n_chunks,
+                               const KeyRange &kr, uint64_t *keys, int32_t *vals, cudaStream_t st);
+
+// out[g] (n_pad rows each) <- the rows of x in chunk g's sorted order perm[g * n ..];
+// padding rows are +inf.
+snaps_status launch_gather_chunks(const float4 *x, const int32_t *perm, int64_t n, int64_t n_pad,
+                                  int n_chunks, float4 *out, cudaStream_t st);
 
 // Copy the first f features of the n population rows out as n x f row-major,
 // in the objects' original order.
