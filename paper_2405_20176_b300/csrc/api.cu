@@ -629,6 +629,7 @@ snaps_status run_job(snaps_ctx *ctx, const JobSpec &j, cudaStream_t st, Scratch 
         unsigned err = 0;
         SNAPS_CHECK_CUDA(cudaMemcpyAsync(&err, &ctrl->error, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
         SNAPS_CHECK_CUDA(cudaStreamSynchronize(st));
+        if (err & kErrBadRow) FAIL(SNAPS_ECUDA, "a join kernel met rows without a valid original index (error word 0x%x)", err);
         if (err) FAIL(SNAPS_ETIMEOUT, "a device-side wait gave up (error word 0x%x)", err);
     }
     return SNAPS_OK;

@@ -49,6 +49,20 @@ __host__ __device__ inline int64_t row_quad(int64_t i, int q) {
     return ((i / kRowPad) * 4 + q) * kRowPad + (i % kRowPad);
 }
 
+// Pair-planar layout of the subspace-batched join's per-chunk row copies.  The
+// 64 rows of step s = p / 64 form 8 planes of 32 float4; lane l's float4 in
+// plane q holds features 2q and 2q + 1 of rows a = 64s + l and b = 64s + 32 + l
+// as (a[2q], b[2q], a[2q + 1], b[2q + 1]), so that one 16-byte load gives two
+// (a, b) operand pairs for the f32x2 instructions.
+// float4 index of plane q of row p's pair:
+__host__ __device__ inline int64_t pair_plane(int64_t p, int q) {
+    return ((p >> 6) * 8 + q) * 32 + (p & 31);
+}
+// float index of feature f of row p:
+__host__ __device__ inline int64_t pair_float(int64_t p, int f) {
+    return pair_plane(p, f >> 1) * 4 + (f & 1) * 2 + ((p >> 5) & 1);
+}
+
 inline int64_t padded_rows(int64_t n) { return (n + kRowPad - 1) / kRowPad * kRowPad; }
 
 // Default squared radius for a d-feature subspace: eps = 0.05 sqrt(d), so
@@ -63,5 +77,6 @@ struct DeviceControl {
     unsigned int pad;
 };
 constexpr unsigned kErrTimeout = 1u;
+constexpr unsigned kErrBadRow = 2u;  // a row's stored original index is out of range
 
 }  // namespace snaps

@@ -68,6 +68,8 @@ snaps_status launch_join_tc(const JoinShape &s, const TcBlock *blocks, int n_blo
                             const JoinOut &o, DeviceControl *ctrl, cudaStream_t st);
 
 // Launch the subspace-batched tree join over `n_chunks` chunks (device array).
+// `s.x` holds the rows in the pair-planar layout (common.cuh): one copy per
+// chunk, s.chunk_stride float4 apart, or one shared copy (chunk_stride 0).
 snaps_status launch_join_tree(const JoinShape &s, const TreeChunk *chunks, int n_chunks,
                               const JoinOut &o, DeviceControl *ctrl, cudaStream_t st);
 

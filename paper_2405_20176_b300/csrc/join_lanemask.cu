@@ -172,7 +172,10 @@ __global__ void __launch_bounds__(kLmWarps * 32)
         }
         used += n_tiles;
 
-        if (active) {
+        if (active && (orig_i < 0 || orig_i >= n)) {
+            // a row that does not carry its index: report, write nothing
+            atomicOr(&ctrl->error, kErrBadRow);
+        } else if (active) {
             const int slot = grp.slot[lane];
             float *sc = o.scores + (int64_t)slot * 4 * n;
             sc[orig_i] = (float)cnt;

@@ -533,7 +533,10 @@ __global__ void __launch_bounds__(kTcWarps * 32)
             tiles_used += n_tiles;
 
             // ---- this query's results: thread c < 64 reports subspace c ------------------------
-            if (tid < kNB && sm.mask[tid] != 0u) {
+            if (tid < kNB && sm.mask[tid] != 0u && (orig_i < 0 || orig_i >= n)) {
+                // a row that does not carry its index: report, write nothing
+                atomicOr(&ctrl->error, kErrBadRow);
+            } else if (tid < kNB && sm.mask[tid] != 0u) {
                 const int c = tid;
                 const int slot = sm.slot[c];
                 float *sc = o.scores + (int64_t)slot * 4 * n;

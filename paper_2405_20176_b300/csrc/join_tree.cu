@@ -260,9 +260,9 @@ __device__ __forceinline__ bool append_hits(WarpState<KMAX> &ws, int ws_off, uns
         const bool pa = v.x < tc, pb = v.y < tc;
         const unsigned ba = __ballot_sync(dev::kFull, pa);
         const unsigned bb = __ballot_sync(dev::kFull, pb);
-        if (pa) ws.tbuf[count + __popc(ba & lower)] = make_uint2(__float_as_uint(v.x), (L << 24) | ja);
+        if (pa) ws.tbuf[count + __popc(ba & lower)] = make_uint2(__float_as_uint(v.x), (L << 24) | (ja & 0xffffff));
         count += __popc(ba);
-        if (pb) ws.tbuf[count + __popc(bb & lower)] = make_uint2(__float_as_uint(v.y), (L << 24) | jb);
+        if (pb) ws.tbuf[count + __popc(bb & lower)] = make_uint2(__float_as_uint(v.y), (L << 24) | (jb & 0xffffff));
         count += __popc(bb);
         if (count > kTFlushAt) {
             changed |= flush_tuples<KMAX>(ws_off, count, k);
@@ -272,20 +272,25 @@ __device__ __forceinline__ bool append_hits(WarpState<KMAX> &ws, int ws_off, uns
     return changed;
 }
 
-// One step's candidates: rows c + lane and c + 32 + lane of a tile, four
-// float4 each, loaded straight from global memory (the population stays in L2).
+// One step's candidates in the pair-planar layout: lane l's 8 float4 hold
+// the 16 floats of rows a = 64s + l and b = 64s + 32 + l, feature pairs (a, b)
+// adjacent.  Loaded straight from global memory (the rows stay in L2).
 struct StepRows {
-    float4 a[4], b[4];
+    float4 r[8];
 };
 
-__device__ __forceinline__ void load_step(const float4 *__restrict__ x, int64_t base, int c, unsigned lane,
+__device__ __forceinline__ void load_step(const float4 *__restrict__ x, int64_t step, unsigned lane,
                                           StepRows &r)
 {
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        r.a[q] = __ldg(&x[(base / kTile * 4 + q) * kTile + c + lane]);
-        r.b[q] = __ldg(&x[(base / kTile * 4 + q) * kTile + c + 32 + lane]);
-    }
+    for (int q = 0; q < 8; ++q) r.r[q] = __ldg(&x[(step * 8 + q) * 32 + lane]);
+}
+
+// (a, b) pair of feature f.
+__device__ __forceinline__ float2 feat_pair(const StepRows &r, int f)
+{
+    const float4 v = r.r[f >> 1];
+    return (f & 1) ? make_float2(v.z, v.w) : make_float2(v.x, v.y);
 }
 
 template <int KMAX, int CW>
@@ -316,15 +321,15 @@ __global__ void __launch_bounds__(CW * 32, kCtasPerSm<CW>)
         const uint32_t high = ch->high;
         const uint32_t active = ch->active;
         float xq[16];
+        const float *xf = reinterpret_cast<const float *>(x);
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const float4 v = x[row_quad(i, q)];
-            xq[4 * q + 0] = v.x;
-            xq[4 * q + 1] = v.y;
-            xq[4 * q + 2] = v.z;
-            xq[4 * q + 3] = v.w;
-        }
+        for (int f = 0; f < 16; ++f) xq[f] = xf[pair_float(i, f)];
         const int orig_i = __float_as_int(xq[15]);  // the query's original index
+        if (orig_i < 0 || orig_i >= n) {
+            // rows that do not carry their index: report, write nothing
+            if (lane == 0) atomicOr(&ctrl->error, kErrBadRow);
+            continue;
+        }
         float2 nxq[15];
 #pragma unroll
         for (int f = 0; f < 15; ++f) nxq[f] = f2(-xq[f], -xq[f]);
@@ -357,36 +362,67 @@ __global__ void __launch_bounds__(CW * 32, kCtasPerSm<CW>)
             float T = ws.T[L];
             int cnt = 0;
             unsigned long long qs = 0;
-            float wgt[15];
-#pragma unroll
-            for (int f = 0; f < 15; ++f) wgt[f] = ((mask >> f) & 1u) ? 1.f : 0.f;
             const int64_t tbase = (int64_t)t0 * kTile;
             const int c_end = (int)std::min<int64_t>(kInit, n - tbase);
-            for (int c = 0; c < c_end; ++c) {
-                if (tbase + c == i) continue;
-                float xc[16];
+            // 64 candidates (one step) at a time: lane l loads its row pair (the
+            // next step in flight while this one is folded) and writes both rows,
+            // quad-planar, into a staging area in the still empty tuple buffer,
+            // from where every lane reads them
+            float4 *stg = reinterpret_cast<float4 *>(ws.tbuf);  // [4][64] float4
+            StepRows pre;
+            load_step(x, (int64_t)t0 * (kTile / 64), lane, pre);
+            for (int c0 = 0; c0 < c_end; c0 += 64) {
+                __syncwarp();
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
-                    const float4 v = __ldg(&x[((int64_t)t0 * 4 + q) * kTile + c]);
-                    xc[4 * q + 0] = v.x;
-                    xc[4 * q + 1] = v.y;
-                    xc[4 * q + 2] = v.z;
-                    xc[4 * q + 3] = v.w;
+                    const float4 lo = pre.r[2 * q], hi = pre.r[2 * q + 1];
+                    stg[q * 64 + lane] = make_float4(lo.x, lo.z, hi.x, hi.z);
+                    stg[q * 64 + 32 + lane] = make_float4(lo.y, lo.w, hi.y, hi.w);
                 }
-                float acc = 0.f;
+                __syncwarp();
+                if (c0 + 64 < c_end) load_step(x, (int64_t)t0 * (kTile / 64) + (c0 + 64) / 64, lane, pre);
+                const int cn = std::min(64, c_end - c0);
+                // four candidates at a time, so that their fold chains overlap
+                for (int u0 = 0; u0 < cn; u0 += 4) {
+                    float acc[4];
+                    int oc[4];
+                    bool use[4];
 #pragma unroll
-                for (int f = 14; f >= 0; --f) {
-                    const float dd = xc[f] - xq[f];
-                    acc = fmaf(dd * wgt[f], dd, acc);
+                    for (int e = 0; e < 4; ++e) {
+                        const int u = std::min(u0 + e, cn - 1);
+                        float xc[16];
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            const float4 v = stg[q * 64 + u];
+                            xc[4 * q + 0] = v.x;
+                            xc[4 * q + 1] = v.y;
+                            xc[4 * q + 2] = v.z;
+                            xc[4 * q + 3] = v.w;
+                        }
+                        // the canonical fold; a feature outside the subspace adds +0
+                        float a = 0.f;
+#pragma unroll
+                        for (int f = 14; f >= 0; --f) {
+                            const float dd = xc[f] - xq[f];
+                            a = fmaf(((mask >> f) & 1u) ? dd : 0.f, dd, a);
+                        }
+                        // the query itself and the slots past the end take no part
+                        use[e] = mine && u0 + e < cn && tbase + c0 + u0 + e != i;
+                        acc[e] = a;
+                        oc[e] = __float_as_int(xc[15]);
+                    }
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        if (use[e] && acc[e] <= e2) {
+                            ++cnt;
+                            qs += dev::eps_quant(acc[e], sc);
+                        }
+                        if (use[e] && (acc[e] < T || (acc[e] == T && oc[e] < ws.lj[L][k - 1])))
+                            T = dev::private_insert(ws.ld[L], ws.lj[L], k, acc[e], oc[e]);
+                    }
                 }
-                if (mine && acc <= e2) {
-                    ++cnt;
-                    qs += dev::eps_quant(acc, sc);
-                }
-                const int oc = __float_as_int(xc[15]);
-                if (mine && (acc < T || (acc == T && oc < ws.lj[L][k - 1])))
-                    T = dev::private_insert(ws.ld[L], ws.lj[L], k, acc, oc);
             }
+            __syncwarp();
             ws.T[L] = T;
             ws.cnt[L] = cnt;
             ws.esum[L] = qs;
@@ -401,43 +437,30 @@ __global__ void __launch_bounds__(CW * 32, kCtasPerSm<CW>)
         int tcount = 0;  // buffered event tuples (warp-uniform)
         const int n_steps = (n_tiles - 1) * (kTile / 64);
         StepRows cur, nxt;
-        if (n_steps > 0) load_step(x, (int64_t)((t0 + 1) % n_tiles) * kTile, 0, lane, cur);
+        constexpr int kSteps = kTile / 64;  // steps per tile
+        if (n_steps > 0) load_step(x, (int64_t)((t0 + 1) % n_tiles) * kSteps, lane, cur);
         for (int sidx = 0; sidx < n_steps; ++sidx) {
-            const int phys = (t0 + 1 + sidx / (kTile / 64)) % n_tiles;
-            const int c = (sidx % (kTile / 64)) * 64;
-            const int64_t base = (int64_t)phys * kTile;
+            const int phys = (t0 + 1 + sidx / kSteps) % n_tiles;
+            const int64_t step = (int64_t)phys * kSteps + sidx % kSteps;
             if (sidx + 1 < n_steps) {
-                const int nphys = (t0 + 1 + (sidx + 1) / (kTile / 64)) % n_tiles;
-                load_step(x, (int64_t)nphys * kTile, ((sidx + 1) % (kTile / 64)) * 64, lane, nxt);
+                const int nphys = (t0 + 1 + (sidx + 1) / kSteps) % n_tiles;
+                load_step(x, (int64_t)nphys * kSteps + (sidx + 1) % kSteps, lane, nxt);
             }
-            const int64_t ja = base + c + lane;
+            const int64_t ja = step * 64 + lane;
             const int64_t jb = ja + 32;
             float2 d[15];
-            int oa, ob;  // original indices of the two candidates
-            {
-                float xa[16], xb[16];
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    xa[4 * q + 0] = cur.a[q].x; xa[4 * q + 1] = cur.a[q].y;
-                    xa[4 * q + 2] = cur.a[q].z; xa[4 * q + 3] = cur.a[q].w;
-                    xb[4 * q + 0] = cur.b[q].x; xb[4 * q + 1] = cur.b[q].y;
-                    xb[4 * q + 2] = cur.b[q].z; xb[4 * q + 3] = cur.b[q].w;
+            for (int f = 0; f < 15; ++f) d[f] = __fadd2_rn(feat_pair(cur, f), nxq[f]);
+            // original indices of the two candidates
+            const int oa = __float_as_int(cur.r[7].z);
+            const int ob = __float_as_int(cur.r[7].w);
+            if ((i >> 6) == step) {
+                // the query itself is in this step: make it infinitely far
+#pragma unroll
+                for (int f = 0; f < 15; ++f) {
+                    if (ja == i) d[f].x = CUDART_INF_F;
+                    if (jb == i) d[f].y = CUDART_INF_F;
                 }
-                oa = __float_as_int(xa[15]);
-                ob = __float_as_int(xb[15]);
-                if (i >= base + c && i < base + c + 64) {
-                    // the query itself is in this step: make it infinitely far
-                    if (ja == i) {
-#pragma unroll
-                        for (int f = 0; f < 16; ++f) xa[f] = CUDART_INF_F;
-                    }
-                    if (jb == i) {
-#pragma unroll
-                        for (int f = 0; f < 16; ++f) xb[f] = CUDART_INF_F;
-                    }
-                }
-#pragma unroll
-                for (int f = 0; f < 15; ++f) d[f] = __fadd2_rn(f2(xa[f], xb[f]), nxq[f]);
             }
             cur = nxt;
             float2 v[kW];

@@ -202,25 +202,35 @@ __global__ void chunk_key_kernel(const float4 *__restrict__ x, int64_t n, int f,
     }
 }
 
-// out[g][p] <- x[perm[g * n + p]] (quad-planar, n_pad rows per chunk).
+// out[g] <- the rows x[perm[g * n + p]], p = 0..n_pad-1, in the pair-planar
+// layout (one thread per row pair a = 64s + l, b = a + 32); padding rows +inf.
 __global__ void gather_chunks_kernel(const float4 *__restrict__ x, const int32_t *__restrict__ perm,
                                      int64_t n, int64_t n_pad, int n_chunks, float4 *__restrict__ out)
 {
-    const int64_t total = n_pad * (int64_t)n_chunks;
+    const int64_t pairs = n_pad / 2;  // per chunk
+    const int64_t total = pairs * (int64_t)n_chunks;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
          e += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t g = e / n_pad;
-        const int64_t p = e - g * n_pad;
-        float4 *dst = out + g * n_pad * 4;
-        if (p < n) {
-            const int64_t o = perm[g * n + p];
+        const int64_t g = e / pairs;
+        const int64_t t = e - g * pairs;  // pair index: step t / 32, lane t % 32
+        const int64_t pa = (t >> 5) * 64 + (t & 31), pb = pa + 32;
+        float4 ra[4], rb[4];
+        const float inf = CUDART_INF_F;
+        const int64_t oa = pa < n ? (perm ? perm[g * n + pa] : pa) : -1;
+        const int64_t ob = pb < n ? (perm ? perm[g * n + pb] : pb) : -1;
 #pragma unroll
-            for (int q = 0; q < 4; ++q) dst[row_quad(p, q)] = x[row_quad(o, q)];
-        } else {
-            const float inf = CUDART_INF_F;
-#pragma unroll
-            for (int q = 0; q < 4; ++q) dst[row_quad(p, q)] = make_float4(inf, inf, inf, inf);
+        for (int q = 0; q < 4; ++q) {
+            ra[q] = oa >= 0 ? x[row_quad(oa, q)] : make_float4(inf, inf, inf, inf);
+            rb[q] = ob >= 0 ? x[row_quad(ob, q)] : make_float4(inf, inf, inf, inf);
         }
+        const float va[16] = {ra[0].x, ra[0].y, ra[0].z, ra[0].w, ra[1].x, ra[1].y, ra[1].z, ra[1].w,
+                              ra[2].x, ra[2].y, ra[2].z, ra[2].w, ra[3].x, ra[3].y, ra[3].z, ra[3].w};
+        const float vb[16] = {rb[0].x, rb[0].y, rb[0].z, rb[0].w, rb[1].x, rb[1].y, rb[1].z, rb[1].w,
+                              rb[2].x, rb[2].y, rb[2].z, rb[2].w, rb[3].x, rb[3].y, rb[3].z, rb[3].w};
+        float4 *dst = out + g * n_pad * 4;
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+            dst[pair_plane(pa, q)] = make_float4(va[2 * q], vb[2 * q], va[2 * q + 1], vb[2 * q + 1]);
     }
 }
 
@@ -472,7 +482,7 @@ snaps_status launch_chunk_keys(const float4 *x, int64_t n, int f, const TreeChun
 snaps_status launch_gather_chunks(const float4 *x, const int32_t *perm, int64_t n, int64_t n_pad,
                                   int n_chunks, float4 *out, cudaStream_t st)
 {
-    const int64_t total = n_pad * (int64_t)n_chunks;
+    const int64_t total = n_pad / 2 * (int64_t)n_chunks;
     const int64_t blocks = std::min<int64_t>((total + 255) / 256, 148 * 16);
     gather_chunks_kernel<<<(unsigned)blocks, 256, 0, st>>>(x, perm, n, n_pad, n_chunks, out);
     SNAPS_CHECK_CUDA(cudaGetLastError());

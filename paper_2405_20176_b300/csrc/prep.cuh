@@ -42,8 +42,8 @@ snaps_status launch_gather_rows(const float4 *src, const int32_t *perm, int64_t 
 snaps_status launch_chunk_keys(const float4 *x, int64_t n, int f, const TreeChunk *chunks, int n_chunks,
                                const KeyRange &kr, uint64_t *keys, int32_t *vals, cudaStream_t st);
 
-// out[g] (n_pad rows each) <- the rows of x in chunk g's sorted order perm[g * n ..];
-// padding rows are +inf.
+// out[g] (n_pad rows each, pair-planar layout) <- the rows of x in chunk g's
+// sorted order perm[g * n ..] (perm NULL: x's own order); padding rows are +inf.
 snaps_status launch_gather_chunks(const float4 *x, const int32_t *perm, int64_t n, int64_t n_pad,
                                   int n_chunks, float4 *out, cudaStream_t st);
 

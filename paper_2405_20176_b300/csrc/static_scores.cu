@@ -37,7 +37,8 @@ constexpr int kStaticMaxGroups = kStaticMaxMasks / 32;
 constexpr size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
 constexpr size_t kOffPop = 0;
 constexpr size_t kPopBytes = align256((size_t)kStaticMaxN * kRowFloats * sizeof(float));
-constexpr size_t kOffStats = kOffPop + kPopBytes;
+constexpr size_t kOffPair = kOffPop + kPopBytes;  // the rows again, pair-planar (tree join)
+constexpr size_t kOffStats = kOffPair + kPopBytes;
 constexpr size_t kOffBad = kOffStats + align256(sizeof(ColStats) * 16);
 constexpr size_t kOffCtrl = kOffBad + 256;
 constexpr size_t kOffChunks = kOffCtrl + align256(sizeof(DeviceControl));
@@ -130,6 +131,7 @@ extern "C" snaps_status snaps_scores_static(int device, const float *feat, int64
     }
     char *base = (char *)g_static_addr[device];
     float4 *pop = (float4 *)(base + kOffPop);
+    float4 *pair = (float4 *)(base + kOffPair);
     ColStats *stats = (ColStats *)(base + kOffStats);
     unsigned *bad = (unsigned *)(base + kOffBad);
     DeviceControl *ctrl = (DeviceControl *)(base + kOffCtrl);
@@ -204,11 +206,18 @@ extern "C" snaps_status snaps_scores_static(int device, const float *feat, int64
     if (h_bad) STATIC_FAIL(SNAPS_EINVAL, "features must be finite (NaN is allowed only with SNAPS_NAN_TO_MEAN)");
     JoinShape shape{pop, n, n_pad, k};
     JoinOut out{scores, nullptr, nullptr, nullptr};
-    SNAPS_TRY(launch_join_tree(shape, d_chunks, n_chunks, out, ctrl, st));
+    if (n_chunks > 0) {
+        // the tree join reads the rows in the pair-planar layout (one copy, input order)
+        SNAPS_TRY(launch_gather_chunks(pop, nullptr, n, n_pad, 1, pair, st));
+        JoinShape ts = shape;
+        ts.x = pair;
+        SNAPS_TRY(launch_join_tree(ts, d_chunks, n_chunks, out, ctrl, st));
+    }
     SNAPS_TRY(launch_join_lanemask(shape, d_groups, n_groups, out, ctrl, st));
     if (top) SNAPS_TRY(launch_top(scores, n, n_masks, top_n, top, st));
     SNAPS_CHECK_CUDA(cudaMemcpyAsync(&h_err, &ctrl->error, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
     SNAPS_CHECK_CUDA(cudaStreamSynchronize(st));
+    if (h_err & kErrBadRow) STATIC_FAIL(SNAPS_ECUDA, "a join kernel met rows without a valid original index (error word 0x%x)", h_err);
     if (h_err) STATIC_FAIL(SNAPS_ETIMEOUT, "a device-side wait gave up (error word 0x%x)", h_err);
     return SNAPS_OK;
 }
