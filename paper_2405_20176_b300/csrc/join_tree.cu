@@ -52,7 +52,7 @@ constexpr int kLB = kTreeLowBits;  // 5
 constexpr int kW = kTreeWidth;     // 32 subspaces per chunk
 constexpr int kTile = 256;
 constexpr int kInit = 256;         // candidates handled lane-per-subspace first (one tile)
-constexpr int kTBuf = 512;         // event tuples buffered per warp
+constexpr int kTBuf = 1024;        // event tuples buffered per warp
 constexpr int kTFlushAt = kTBuf - 64;  // a node appends at most 64 tuples
 constexpr int kFlushMin = 16;      // tuples that trigger an end-of-step flush
 
@@ -96,16 +96,19 @@ constexpr DfsTable make_dfs() {
     return t;
 }
 constexpr DfsTable kDfs = make_dfs();
+static_assert(kTBuf * 2 >= kW * 64, "the set-up transpose fits the tuple buffer");
+static_assert(kTBuf * ((1u << 20) + 1u) < (1ull << 32), "a flush's eps partial sums fit 32 bits");
 static_assert(kDfs.node[1] == 16 && kDfs.parent[kW / 2] > 0, "DFS order as expected");
 
 // Per consumer warp: the state of its query across the chunk's 32 subspaces.
 template <int KMAX>
 struct WarpState {
-    uint2 tbuf[512];                // pending events: (d2 bits, L << 24 | candidate)
+    uint2 tbuf[kTBuf];              // pending events: (d2 bits, L << 24 | candidate);
+                                    // during the set-up phase, the transpose buffer
     float ld[kW][KMAX + 1];         // kNN lists by L; +1 keeps both access patterns
     int lj[kW][KMAX + 1];           // free of bank conflicts
     unsigned long long esum[kW];    // exact quantised eps distance sums
-    unsigned epart[kW];             // this flush's partial sums (<= 512 terms of <= 2^20 + 1)
+    unsigned epart[kW];             // this flush's partial sums (<= kTBuf terms of <= 2^20 + 1)
     float T[kW];                    // current k-th squared distance
     float tc[kW];                   // pass threshold max(T, eps) by L
     int cnt[kW];                    // eps-neighbour counts
@@ -236,6 +239,26 @@ __device__ __forceinline__ void walk(float2 (&v)[kW], const float2 (&d)[15], con
     }
 }
 
+// The walk without thresholds (set-up phase): every node's two values go to
+// the transpose buffer as soon as they are folded -- row L (the node's
+// subspace), columns lane ^ L (candidate a) and 32 + (lane ^ L) (candidate b),
+// so that these stores and the row scans that follow touch 32 different banks.
+template <int P>
+__device__ __forceinline__ void fold_store(float2 (&v)[kW], const float2 (&d)[15], float *stg, unsigned lane)
+{
+    if constexpr (P < kW) {
+        if constexpr (P > 0) {
+            constexpr int b = kDfs.bit[P];
+            constexpr int par = kDfs.parent[P];
+            v[P] = __ffma2_rn(d[b], d[b], v[par]);
+        }
+        constexpr int L = kDfs.node[P];
+        stg[L * 64 + (lane ^ L)] = v[P].x;
+        stg[L * 64 + 32 + (lane ^ L)] = v[P].y;
+        fold_store<P + 1>(v, d, stg, lane);
+    }
+}
+
 // Append the tuples of the subspaces in `hit` (a warp-uniform mask): each
 // node's distances are recomputed from the root with the walk's own FFMA2
 // chain (the low features of L folded from the highest down), so they are
@@ -351,75 +374,55 @@ __global__ void __launch_bounds__(CW * 32, kCtasPerSm<CW>)
             ws.T[L] = (((active >> L) & 1u) && k > 0) ? CUDART_INF_F : -CUDART_INF_F;
         }
         __syncwarp();
-        // ---- set-up phase: lane L folds subspace L over the query's own tile and
-        // keeps a private sorted list ---------------------------------------------------
+        // The candidate stream: all steps of 64 rows, starting at the query's own
+        // tile (in the chunk's order, its neighbourhood) and wrapping around.
+        constexpr int kSteps = kTile / 64;  // steps per tile
+        const int64_t n_steps = (int64_t)n_tiles * kSteps;
+        const int64_t s0 = (int64_t)t0 * kSteps;
+        // ---- set-up phase: the first kInit candidates go straight into the
+        // lists.  The walk folds each step; its node values are transposed through
+        // the still empty tuple buffer so that lane L scans subspace L's 32 values
+        // per half-step, keeping its list and eps sums privately -------------------
         {
             const uint32_t L = lane;
             const bool mine = (active >> L) & 1u;
-            const uint32_t mask = (high << kLB) | L;
             const float e2 = ws.eps2[L];
             const float sc = ws.escale[L];
             float T = ws.T[L];
             int cnt = 0;
             unsigned long long qs = 0;
-            const int64_t tbase = (int64_t)t0 * kTile;
-            const int c_end = (int)std::min<int64_t>(kInit, n - tbase);
-            // 64 candidates (one step) at a time: lane l loads its row pair (the
-            // next step in flight while this one is folded) and writes both rows,
-            // quad-planar, into a staging area in the still empty tuple buffer,
-            // from where every lane reads them
-            float4 *stg = reinterpret_cast<float4 *>(ws.tbuf);  // [4][64] float4
-            StepRows pre;
-            load_step(x, (int64_t)t0 * (kTile / 64), lane, pre);
-            for (int c0 = 0; c0 < c_end; c0 += 64) {
+            float *stg = reinterpret_cast<float *>(ws.tbuf);  // [32][64], columns XOR-swizzled by row
+            const int64_t init_steps = std::min<int64_t>(kInit / 64, n_steps);
+            StepRows r;
+            load_step(x, s0 % n_steps, lane, r);
+            for (int64_t u = 0; u < init_steps; ++u) {
+                const int64_t step = (s0 + u) % n_steps;
+                float2 d[15];
+#pragma unroll
+                for (int f = 0; f < 15; ++f) d[f] = __fadd2_rn(feat_pair(r, f), nxq[f]);
+                const int oa = __float_as_int(r.r[7].z), ob = __float_as_int(r.r[7].w);
+                // the next step's rows load while this one is folded and scanned
+                if (u + 1 < init_steps) load_step(x, (s0 + u + 1) % n_steps, lane, r);
+                float2 v[kW];
+                v[0] = f2(0.f, 0.f);
+#pragma unroll
+                for (int f = 14; f >= kLB; --f)
+                    if ((high >> (f - kLB)) & 1u) v[0] = __ffma2_rn(d[f], d[f], v[0]);
                 __syncwarp();
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const float4 lo = pre.r[2 * q], hi = pre.r[2 * q + 1];
-                    stg[q * 64 + lane] = make_float4(lo.x, lo.z, hi.x, hi.z);
-                    stg[q * 64 + 32 + lane] = make_float4(lo.y, lo.w, hi.y, hi.w);
-                }
+                fold_store<0>(v, d, stg, lane);
                 __syncwarp();
-                if (c0 + 64 < c_end) load_step(x, (int64_t)t0 * (kTile / 64) + (c0 + 64) / 64, lane, pre);
-                const int cn = std::min(64, c_end - c0);
-                // four candidates at a time, so that their fold chains overlap
-                for (int u0 = 0; u0 < cn; u0 += 4) {
-                    float acc[4];
-                    int oc[4];
-                    bool use[4];
-#pragma unroll
-                    for (int e = 0; e < 4; ++e) {
-                        const int u = std::min(u0 + e, cn - 1);
-                        float xc[16];
-#pragma unroll
-                        for (int q = 0; q < 4; ++q) {
-                            const float4 v = stg[q * 64 + u];
-                            xc[4 * q + 0] = v.x;
-                            xc[4 * q + 1] = v.y;
-                            xc[4 * q + 2] = v.z;
-                            xc[4 * q + 3] = v.w;
-                        }
-                        // the canonical fold; a feature outside the subspace adds +0
-                        float a = 0.f;
-#pragma unroll
-                        for (int f = 14; f >= 0; --f) {
-                            const float dd = xc[f] - xq[f];
-                            a = fmaf(((mask >> f) & 1u) ? dd : 0.f, dd, a);
-                        }
-                        // the query itself and the slots past the end take no part
-                        use[e] = mine && u0 + e < cn && tbase + c0 + u0 + e != i;
-                        acc[e] = a;
-                        oc[e] = __float_as_int(xc[15]);
+                for (int c = 0; c < 64; ++c) {
+                    const float val = stg[L * 64 + (c ^ L)];
+                    const int oc = __shfl_sync(dev::kFull, c < 32 ? oa : ob, c & 31);
+                    const int64_t row = step * 64 + c;
+                    // the query itself and padding rows take no part
+                    const bool use = mine && row < n && row != i;
+                    if (use && val <= e2) {
+                        ++cnt;
+                        qs += dev::eps_quant(val, sc);
                     }
-#pragma unroll
-                    for (int e = 0; e < 4; ++e) {
-                        if (use[e] && acc[e] <= e2) {
-                            ++cnt;
-                            qs += dev::eps_quant(acc[e], sc);
-                        }
-                        if (use[e] && (acc[e] < T || (acc[e] == T && oc[e] < ws.lj[L][k - 1])))
-                            T = dev::private_insert(ws.ld[L], ws.lj[L], k, acc[e], oc[e]);
-                    }
+                    if (use && (val < T || (val == T && oc < ws.lj[L][k - 1])))
+                        T = dev::private_insert(ws.ld[L], ws.lj[L], k, val, oc);
                 }
             }
             __syncwarp();
@@ -432,20 +435,14 @@ __global__ void __launch_bounds__(CW * 32, kCtasPerSm<CW>)
         float Tc[kW];
         load_thresholds<0>(ws, Tc);
 
-        // ---- main loop: the other tiles, 64 candidates a step, the next step's rows
-        // loaded while this one is walked -----------------------------------------------
+        // ---- main loop: the rest of the stream, 64 candidates a step, the next
+        // step's rows loaded while this one is walked --------------------------------
         int tcount = 0;  // buffered event tuples (warp-uniform)
-        const int n_steps = (n_tiles - 1) * (kTile / 64);
-        StepRows cur, nxt;
-        constexpr int kSteps = kTile / 64;  // steps per tile
-        if (n_steps > 0) load_step(x, (int64_t)((t0 + 1) % n_tiles) * kSteps, lane, cur);
-        for (int sidx = 0; sidx < n_steps; ++sidx) {
-            const int phys = (t0 + 1 + sidx / kSteps) % n_tiles;
-            const int64_t step = (int64_t)phys * kSteps + sidx % kSteps;
-            if (sidx + 1 < n_steps) {
-                const int nphys = (t0 + 1 + (sidx + 1) / kSteps) % n_tiles;
-                load_step(x, (int64_t)nphys * kSteps + (sidx + 1) % kSteps, lane, nxt);
-            }
+        StepRows cur;
+        const int64_t init_steps = std::min<int64_t>(kInit / 64, n_steps);
+        if (init_steps < n_steps) load_step(x, (s0 + init_steps) % n_steps, lane, cur);
+        for (int64_t u = init_steps; u < n_steps; ++u) {
+            const int64_t step = (s0 + u) % n_steps;
             const int64_t ja = step * 64 + lane;
             const int64_t jb = ja + 32;
             float2 d[15];
@@ -462,7 +459,8 @@ __global__ void __launch_bounds__(CW * 32, kCtasPerSm<CW>)
                     if (jb == i) d[f].y = CUDART_INF_F;
                 }
             }
-            cur = nxt;
+            // the next step's rows load while this one is walked
+            if (u + 1 < n_steps) load_step(x, (s0 + u + 1) % n_steps, lane, cur);
             float2 v[kW];
             v[0] = f2(0.f, 0.f);
 #pragma unroll
