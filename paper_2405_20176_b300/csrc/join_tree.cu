@@ -9,34 +9,35 @@
 // (query, candidate) pair with 15 subtractions, <= 10 root FMAs and 31 tree
 // FMAs -- about one FMA per subspace instead of one per feature.
 //
-// Mapping: a consumer warp owns one query; each lane owns two candidates
-// (rows c+lane and c+32+lane of the staged tile), packed so that the f32x2
-// instructions (FADD2/FFMA2) process both.  The per-subspace thresholds are
-// warp-uniform.  The unrolled tree walk spends, per subspace, one FFMA2, two
-// compares and a warp vote on whether any lane's distance fell below
-// max(current k-th distance, eps); it votes on 8 subspaces before branching,
-// so their latencies overlap.  Only the lanes that passed then append a
-// (squared distance, subspace, candidate) tuple to the warp's buffer in
-// shared memory (a ballot prefix sum gives each its slot).  Once enough
-// tuples wait (or the buffer fills), a flush processes 32 tuples at a time
-// with every lane busy: eps counts and exact fixed-point distance sums by
-// shared-memory atomics, then kNN insertions, lanes holding different
-// subspaces inserting into their lists at the same time.
+// Mapping: a warp owns one work item, one query of one chunk, which it
+// claims from an atomic counter.  Each lane owns two candidates per step of
+// 64 rows, packed so that the f32x2 instructions (FADD2/FFMA2) process both;
+// the rows are read straight from global memory (the population stays in L2),
+// the next step's while the current one is walked.  The walk spends, per
+// subspace, one FFMA2 and two compares against the subspace's pass threshold,
+// max(current k-th distance, eps), which sits in shared memory (warp-uniform,
+// broadcast).  The step's 32 subspace votes end in one warp OR-reduction; on
+// the few steps where it is non-zero, an out-of-line handler recomputes the
+// triggered subspaces' distances and appends (squared distance, subspace,
+// candidate) tuples to the warp's buffer.  Once enough tuples wait (or the
+// buffer fills), a flush processes 32 tuples at a time with every lane busy:
+// eps counts and exact fixed-point distance sums by shared-memory atomics,
+// then kNN insertions, lanes holding different subspaces inserting into their
+// lists at the same time.
 //
-// Rows are stored in cell order (sorted by a 15-feature Morton key when the
-// population is indexed) and carry their original index in float 15; lists,
-// ties and outputs use original indices, so results do not depend on the
-// order.  A work item's candidate stream starts at the tile holding its
-// queries and wraps around: its first 256 candidates are the queries' own
-// neighbourhood, handled lane-per-subspace (each lane folds its own subspace
-// and keeps a private list), so the lists start full and the thresholds tight
-// instead of sending every early candidate to the flush.
+// Row order: each chunk gets its own copy of the rows, sorted by a Morton key
+// over the chunk's high features (the features all 32 of its subspaces share)
+// and stored pair-planar (common.cuh); every row carries its original index in
+// float 15, and lists, ties and outputs use original indices, so results do
+// not depend on the order.  A query's stream starts at its own tile -- its
+// neighbourhood in those features -- and wraps around.  The first 256
+// candidates (the set-up phase, out of line) go straight into the lists: the
+// walk's node values are transposed through shared memory so that lane L
+// scans subspace L's values and keeps its list privately.  The thresholds then
+// start tight instead of sending every early candidate to the flush.
 //
-// A producer warp streams candidate tiles with 1-D bulk copies (TMA) into a
-// ring of stages guarded by full / empty mbarriers, so consumer warps move at
-// their own pace; it also hands out work items (chunk x query block) from an
-// atomic counter, tagging every stage with the work item it belongs to.  Two
-// CTAs share an SM (k <= 16), each with its own stream and work items.
+// Two CTAs share an SM (16 warps with k <= 16), with no barriers between
+// warps: every warp streams at its own pace.
 
 #include <math_constants.h>
 
@@ -114,9 +115,11 @@ struct WarpState {
     int cnt[kW];                    // eps-neighbour counts
     float eps2[kW];                 // radii of this chunk
     float escale[kW];               // 2^20 / eps
+    float2 nxq[16];                 // the query's negated features, as (a, b) pairs
 };
 
-// Two CTAs of six warps share an SM: 12 warps, each with up to 170 registers.
+// Two CTAs share an SM: 2 x 8 warps (k <= 16, 128 registers a thread) or
+// 2 x 6 warps (k <= 32, whose lists need more shared memory; 168 registers).
 template <int CW>
 constexpr int kCtasPerSm = 2;
 
@@ -209,22 +212,11 @@ __device__ __noinline__ bool flush_tuples(int ws_off, int count, int k)
     return changed != 0u;
 }
 
-// Pass thresholds into registers, by DFS position.
-template <int P, int KMAX>
-__device__ __forceinline__ void load_thresholds(const WarpState<KMAX> &ws, float (&Tc)[kW])
-{
-    if constexpr (P < kW) {
-        constexpr int L = kDfs.node[P];
-        Tc[P] = ws.tc[L];
-        load_thresholds<P + 1>(ws, Tc);
-    }
-}
-
 // The walk: the 32 subspace distances of this lane's two candidates in DFS
 // order (one FFMA2 per node), and the set of subspaces L in which either
 // candidate fell below its pass threshold (bit L of `bits`).  No branches.
 template <int P>
-__device__ __forceinline__ void walk(float2 (&v)[kW], const float2 (&d)[15], const float (&Tc)[kW],
+__device__ __forceinline__ void walk(float2 (&v)[kW], const float2 (&d)[15], const float *tc,
                                      unsigned &bits)
 {
     if constexpr (P < kW) {
@@ -234,8 +226,9 @@ __device__ __forceinline__ void walk(float2 (&v)[kW], const float2 (&d)[15], con
             v[P] = __ffma2_rn(d[b], d[b], v[par]);
         }
         constexpr int L = kDfs.node[P];
-        bits |= ((v[P].x < Tc[P]) | (v[P].y < Tc[P])) ? (1u << L) : 0u;
-        walk<P + 1>(v, d, Tc, bits);
+        const float t = tc[L];
+        bits |= ((v[P].x < t) | (v[P].y < t)) ? (1u << L) : 0u;
+        walk<P + 1>(v, d, tc, bits);
     }
 }
 
@@ -259,17 +252,19 @@ __device__ __forceinline__ void fold_store(float2 (&v)[kW], const float2 (&d)[15
     }
 }
 
-// Append the tuples of the subspaces in `hit` (a warp-uniform mask): each
-// node's distances are recomputed from the root with the walk's own FFMA2
-// chain (the low features of L folded from the highest down), so they are
-// bit-identical to the walk's.  A nearly full buffer is flushed; returns true
-// when a flush changed a kNN list.
+// Append the kNN / eps tuples of the subspaces in `hit` (a warp-uniform
+// mask).  Each node's distances are recomputed from the root with the walk's
+// own FFMA2 chain (the low features of L folded from the highest down), so
+// they are bit-identical to the walk's.  A nearly full buffer is flushed.
+// Out of line: it runs on a minority of steps, and inlined its registers would
+// count against the walk's.  Returns the new tuple count.
 template <int KMAX>
-__device__ __forceinline__ bool append_hits(WarpState<KMAX> &ws, int ws_off, unsigned hit, float2 root,
-                                            const float2 (&d)[15], int &count, int ja, int jb, int k)
+__device__ __noinline__ int append_hits(int ws_off, unsigned hit, float2 root, float2 d0, float2 d1,
+                                        float2 d2, float2 d3, float2 d4, int count, int ja, int jb, int k)
 {
+    WarpState<KMAX> &ws = *reinterpret_cast<WarpState<KMAX> *>(tree_smem + ws_off);
+    const float2 d[5] = {d0, d1, d2, d3, d4};
     const unsigned lower = (1u << dev::lane_id()) - 1u;
-    bool changed = false;
     while (hit) {
         const int L = __ffs(hit) - 1;
         hit &= hit - 1;
@@ -288,11 +283,11 @@ __device__ __forceinline__ bool append_hits(WarpState<KMAX> &ws, int ws_off, uns
         if (pb) ws.tbuf[count + __popc(bb & lower)] = make_uint2(__float_as_uint(v.y), (L << 24) | (jb & 0xffffff));
         count += __popc(bb);
         if (count > kTFlushAt) {
-            changed |= flush_tuples<KMAX>(ws_off, count, k);
+            flush_tuples<KMAX>(ws_off, count, k);
             count = 0;
         }
     }
-    return changed;
+    return count;
 }
 
 // One step's candidates in the pair-planar layout: lane l's 8 float4 hold
@@ -302,7 +297,7 @@ struct StepRows {
     float4 r[8];
 };
 
-__device__ __forceinline__ void load_step(const float4 *__restrict__ x, int64_t step, unsigned lane,
+__device__ __forceinline__ void load_step(const float4 *__restrict__ x, int step, unsigned lane,
                                           StepRows &r)
 {
 #pragma unroll
@@ -314,6 +309,63 @@ __device__ __forceinline__ float2 feat_pair(const StepRows &r, int f)
 {
     const float4 v = r.r[f >> 1];
     return (f & 1) ? make_float2(v.z, v.w) : make_float2(v.x, v.y);
+}
+
+// Set-up phase (see the kernel), kept out of line so that its registers do
+// not add to the main loop's.
+template <int KMAX>
+__device__ __noinline__ void setup_phase(int ws_off, const float4 *__restrict__ x, int64_t i, int64_t n,
+                                         uint32_t high, uint32_t active, int64_t s0, int64_t n_steps, int k)
+{
+    WarpState<KMAX> &ws = *reinterpret_cast<WarpState<KMAX> *>(tree_smem + ws_off);
+    const unsigned lane = dev::lane_id();
+    const float2 *nxq = ws.nxq;
+    const uint32_t L = lane;
+    const bool mine = (active >> L) & 1u;
+    const float e2 = ws.eps2[L];
+    const float sc = ws.escale[L];
+    float T = ws.T[L];
+    int cnt = 0;
+    unsigned long long qs = 0;
+    float *stg = reinterpret_cast<float *>(ws.tbuf);  // [32][64], columns XOR-swizzled by row
+    const int64_t init_steps = std::min<int64_t>(kInit / 64, n_steps);
+    StepRows r;
+    load_step(x, s0 % n_steps, lane, r);
+    for (int64_t u = 0; u < init_steps; ++u) {
+        const int64_t step = (s0 + u) % n_steps;
+        float2 d[15];
+#pragma unroll
+        for (int f = 0; f < 15; ++f) d[f] = __fadd2_rn(feat_pair(r, f), nxq[f]);
+        const int oa = __float_as_int(r.r[7].z), ob = __float_as_int(r.r[7].w);
+        // the next step's rows load while this one is folded and scanned
+        if (u + 1 < init_steps) load_step(x, (s0 + u + 1) % n_steps, lane, r);
+        float2 v[kW];
+        v[0] = f2(0.f, 0.f);
+#pragma unroll
+        for (int f = 14; f >= kLB; --f)
+            if ((high >> (f - kLB)) & 1u) v[0] = __ffma2_rn(d[f], d[f], v[0]);
+        __syncwarp();
+        fold_store<0>(v, d, stg, lane);
+        __syncwarp();
+        for (int c = 0; c < 64; ++c) {
+            const float val = stg[L * 64 + (c ^ L)];
+            const int oc = __shfl_sync(dev::kFull, c < 32 ? oa : ob, c & 31);
+            const int64_t row = step * 64 + c;
+            // the query itself and padding rows take no part
+            const bool use = mine && row < n && row != i;
+            if (use && val <= e2) {
+                ++cnt;
+                qs += dev::eps_quant(val, sc);
+            }
+            if (use && (val < T || (val == T && oc < ws.lj[L][k - 1])))
+                T = dev::private_insert(ws.ld[L], ws.lj[L], k, val, oc);
+        }
+    }
+    __syncwarp();
+    ws.T[L] = T;
+    ws.cnt[L] = cnt;
+    ws.esum[L] = qs;
+    ws.tc[L] = mine ? fmaxf(next_up(T), eps_up(e2)) : -CUDART_INF_F;
 }
 
 template <int KMAX, int CW>
@@ -340,7 +392,7 @@ __global__ void __launch_bounds__(CW * 32, kCtasPerSm<CW>)
         const TreeChunk *ch = &chunks[w / n];
         // the chunk's rows (in the chunk's own order when each chunk has a copy)
         const float4 *__restrict__ x = s.x + (w / n) * s.chunk_stride;
-        const int64_t i = w % n;  // the query's row in that order
+        const int i = (int)(w % n);  // the query's row in that order (n <= 2^24)
         const uint32_t high = ch->high;
         const uint32_t active = ch->active;
         float xq[16];
@@ -353,9 +405,9 @@ __global__ void __launch_bounds__(CW * 32, kCtasPerSm<CW>)
             if (lane == 0) atomicOr(&ctrl->error, kErrBadRow);
             continue;
         }
-        float2 nxq[15];
-#pragma unroll
-        for (int f = 0; f < 15; ++f) nxq[f] = f2(-xq[f], -xq[f]);
+        if (lane < 15) ws.nxq[lane] = f2(-xq[lane], -xq[lane]);
+        __syncwarp();
+        const float2 *nxq = ws.nxq;
         // the candidate stream starts at the query's own tile (in cell order, its
         // neighbourhood) and wraps around
         const int t0 = (int)(i / kTile);
@@ -377,74 +429,21 @@ __global__ void __launch_bounds__(CW * 32, kCtasPerSm<CW>)
         // The candidate stream: all steps of 64 rows, starting at the query's own
         // tile (in the chunk's order, its neighbourhood) and wrapping around.
         constexpr int kSteps = kTile / 64;  // steps per tile
-        const int64_t n_steps = (int64_t)n_tiles * kSteps;
-        const int64_t s0 = (int64_t)t0 * kSteps;
-        // ---- set-up phase: the first kInit candidates go straight into the
-        // lists.  The walk folds each step; its node values are transposed through
-        // the still empty tuple buffer so that lane L scans subspace L's 32 values
-        // per half-step, keeping its list and eps sums privately -------------------
-        {
-            const uint32_t L = lane;
-            const bool mine = (active >> L) & 1u;
-            const float e2 = ws.eps2[L];
-            const float sc = ws.escale[L];
-            float T = ws.T[L];
-            int cnt = 0;
-            unsigned long long qs = 0;
-            float *stg = reinterpret_cast<float *>(ws.tbuf);  // [32][64], columns XOR-swizzled by row
-            const int64_t init_steps = std::min<int64_t>(kInit / 64, n_steps);
-            StepRows r;
-            load_step(x, s0 % n_steps, lane, r);
-            for (int64_t u = 0; u < init_steps; ++u) {
-                const int64_t step = (s0 + u) % n_steps;
-                float2 d[15];
-#pragma unroll
-                for (int f = 0; f < 15; ++f) d[f] = __fadd2_rn(feat_pair(r, f), nxq[f]);
-                const int oa = __float_as_int(r.r[7].z), ob = __float_as_int(r.r[7].w);
-                // the next step's rows load while this one is folded and scanned
-                if (u + 1 < init_steps) load_step(x, (s0 + u + 1) % n_steps, lane, r);
-                float2 v[kW];
-                v[0] = f2(0.f, 0.f);
-#pragma unroll
-                for (int f = 14; f >= kLB; --f)
-                    if ((high >> (f - kLB)) & 1u) v[0] = __ffma2_rn(d[f], d[f], v[0]);
-                __syncwarp();
-                fold_store<0>(v, d, stg, lane);
-                __syncwarp();
-                for (int c = 0; c < 64; ++c) {
-                    const float val = stg[L * 64 + (c ^ L)];
-                    const int oc = __shfl_sync(dev::kFull, c < 32 ? oa : ob, c & 31);
-                    const int64_t row = step * 64 + c;
-                    // the query itself and padding rows take no part
-                    const bool use = mine && row < n && row != i;
-                    if (use && val <= e2) {
-                        ++cnt;
-                        qs += dev::eps_quant(val, sc);
-                    }
-                    if (use && (val < T || (val == T && oc < ws.lj[L][k - 1])))
-                        T = dev::private_insert(ws.ld[L], ws.lj[L], k, val, oc);
-                }
-            }
-            __syncwarp();
-            ws.T[L] = T;
-            ws.cnt[L] = cnt;
-            ws.esum[L] = qs;
-            ws.tc[L] = mine ? fmaxf(next_up(T), eps_up(e2)) : -CUDART_INF_F;
-        }
+        const int n_steps = n_tiles * kSteps;
+        const int s0 = t0 * kSteps;
+        setup_phase<KMAX>(ws_off, x, i, n, high, active, s0, n_steps, k);
         __syncwarp();
-        float Tc[kW];
-        load_thresholds<0>(ws, Tc);
 
         // ---- main loop: the rest of the stream, 64 candidates a step, the next
         // step's rows loaded while this one is walked --------------------------------
         int tcount = 0;  // buffered event tuples (warp-uniform)
         StepRows cur;
-        const int64_t init_steps = std::min<int64_t>(kInit / 64, n_steps);
+        const int init_steps = std::min(kInit / 64, n_steps);
         if (init_steps < n_steps) load_step(x, (s0 + init_steps) % n_steps, lane, cur);
-        for (int64_t u = init_steps; u < n_steps; ++u) {
-            const int64_t step = (s0 + u) % n_steps;
-            const int64_t ja = step * 64 + lane;
-            const int64_t jb = ja + 32;
+        for (int u = init_steps; u < n_steps; ++u) {
+            const int step = (s0 + u) % n_steps;
+            const int ja = step * 64 + (int)lane;
+            const int jb = ja + 32;
             float2 d[15];
 #pragma unroll
             for (int f = 0; f < 15; ++f) d[f] = __fadd2_rn(feat_pair(cur, f), nxq[f]);
@@ -459,25 +458,24 @@ __global__ void __launch_bounds__(CW * 32, kCtasPerSm<CW>)
                     if (jb == i) d[f].y = CUDART_INF_F;
                 }
             }
-            // the next step's rows load while this one is walked
-            if (u + 1 < n_steps) load_step(x, (s0 + u + 1) % n_steps, lane, cur);
             float2 v[kW];
             v[0] = f2(0.f, 0.f);
 #pragma unroll
             for (int f = 14; f >= kLB; --f)
                 if ((high >> (f - kLB)) & 1u) v[0] = __ffma2_rn(d[f], d[f], v[0]);
+            // the next step's rows load while this one is walked
+            if (u + 1 < n_steps) load_step(x, (s0 + u + 1) % n_steps, lane, cur);
             unsigned bits = 0u;
-            walk<0>(v, d, Tc, bits);
+            walk<0>(v, d, ws.tc, bits);
             const unsigned hit = __reduce_or_sync(dev::kFull, bits);
             if (hit) {
-                bool changed = append_hits<KMAX>(ws, ws_off, hit, v[0], d, tcount, oa, ob, k);
+                tcount = append_hits<KMAX>(ws_off, hit, v[0], d[0], d[1], d[2], d[3], d[4], tcount, oa, ob, k);
                 // flushing once a batch is waiting keeps the kNN thresholds fresh
                 // without paying a flush per step
                 if (tcount >= kFlushMin) {
-                    changed |= flush_tuples<KMAX>(ws_off, tcount, k);
+                    flush_tuples<KMAX>(ws_off, tcount, k);
                     tcount = 0;
                 }
-                if (changed) load_thresholds<0>(ws, Tc);
             }
         }
         if (tcount > 0) flush_tuples<KMAX>(ws_off, tcount, k);
@@ -539,7 +537,7 @@ snaps_status launch_join_tree(const JoinShape &s, const TreeChunk *chunks, int n
                               const JoinOut &o, DeviceControl *ctrl, cudaStream_t st)
 {
     if (n_chunks <= 0) return SNAPS_OK;
-    if (s.k <= 16) return launch_tree<16, 6>(s, chunks, n_chunks, o, ctrl, st);
+    if (s.k <= 16) return launch_tree<16, 8>(s, chunks, n_chunks, o, ctrl, st);
     return launch_tree<32, 6>(s, chunks, n_chunks, o, ctrl, st);
 }
 
