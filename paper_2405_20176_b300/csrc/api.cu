@@ -285,11 +285,18 @@ Plan make_plan(const JobSpec &j)
 {
     Plan pl;
     if (j.precision == SNAPS_TC_F16) {
-        // the tensor-core join takes any subspaces, 64 at a time
+        // the tensor-core join takes any subspaces, 128 at a time; sorted by
+        // dimension, so that the threads of a warp see similar hit rates
+        std::vector<int> order(j.n_masks);
+        for (int m = 0; m < j.n_masks; ++m) order[m] = m;
+        std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+            const int da = popc16(j.masks[a]), db = popc16(j.masks[b]);
+            return da != db ? da < db : j.masks[a] < j.masks[b];
+        });
         for (int b = 0; b < j.n_masks; b += kTcBlockWidth) {
             TcBlock blk{};
             for (int c = 0; c < kTcBlockWidth; ++c) {
-                const int m = b + c;
+                const int m = b + c < j.n_masks ? order[b + c] : j.n_masks;
                 if (m < j.n_masks) {
                     blk.mask[c] = j.masks[m];
                     blk.eps2[c] = !j.want_eps ? -1.f

@@ -28,9 +28,9 @@ struct TreeChunk {
     int32_t slot[kTreeWidth];
 };
 
-// Up to 64 subspaces of any kind, as scheduled for the tensor-core join.  An
-// unused entry has mask 0.
-constexpr int kTcBlockWidth = 64;
+// Up to 256 subspaces of any kind, as scheduled for the tensor-core join (two
+// MMAs of M = 128 share each B operand).  An unused entry has mask 0.
+constexpr int kTcBlockWidth = 256;
 struct TcBlock {
     uint32_t mask[kTcBlockWidth];
     float eps2[kTcBlockWidth];

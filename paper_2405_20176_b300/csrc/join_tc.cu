@@ -4,30 +4,52 @@
 // on the 5th-generation tensor cores (tcgen05, kind::f16, FP32 accumulators
 // in tensor memory).
 //
-// For one query i and a tile of 256 candidates j, the A operand holds, per
-// candidate, the 15 squared differences (x_j - x_i)^2 rounded to FP16 and a
-// constant 1; the B operand holds, per subspace S, its 15 mask bits and minus
-// its filter threshold.  So one MMA row gives, for every subspace,
-//     D[j][S] ~= sum_{f in S} (x_jf - x_if)^2 - Tf_S,
-// and D < 0 marks the candidates that may lie within eps or below the current
-// k-th distance.  Tf_S = max(k-th squared distance, eps^2) * (1 + 2^-8) +
-// 2^-20, rounded up to FP16: the FP16 rounding of the squared differences is
-// <= 2^-11 relative + 2^-25 absolute per term, and the FP32 accumulation adds
-// far less, so no true neighbour is lost.  Every candidate that passes is
-// recomputed exactly with the library's canonical FP32 fold, and only exact
-// results decide counts, sums and kNN lists -- the results are identical to
-// the plain FP32 path.
+// The contraction.  For a query i and 128 candidates j, the B operand holds
+// per candidate the 15 squared differences (x_j - x_i)^2 rounded to FP16 and
+// a constant 1; the A operand holds per subspace S its 15 mask bits and minus
+// its filter threshold.  One MMA (M = 128 subspaces, N = 128 candidates,
+// K = 16) gives in tensor memory
+//     D[S][j] ~= sum_{f in S} (x_jf - x_if)^2 - Tf_S,
+// and D < 0 marks the candidates that may lie within eps of the query or
+// below the current k-th distance.  Tf_S = max(k-th squared distance, eps^2)
+// * (1 + 2^-8) + 2^-20, rounded up to FP16: the FP16 rounding of a squared
+// difference is <= 2^-11 relative (2^-25 absolute below FP16's normal range)
+// and the FP32 accumulation of 16 exact products adds far less, so no true
+// neighbour is lost.  Every candidate that passes is recomputed with the
+// library's canonical FP32 fold (FMAs from the highest feature down), and only
+// that exact value decides counts, sums and kNN lists: the results are the
+// plain FP32 path's, bit for bit.
 //
-// Layout: a CTA (4 warps, one warpgroup) owns a block of 64 subspaces and a
-// query block; it handles one query at a time.  Per candidate tile it builds
-// A (256 rows, two 128-row MMAs) in shared memory, one thread issues the two
-// MMAs into two 64-column TMEM regions and commits to an mbarrier, and each
-// warp reads its 32 rows of both regions with tcgen05.ld.  Two subspaces are
-// voted on at once by OR-ing the sign bits of four accumulators.  Survivors
-// of the exact tests become (d2, subspace, candidate) tuples; the kNN lists
-// and the B thresholds are updated once per tile.  Populations whose features
-// span more than a unit range are rejected by the host (their squared
-// differences could overflow FP16).
+// Mapping.  A CTA owns work items of one query x 256 subspaces (two 128-row A
+// operands).  Its 8 consumer warps are the subspace threads: thread s reads
+// row s % 128 of the accumulator of half s / 128 -- warp w reaches
+// tensor-memory lanes 32 (w % 4) .. 32 (w % 4) + 31 -- and keeps that
+// subspace's eps count, exact distance sum and kNN list privately, so events
+// need no atomics, locks or buffers.  One producer warp issues the bulk copies
+// (TMA) of 256-row candidate tiles into a ring and, per sub-tile of 128
+// candidates, the two MMAs into one of two accumulator sets (2 x 128 columns
+// each, 512 in all).  The warps meet only at mbarriers: consumers build a
+// sub-tile's B rows (half a row each) and arrive on `b_ready`; the producer
+// waits for that and for `t_empty` (the accumulator set it will overwrite has
+// been read), issues the MMAs and commits them to `mma_done`; consumers wait
+// for `mma_done`, filter -- 32 accumulators OR-ed into one sign test --
+// recompute and decide the survivors, write tightened thresholds into the A
+// copy that batch used (its next reader is issued only after they arrive on
+// `t_empty`), and arrive.  Subspaces arrive sorted by dimension, so the
+// threads of a warp see similar hit rates.
+//
+// kNN lists are kept unsorted with their largest entry tracked: a better
+// candidate overwrites that entry and the k entries are rescanned (k
+// independent loads instead of a dependent shift chain); each list is sorted
+// once, when its query's results are written.
+//
+// Start-up: the 32 rows around the query (in the stored cell order) are
+// staged in shared memory and folded exactly first, so the thresholds start
+// finite; the stream skips them.  Every wait is bounded and also gives up
+// when another warp has raised the CTA's abort flag; the CTA then sets the
+// error word, waits for its copies and MMAs in flight, frees its tensor
+// memory and leaves.  Populations whose features span more than a unit range
+// are rejected by the host (their squared differences could overflow FP16).
 
 #include <cuda_fp16.h>
 #include <math_constants.h>
@@ -40,50 +62,45 @@
 namespace snaps {
 namespace {
 
-constexpr int kNB = kTcBlockWidth;  // 64 subspaces per block
-constexpr int kTcWarps = 4;
-constexpr int kTile = 256;
-constexpr int kTcStages = 2;
-constexpr int kTcInit = 256;         // candidates of tile 0 handled subspace-per-thread first
-constexpr int kTcTBuf = 512;         // kNN tuples per warp between flushes (a column pair adds <= 128)
-constexpr int kTcFlushAt = kTcTBuf - 128;
-constexpr unsigned kLockSpin = 1u << 22;  // bound on waiting for the list lock
-constexpr uint32_t kLBO = 128;       // K-direction step between 8x16-byte core matrices
-constexpr uint32_t kSBO = 256;       // row-direction step
-constexpr uint32_t kTmemCols = 128;  // two 64-column accumulator regions
-constexpr int kTcQueries = 4;        // queries per work item
+constexpr int kNS = kTcBlockWidth;       // 256 subspaces per block (one query)
+constexpr int kM = 128;                  // MMA M: subspaces per A operand
+constexpr int kHalves = kNS / kM;        // 2
+constexpr int kNC = 128;                 // candidates per sub-tile = MMA N
+constexpr int kConsumers = kNS;          // 256: thread s
+constexpr int kProducerWarp = kConsumers / 32;
+constexpr int kCtaThreads = kConsumers + 32;
+constexpr int kTile = 256;               // rows per staged tile (one 16 KB bulk copy)
+constexpr int kSubPerTile = kTile / kNC; // 2
+constexpr int kStages = 6;               // ring depth in tiles
+constexpr int kWarm = 32;                // rows folded exactly before the filter starts
+constexpr uint32_t kLBO = 128;           // K-direction step between 8x16-byte core matrices
+constexpr uint32_t kSBO = 256;           // row-direction step
+constexpr uint32_t kTmemCols = 2 * kHalves * kNC;  // 512: two accumulator sets
+static_assert(kHalves == 2 && kTmemCols == 512, "one CTA holds all of an SM's tensor memory");
+static_assert(kNC * 2 == kConsumers, "every consumer builds half of one B row");
+static_assert(kRowPad % kTile == 0, "padded rows must cover whole tiles");
 
 template <int KMAX>
 struct TcSmem {
-    float4 tile[kTcStages][kTile * 4];           // 32 KB candidate tiles (quad-planar)
-    alignas(1024) unsigned char A[2][4096];      // two 128-row A operands, K-major, no swizzle
-    alignas(1024) unsigned char B[2048];         // 64-row B operand
-    uint2 tbuf[kTcWarps][kTcTBuf];               // event tuples per warp
-    float ld[kNB][KMAX + 1];                     // kNN lists by subspace
-    int lj[kNB][KMAX + 1];
-    unsigned long long esum[kNB];
-    unsigned epart[kNB];
-    float T[kNB];
-    float eps2[kNB];
-    float escale[kNB];
-    int cnt[kNB];
-    uint32_t mask[kNB];
-    int slot[kNB];
-    int tcount[kTcWarps];
-    int changed;
-    int lock;                                    // serialises kNN list updates across warps
-    uint64_t full[kTcStages];
-    uint64_t mma_bar;
+    float4 ring[kStages][kTile * 4];                   // candidate tiles (quad-planar)
+    alignas(1024) unsigned char A[2][kHalves][kM * 32]; // FP16 128 x 16, K-major
+    alignas(1024) unsigned char B[2][kNC * 32];         // FP16 128 x 16, K-major
+    float ld[KMAX][kConsumers];                         // kNN lists, entry-major: private
+    int lj[KMAX][kConsumers];                           // to a thread, distinct banks
+    float4 warm[4][kWarm];                              // start-up rows, quad-planar
+    float4 xq[4];                                       // the item's query row
+    uint64_t full[kStages];                             // tile landed
+    uint64_t b_ready[2];                                // B rows written (8 warp arrivals)
+    uint64_t t_empty[2];                                // accumulators read (8 warp arrivals)
+    uint64_t mma_done[2];                               // MMA batch complete (commit)
+    uint64_t cbar;                                      // consumer-only barrier (8 warps)
     uint32_t tmem_base;
-    long long work;
+    int abort;
 };
 
-__device__ __forceinline__ float eps_up(float e2) {
-    return e2 >= 0.f ? __uint_as_float(__float_as_uint(e2) + 1u) : -CUDART_INF_F;
-}
-
 // Smem matrix descriptor: K-major, no swizzle, version 1 (sm_100 family).
-__device__ __forceinline__ uint64_t smem_desc(const void *p) {
+__device__ __forceinline__ uint64_t smem_desc(const void *p)
+{
     const uint32_t a = dev::smem_addr(p);
     uint64_t d = (uint64_t)((a >> 4) & 0x3FFFu);
     d |= (uint64_t)((kLBO >> 4) & 0x3FFFu) << 16;
@@ -93,18 +110,42 @@ __device__ __forceinline__ uint64_t smem_desc(const void *p) {
 }
 
 // Byte offset of element (r, k) in a K-major 16-column FP16 operand.
-__device__ __forceinline__ uint32_t op_off(int r, int k) {
+__device__ __forceinline__ uint32_t op_off(int r, int k)
+{
     return (uint32_t)((r >> 3) * kSBO + (k >> 3) * kLBO + (r & 7) * 16 + (k & 7) * 2);
 }
 
-// B row 15 entry for subspace c: minus its conservative FP16 filter threshold.
-__device__ __forceinline__ __half neg_filter(float tc) {
-    if (!(tc >= 0.f)) return __float2half(1.f);  // inactive subspace: D = +1 > 0 for real rows
-    const float t = fminf(tc * (1.f + 0.00390625f) + 9.5367431640625e-07f, 65504.f);
-    return __hneg(__float2half_ru(t));
+// A row entry 15 for a subspace: minus its conservative FP16 filter threshold.
+__device__ __forceinline__ __half neg_filter(float t)
+{
+    if (!(t >= 0.f)) return __float2half(1.f);  // nothing to find: D >= +1 - 1 * 0 on real rows
+    const float f = fminf(t * (1.f + 0.00390625f) + 9.5367431640625e-07f, 65504.f);
+    return __hneg(__float2half_ru(f));
 }
 
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+__device__ __forceinline__ float eps_floor(float e2) { return e2 >= 0.f ? e2 : -CUDART_INF_F; }
+
+// Bounded mbarrier wait that also gives up once the CTA's abort flag is set.
+__device__ __forceinline__ bool wait_or_abort(uint64_t *bar, unsigned parity, const int *abort)
+{
+    const uint32_t addr = dev::smem_addr(bar);
+    for (unsigned it = 0; it < dev::kSpinLimit; ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(addr), "r"(parity)
+            : "memory");
+        if (done) return true;
+        if ((it & 63u) == 63u && *(volatile const int *)abort) return false;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32])
+{
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
         "%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
@@ -116,138 +157,127 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
         : "r"(taddr));
 }
 
-// Canonical FP32 squared distance of subspace `mask` (highest feature first).
-__device__ __forceinline__ float fold_exact(const float (&xq)[16], const float4 *tile, int row,
-                                            uint32_t mask)
+// Canonical FP32 squared distance of subspace `mask` to the candidate at
+// `base[p * stride + row]` (quad-planar): FMAs over the squared differences
+// from the highest feature down, starting from +0.  Branch-free: a feature
+// outside the subspace adds (0 * d) * d = +-0, which leaves the sum unchanged.
+__device__ __forceinline__ float fold_exact(const float4 *xq, const float4 *base, int stride, int row,
+                                            uint32_t mask, int &orig)
 {
-    float xc[16];
+    float xc[16], xo[16];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        const float4 v = tile[q * kTile + row];
-        xc[4 * q + 0] = v.x;
-        xc[4 * q + 1] = v.y;
-        xc[4 * q + 2] = v.z;
-        xc[4 * q + 3] = v.w;
+    for (int p = 0; p < 4; ++p) {
+        const float4 t = base[p * stride + row];
+        const float4 u = xq[p];
+        xc[4 * p + 0] = t.x;
+        xc[4 * p + 1] = t.y;
+        xc[4 * p + 2] = t.z;
+        xc[4 * p + 3] = t.w;
+        xo[4 * p + 0] = u.x;
+        xo[4 * p + 1] = u.y;
+        xo[4 * p + 2] = u.z;
+        xo[4 * p + 3] = u.w;
     }
+    orig = __float_as_int(xc[15]);
     float acc = 0.f;
 #pragma unroll
     for (int f = 14; f >= 0; --f) {
-        const float d = xc[f] - xq[f];
-        acc = fmaf(d * (((mask >> f) & 1u) ? 1.f : 0.f), d, acc);
+        const float d = xc[f] - xo[f];
+        acc = fmaf(((mask >> f) & 1u) ? d : 0.f, d, acc);
     }
     return acc;
 }
 
-// Append the (d2, column, candidate) tuples of the lanes flagged in `p`.
-__device__ __forceinline__ void append(uint2 *buf, int &count, bool p, float d2, int col, int j)
-{
-    const unsigned b = __ballot_sync(dev::kFull, p);
-    if (p) buf[count + __popc(b & ((1u << dev::lane_id()) - 1u))] =
-        make_uint2(__float_as_uint(d2), ((unsigned)col << 24) | (unsigned)j);
-    count += __popc(b);
-}
+// A thread's kNN list: k entries (squared distance, original index) in shared
+// memory, unsorted, with its largest entry by (distance, index) tracked in
+// registers.  Unused entries are (+inf, INT_MAX).
+struct KnnMax {
+    float T;   // largest distance: the k-th nearest so far (+inf until k entries)
+    int Tj;    // its index
+    int Tp;    // its position
+};
 
-// Insert one warp's buffered kNN candidates (d2, subspace, candidate) into
-// the sorted lists: warp-cooperative, one candidate at a time, by (distance,
-// index) -- candidates arrive out of index order across warps.  The caller
-// holds the list lock.
+// One candidate's exact decisions for thread `tid`'s subspace: eps count and
+// quantised distance sum, then, when it beats the list's largest entry by
+// (distance, index), it takes that entry's place and the new largest is found.
 template <int KMAX>
-__device__ void tc_flush(TcSmem<KMAX> &sm, const uint2 *buf, int count, int k)
+__device__ __forceinline__ void decide(TcSmem<KMAX> &sm, int tid, int k, float d2, int oj, float e2,
+                                       float esc, int &cnt, unsigned long long &qs, KnnMax &m)
 {
-    const unsigned lane = dev::lane_id();
-    for (int b = 0; b < count; b += 32) {
-        const int idx = b + (int)lane;
-        const bool ok = idx < count;
-        const uint2 t = ok ? buf[idx] : make_uint2(0x7f800000u, 0u);
-        const int c = (int)(t.y >> 24);
-        const int j = (int)(t.y & 0xffffffu);
-        const float d2 = __uint_as_float(t.x);
-        unsigned kb = __ballot_sync(dev::kFull, ok && d2 <= sm.T[c]);
-        while (kb) {
-            const int src = __ffs(kb) - 1;
-            kb &= kb - 1;
-            const int cs = __shfl_sync(dev::kFull, c, src);
-            const float ds = __shfl_sync(dev::kFull, d2, src);
-            const int js = __shfl_sync(dev::kFull, j, src);
-            float T = sm.T[cs];
-            if (!(ds < T || (ds == T && js < sm.lj[cs][k - 1]))) continue;
-            float my_d = lane < (unsigned)k ? sm.ld[cs][lane] : CUDART_INF_F;
-            int my_j = lane < (unsigned)k ? sm.lj[cs][lane] : 0x7fffffff;
-            const bool before = lane < (unsigned)k && (my_d < ds || (my_d == ds && my_j < js));
-            const int pos = __popc(__ballot_sync(dev::kFull, before));
-            const float up_d = __shfl_up_sync(dev::kFull, my_d, 1);
-            const int up_j = __shfl_up_sync(dev::kFull, my_j, 1);
-            if (lane == (unsigned)pos) {
-                my_d = ds;
-                my_j = js;
-            } else if (lane > (unsigned)pos && lane < (unsigned)k) {
-                my_d = up_d;
-                my_j = up_j;
-            }
-            T = __shfl_sync(dev::kFull, my_d, k - 1);
-            if (lane < (unsigned)k) {
-                sm.ld[cs][lane] = my_d;
-                sm.lj[cs][lane] = my_j;
-            }
-            if (lane == 0) {
-                sm.T[cs] = T;
-                sm.changed = 1;
-            }
-            __syncwarp();
+    if (d2 <= e2) {
+        ++cnt;
+        qs += dev::eps_quant(d2, esc);
+    }
+    if (d2 < m.T || (d2 == m.T && oj < m.Tj)) {
+        sm.ld[m.Tp][tid] = d2;
+        sm.lj[m.Tp][tid] = oj;
+        float mx = sm.ld[0][tid];
+        int mj = sm.lj[0][tid], mp = 0;
+        for (int p = 1; p < k; ++p) {
+            const float v = sm.ld[p][tid];
+            const int j = sm.lj[p][tid];
+            const bool gt = v > mx || (v == mx && j > mj);
+            mx = gt ? v : mx;
+            mj = gt ? j : mj;
+            mp = gt ? p : mp;
         }
+        m.T = mx;
+        m.Tj = mj;
+        m.Tp = mp;
     }
 }
 
-// Take / release the list lock for a whole warp (bounded wait).
-template <int KMAX>
-__device__ __forceinline__ bool lock_lists(TcSmem<KMAX> &sm)
+// Write the A row of subspace r (mask bits, then minus the filter threshold).
+__device__ __forceinline__ void write_a_row(unsigned char *A, int r, uint32_t mask, unsigned short thr)
 {
-    int got = 0;
-    if (dev::lane_id() == 0) {
-        for (unsigned it = 0; it < kLockSpin; ++it) {
-            if (atomicCAS(&sm.lock, 0, 1) == 0) {
-                got = 1;
-                break;
-            }
-            __nanosleep(64);
-        }
-        __threadfence_block();
+    uint32_t w[8];
+#pragma unroll
+    for (int p = 0; p < 8; ++p) {
+        const int f0 = 2 * p, f1 = 2 * p + 1;
+        const uint32_t lo = ((mask >> f0) & 1u) ? 0x3C00u : 0u;  // FP16 1.0 / 0.0
+        const uint32_t hi = f1 == 15 ? (uint32_t)thr : (((mask >> f1) & 1u) ? 0x3C00u : 0u);
+        w[p] = lo | (hi << 16);
     }
-    return __shfl_sync(dev::kFull, got, 0) != 0;
+    *reinterpret_cast<uint4 *>(A + op_off(r, 0)) = make_uint4(w[0], w[1], w[2], w[3]);
+    *reinterpret_cast<uint4 *>(A + op_off(r, 8)) = make_uint4(w[4], w[5], w[6], w[7]);
 }
 
-template <int KMAX>
-__device__ __forceinline__ void unlock_lists(TcSmem<KMAX> &sm)
+__device__ __forceinline__ uint32_t pack_half2(float a, float b)
 {
-    __syncwarp();
-    if (dev::lane_id() == 0) {
-        __threadfence_block();
-        atomicExch(&sm.lock, 0);
-    }
+    const __half2 h = __floats2half2_rn(a, b);
+    return *reinterpret_cast<const uint32_t *>(&h);
 }
 
 template <int KMAX>
-__global__ void __launch_bounds__(kTcWarps * 32)
+__global__ void __launch_bounds__(kCtaThreads, 1)
     join_tc_kernel(JoinShape s, const TcBlock *__restrict__ blocks, int n_blocks, JoinOut o,
                    DeviceControl *ctrl)
 {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
-    TcSmem<KMAX> &sm = *reinterpret_cast<TcSmem<KMAX> *>(smem_raw);
+    unsigned char *smem_al = smem_raw + ((1024u - (dev::smem_addr(smem_raw) & 1023u)) & 1023u);
+    TcSmem<KMAX> &sm = *reinterpret_cast<TcSmem<KMAX> *>(smem_al);
     const int tid = threadIdx.x;
     const int warp = tid >> 5;
     const unsigned lane = tid & 31u;
-    const int64_t n = s.n;
+
+    const int n = (int)s.n;  // <= 2^24
     const int k = s.k;
-    constexpr int kQB = kTcQueries;  // queries per work item
-    const long long n_qb = (n + kQB - 1) / kQB;
-    const long long total = n_qb * (long long)n_blocks;
     const int n_tiles = (int)(s.n_pad / kTile);
+    const int n_sub = n_tiles * kSubPerTile;  // even
+    const long long total = (long long)n * n_blocks;  // work items: (block, query)
     const float4 *x = s.x;
-    const uint32_t idesc = (1u << 4) | ((uint32_t)(kNB >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+    // work items of this CTA: blockIdx.x, blockIdx.x + gridDim.x, ...
+    const int my_items = total > blockIdx.x ? (int)((total - blockIdx.x + gridDim.x - 1) / gridDim.x) : 0;
 
     if (tid == 0) {
-        for (int st = 0; st < kTcStages; ++st) dev::mbar_init(&sm.full[st], 1);
-        dev::mbar_init(&sm.mma_bar, 1);
+        for (int st = 0; st < kStages; ++st) dev::mbar_init(&sm.full[st], 1);
+        for (int b = 0; b < 2; ++b) {
+            dev::mbar_init(&sm.b_ready[b], kConsumers / 32);
+            dev::mbar_init(&sm.t_empty[b], kConsumers / 32);
+            dev::mbar_init(&sm.mma_done[b], 1);
+        }
+        dev::mbar_init(&sm.cbar, kConsumers / 32);
+        sm.abort = 0;
         dev::fence_barrier_init();
     }
     if (warp == 0) {
@@ -261,294 +291,287 @@ __global__ void __launch_bounds__(kTcWarps * 32)
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = sm.tmem_base;
 
-    uint32_t tiles_used = 0;  // tiles consumed (stage / phase bookkeeping)
-    uint32_t mma_used = 0;    // MMA commits waited on
-    bool failed = false;
-    for (;;) {
-        if (tid == 0) sm.work = (long long)atomicAdd(&ctrl->next_work, 1ull);
-        __syncthreads();
-        const long long w = sm.work;
-        __syncthreads();
-        if (w >= total || failed) break;
-        const TcBlock &blk = blocks[w / n_qb];
-        const int64_t q0 = (w % n_qb) * kQB;
+    auto fail = [&]() {
+        *(volatile int *)&sm.abort = 1;
+        atomicOr(&ctrl->error, kErrTimeout);
+    };
 
-        if (tid < kNB) {
-            sm.mask[tid] = blk.mask[tid];
-            sm.slot[tid] = blk.slot[tid];
-            const float e2 = blk.eps2[tid];
-            sm.eps2[tid] = e2;
-            sm.escale[tid] = dev::eps_scale(e2).scale;
-        }
-        __syncthreads();
-
-        for (int64_t i = q0; i < q0 + kQB && i < n && !failed; ++i) {
-            float xq[16];
+    if (warp == kProducerWarp) {
+        // ================================ producer ================================================
+        if (lane == 0) {
+            // The z-th tile of this CTA's stream: tile iv of its work item ii, whose stream
+            // starts at the query's own tile and wraps around.
+            int ii = 0, iv = 0, it0 = 0;  // next tile to issue: item, tile within item, first tile
+            auto item_t0 = [&](int item_iter) {
+                const long long item = blockIdx.x + (long long)item_iter * gridDim.x;
+                return (int)((item % n) / kTile);
+            };
+            if (my_items > 0) it0 = item_t0(0);
+            long long issued = 0;
+            auto issue_next = [&]() {
+                if (ii < my_items) {
+                    int tt = it0 + iv;
+                    if (tt >= n_tiles) tt -= n_tiles;
+                    const int st = (int)(issued % kStages);
+                    dev::bulk_load(sm.ring[st], x + (int64_t)tt * kTile * 4, kTile * 64, &sm.full[st]);
+                    if (++iv == n_tiles) {
+                        iv = 0;
+                        if (++ii < my_items) it0 = item_t0(ii);
+                    }
+                }
+                ++issued;
+            };
+            for (int st = 0; st < kStages; ++st) issue_next();
+            const long long total_sub = (long long)my_items * n_sub;
+            // D = F32, A = B = F16, both K-major; N = 128, M = 128
+            const uint32_t idesc = (1u << 4) | ((uint32_t)(kNC >> 3) << 17) | ((uint32_t)(kM >> 4) << 24);
+            long long g = 0;
+            bool ok = true;
+            for (; g < total_sub; ++g) {
+                const int b = (int)(g & 1);
+                const unsigned ph = (unsigned)((g >> 1) & 1);
+                ok = wait_or_abort(&sm.b_ready[b], ph, &sm.abort);
+                if (ok && g >= 2) ok = wait_or_abort(&sm.t_empty[b], ph ^ 1u, &sm.abort);
+                if (!ok) break;
+                // sub-tiles <= g - 2 are done with: refill the ring behind them
+                if (g >= 2) {
+                    const long long tiles_done = (g - 1) / kSubPerTile;
+                    while (issued < tiles_done + kStages) issue_next();
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint64_t bdesc = smem_desc(sm.B[b]);
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const float4 v = x[row_quad(i, q)];
-                xq[4 * q + 0] = v.x;
-                xq[4 * q + 1] = v.y;
-                xq[4 * q + 2] = v.z;
-                xq[4 * q + 3] = v.w;
+                for (int hf = 0; hf < kHalves; ++hf) {
+                    const uint64_t adesc = smem_desc(sm.A[b][hf]);
+                    const uint32_t dt = tmem + (uint32_t)((b * kHalves + hf) * kNC);
+                    asm volatile(
+                        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(dt),
+                        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(0));
+                }
+                asm volatile(
+                    "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                        dev::smem_addr(&sm.mma_done[b])));
             }
-            const int orig_i = __float_as_int(xq[15]);  // the query's original index
-            // stream the tiles: prologue
-            if (tid == 0) {
-                for (int t = 0; t < kTcStages && t < n_tiles; ++t) {
-                    const uint32_t st = (tiles_used + t) % kTcStages;
-                    dev::bulk_load(sm.tile[st], x + (int64_t)t * kTile * 4, kTile * 64, &sm.full[st]);
+            if (!ok) {
+                fail();
+                // let the copies and MMAs in flight land before the CTA leaves: the last
+                // kStages tiles issued (earlier ones were consumed before their slots were refilled)
+                const long long real = std::min(issued, (long long)my_items * n_tiles);
+                for (long long z = std::max(0ll, real - kStages); z < real; ++z)
+                    dev::mbar_wait(&sm.full[z % kStages], (unsigned)((z / kStages) & 1));
+                if (g >= 1) dev::mbar_wait(&sm.mma_done[(g - 1) & 1], (unsigned)(((g - 1) >> 1) & 1));
+            }
+        }
+        __syncwarp();
+    } else {
+        // ================================ consumers ===============================================
+        // event role: subspace sidx = half * 128 + arow (TMEM lane arow of half `half`)
+        const int half = warp >> 2;
+        const int sub = warp & 3;
+        const int arow = (sub << 5) | (int)lane;
+        const int sidx = half * kM + arow;
+        // B-build role: candidate row br of the sub-tile, K half bh
+        const int br = tid >> 1;
+        const int bh = tid & 1;
+        long long gsub = 0;  // global index of this item's first sub-tile
+        bool ok = true;
+        // every lane of a warp takes the same branch after a wait
+        auto wwait = [&](uint64_t *bar, unsigned parity) -> bool {
+            return __all_sync(dev::kFull, wait_or_abort(bar, parity, &sm.abort));
+        };
+        // barrier of the consumer warps (an mbarrier, so that it can give up)
+        unsigned cuses = 0;
+        auto cbarrier = [&]() -> bool {
+            __syncwarp();
+            if (lane == 0) dev::mbar_arrive(&sm.cbar);
+            return wwait(&sm.cbar, (cuses++) & 1u);
+        };
+
+        for (int it = 0; it < my_items && ok; ++it, gsub += n_sub) {
+            const long long item = blockIdx.x + (long long)it * gridDim.x;
+            const int blk = (int)(item / n);
+            const int iq = (int)(item % n);  // the query's stored row
+            const TcBlock &bk = blocks[blk];
+
+            // ---- this thread's subspace ------------------------------------------------------------
+            const uint32_t mask = bk.mask[sidx];
+            const bool act = mask != 0u;
+            const float e2 = bk.eps2[sidx];
+            const float esc = dev::eps_scale(e2).scale;
+            const float4 *xq = sm.xq;
+            // ---- B-build role: the query's features of K half bh ----------------------------------
+            const float4 bx0 = x[row_quad(iq, 2 * bh)], bx1 = x[row_quad(iq, 2 * bh + 1)];
+            // the rows folded exactly first: a window of kWarm rows around the query
+            const int wcount = n < kWarm ? n : kWarm;
+            const int w0 = std::min(std::max(iq - kWarm / 2, 0), n - wcount);
+            if (!cbarrier()) {  // the previous item's shared rows are no longer read
+                ok = false;
+                break;
+            }
+            if (tid < 4 * kWarm) {
+                const int p = tid / kWarm, r = tid % kWarm;
+                sm.warm[p][r] = r < wcount ? x[row_quad(w0 + r, p)] : make_float4(0.f, 0.f, 0.f, 0.f);
+            } else if (tid < 4 * kWarm + 4) {
+                sm.xq[tid - 4 * kWarm] = x[row_quad(iq, tid - 4 * kWarm)];
+            }
+#pragma unroll 1
+            for (int p = 0; p < KMAX; ++p) {
+                sm.ld[p][tid] = CUDART_INF_F;
+                sm.lj[p][tid] = 0x7fffffff;
+            }
+            if (!cbarrier()) {  // start-up rows staged
+                ok = false;
+                break;
+            }
+
+            // ---- start-up: the private list from the window -----------------------------------------
+            KnnMax km;
+            km.T = (act && k > 0) ? CUDART_INF_F : -CUDART_INF_F;
+            km.Tj = 0x7fffffff;
+            km.Tp = 0;
+            int cnt = 0;
+            unsigned long long qs = 0ull;
+            if (act) {
+#pragma unroll 1
+                for (int r = 0; r < wcount; ++r) {
+                    if (w0 + r == iq) continue;
+                    int oj;
+                    const float d2 = fold_exact(xq, &sm.warm[0][0], kWarm, r, mask, oj);
+                    decide<KMAX>(sm, tid, k, d2, oj, e2, esc, cnt, qs, km);
                 }
             }
-            if (tid < kTcWarps) sm.tcount[tid] = 0;
-            if (tid == 0) {
-                sm.lock = 0;
-                sm.changed = 0;
+            // the threshold last written into each A copy
+            float t_w0 = act ? fmaxf(km.T, eps_floor(e2)) : -1.f, t_w1 = t_w0;
+            {
+                const unsigned short th = __half_as_ushort(neg_filter(t_w0));
+                write_a_row(sm.A[0][half], arow, mask, th);
+                write_a_row(sm.A[1][half], arow, mask, th);
             }
-            for (int t = 0; t < n_tiles; ++t) {
-                const uint32_t st = (tiles_used + t) % kTcStages;
-                const bool ok = dev::mbar_wait(&sm.full[st], ((tiles_used + t) / kTcStages) & 1u);
-                if (__syncthreads_or(!ok)) {
-                    if (tid == 0) {
-                        atomicOr(&ctrl->error, kErrTimeout);
-                        // let the copies still in flight land before the CTA leaves
-                        for (int u = t + 1; u < t + kTcStages && u < n_tiles; ++u)
-                            dev::mbar_wait(&sm.full[(tiles_used + u) % kTcStages],
-                                           ((tiles_used + u) / kTcStages) & 1u);
-                    }
-                    failed = true;
+
+            const int t0 = iq / kTile;
+            // Build the B rows of sub-tile u (waiting for its tile first when it starts
+            // one), then announce them to the producer.
+            auto build = [&](int u) -> bool {
+                const int v = u / kSubPerTile;
+                const long long z = gsub / kSubPerTile + v;
+                const int slot = (int)(z % kStages);
+                if (u % kSubPerTile == 0 && !wwait(&sm.full[slot], (unsigned)((z / kStages) & 1))) return false;
+                int vt = t0 + v;
+                if (vt >= n_tiles) vt -= n_tiles;
+                const int rr = (u % kSubPerTile) * kNC + br;
+                const int j = vt * kTile + rr;
+                const bool skip = j >= n || j == iq || (unsigned)(j - w0) < (unsigned)wcount;
+                uint4 wd;
+                if (skip) {
+                    // never passes: every feature 65504, no threshold column
+                    wd = make_uint4(0x7BFF7BFFu, 0x7BFF7BFFu, 0x7BFF7BFFu, bh ? 0x00007BFFu : 0x7BFF7BFFu);
+                } else {
+                    const float4 c0 = sm.ring[slot][(2 * bh) * kTile + rr];
+                    const float4 c1 = sm.ring[slot][(2 * bh + 1) * kTile + rr];
+                    const float d0 = c0.x - bx0.x, d1 = c0.y - bx0.y, d2 = c0.z - bx0.z, d3 = c0.w - bx0.w;
+                    const float d4 = c1.x - bx1.x, d5 = c1.y - bx1.y, d6 = c1.z - bx1.z, d7 = c1.w - bx1.w;
+                    wd.x = pack_half2(d0 * d0, d1 * d1);
+                    wd.y = pack_half2(d2 * d2, d3 * d3);
+                    wd.z = pack_half2(d4 * d4, d5 * d5);
+                    wd.w = pack_half2(d6 * d6, bh ? 1.f : d7 * d7);
+                }
+                *reinterpret_cast<uint4 *>(&sm.B[u & 1][op_off(br, 8 * bh)]) = wd;
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                __syncwarp();
+                if (lane == 0) dev::mbar_arrive(&sm.b_ready[u & 1]);
+                return true;
+            };
+            ok = build(0);
+#pragma unroll 1
+            for (int u = 0; u < n_sub && ok; ++u) {
+                if (u + 1 < n_sub && !build(u + 1)) {
+                    ok = false;
                     break;
                 }
-                const float4 *tile = sm.tile[st];
-                const int64_t base = (int64_t)t * kTile;
-                if (t == 0) {
-                    // ---- set-up: thread c < 64 folds subspace c over the first candidates ----
-                    if (tid < kNB) {
-                        const int c = tid;
-                        const uint32_t mask = sm.mask[c];
-                        const bool act = mask != 0u && k > 0;
-                        float T = act ? CUDART_INF_F : -CUDART_INF_F;
-                        const float e2 = sm.eps2[c];
-                        const float sc = sm.escale[c];
-                        for (int p = 0; p < KMAX; ++p) {
-                            sm.ld[c][p] = CUDART_INF_F;
-                            sm.lj[c][p] = 0x7fffffff;
-                        }
-                        int cnt = 0;
-                        unsigned long long qs = 0;
-                        const int c_end = (int)std::min<int64_t>(kTcInit, n);
-                        for (int r = 0; r < c_end; ++r) {
-                            if ((int64_t)r == i || mask == 0u) continue;
-                            const float acc = fold_exact(xq, tile, r, mask);
-                            if (acc <= e2) {
-                                ++cnt;
-                                qs += dev::eps_quant(acc, sc);
-                            }
-                            const int oc = __float_as_int(tile[3 * kTile + r].w);
-                            if (act && (acc < T || (acc == T && oc < sm.lj[c][k - 1])))
-                                T = dev::private_insert(sm.ld[c], sm.lj[c], k, acc, oc);
-                        }
-                        sm.T[c] = T;
-                        sm.cnt[c] = cnt;
-                        sm.esum[c] = qs;
-                        sm.epart[c] = 0u;
-                        // B operand row c: mask bits, then minus the filter threshold
-                        __half row[16];
-#pragma unroll
-                        for (int f = 0; f < 15; ++f) row[f] = __float2half(((mask >> f) & 1u) ? 1.f : 0.f);
-                        row[15] = neg_filter(mask ? fmaxf(T, eps_up(e2)) : -1.f);
-#pragma unroll
-                        for (int f = 0; f < 16; ++f)
-                            *reinterpret_cast<__half *>(sm.B + op_off(c, f)) = row[f];
-                    }
-                    __syncthreads();  // set-up lists and B complete before tile 0's MMA
+                // ---- filter and decide sub-tile u ----------------------------------------------------
+                const long long gu = gsub + u;
+                const int b = (int)(gu & 1);
+                if (!wwait(&sm.mma_done[b], (unsigned)((gu >> 1) & 1))) {
+                    ok = false;
+                    break;
                 }
-                {
-                    // ---- A operand: rows tid and tid + 128 of this tile ------------------------
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const float4 *tl = sm.ring[(gsub / kSubPerTile + u / kSubPerTile) % kStages];
+                const int rbase = (u % kSubPerTile) * kNC;
+                const uint32_t taddr = tmem + ((uint32_t)(sub * 32) << 16) + (uint32_t)((b * kHalves + half) * kNC);
+#pragma unroll 1
+                for (int h = 0; h < kNC / 32; ++h) {
+                    uint32_t r[32];
+                    tmem_ld32(taddr + (uint32_t)(32 * h), r);
+                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                    uint32_t any = 0u;
 #pragma unroll
-                    for (int h = 0; h < 2; ++h) {
-                        const int r = tid + 128 * h;
-                        const int64_t j = base + r;
-                        uint32_t wds[8];  // 16 FP16 values, two per word
-                        if (j == i || j >= n || j < kTcInit) {
-                            // never passes: 65504 per feature, no threshold column
-                            const __half2 big = __float2half2_rn(65504.f);
+                    for (int c = 0; c < 32; ++c) any |= r[c];
+                    if (act && (int)any < 0) {
+                        uint32_t hm = 0u;  // bit c: column c passed the filter
 #pragma unroll
-                            for (int q = 0; q < 7; ++q) wds[q] = *reinterpret_cast<const uint32_t *>(&big);
-                            const __half2 last = __halves2half2(__float2half(65504.f), __float2half(0.f));
-                            wds[7] = *reinterpret_cast<const uint32_t *>(&last);
-                        } else {
-                            float sq[16];
-#pragma unroll
-                            for (int q = 0; q < 4; ++q) {
-                                const float4 v = tile[q * kTile + r];
-                                const float d0 = v.x - xq[4 * q], d1 = v.y - xq[4 * q + 1];
-                                const float d2 = v.z - xq[4 * q + 2], d3 = v.w - xq[4 * q + 3];
-                                sq[4 * q + 0] = d0 * d0;
-                                sq[4 * q + 1] = d1 * d1;
-                                sq[4 * q + 2] = d2 * d2;
-                                sq[4 * q + 3] = d3 * d3;
-                            }
-                            sq[15] = 1.f;  // threshold column
-#pragma unroll
-                            for (int q = 0; q < 8; ++q) {
-                                const __half2 hv = __floats2half2_rn(sq[2 * q], sq[2 * q + 1]);
-                                wds[q] = *reinterpret_cast<const uint32_t *>(&hv);
-                            }
+                        for (int c = 31; c >= 0; --c) hm = __funnelshift_l(r[c], hm, 1);
+                        // two survivors at a time: their folds overlap
+                        while (hm) {
+                            const int c1 = __ffs(hm) - 1;
+                            hm &= hm - 1u;
+                            const int c2 = hm ? __ffs(hm) - 1 : c1;
+                            const bool two = hm != 0u;
+                            hm &= hm - 1u;
+                            int o1, o2;
+                            const float a1 = fold_exact(xq, tl, kTile, rbase + 32 * h + c1, mask, o1);
+                            const float a2 = fold_exact(xq, tl, kTile, rbase + 32 * h + c2, mask, o2);
+                            decide<KMAX>(sm, tid, k, a1, o1, e2, esc, cnt, qs, km);
+                            if (two) decide<KMAX>(sm, tid, k, a2, o2, e2, esc, cnt, qs, km);
                         }
-                        unsigned char *Ab = sm.A[h];
-                        *reinterpret_cast<uint4 *>(Ab + op_off(tid, 0)) = make_uint4(wds[0], wds[1], wds[2], wds[3]);
-                        *reinterpret_cast<uint4 *>(Ab + op_off(tid, 8)) = make_uint4(wds[4], wds[5], wds[6], wds[7]);
+                    }
+                }
+                // tightened threshold into the A copy batch gu used: its next reader (batch
+                // gu + 2) is issued only after this warp's t_empty arrival
+                if (act) {
+                    const float tn = fmaxf(km.T, eps_floor(e2));
+                    float &tw = b ? t_w1 : t_w0;
+                    if (tn != tw) {
+                        tw = tn;
+                        *reinterpret_cast<__half *>(&sm.A[b][half][op_off(arow, 15)]) = neg_filter(tn);
                     }
                 }
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                __syncthreads();
-                {
-                    // ---- two MMAs: rows 0..127 -> columns 0..63, rows 128..255 -> 64..127 -----
-                    if (tid == 0) {
-                        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                        const uint64_t bdesc = smem_desc(sm.B);
-#pragma unroll
-                        for (int h = 0; h < 2; ++h) {
-                            const uint64_t adesc = smem_desc(sm.A[h]);
-                            asm volatile(
-                                "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-                                "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(
-                                    tmem + (uint32_t)(h * kNB)),
-                                "l"(adesc), "l"(bdesc), "r"(idesc), "r"(0));
-                        }
-                        asm volatile(
-                            "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                                dev::smem_addr(&sm.mma_bar)));
-                    }
-                    const bool mok = dev::mbar_wait(&sm.mma_bar, mma_used & 1u);
-                    ++mma_used;
-                    if (__syncthreads_or(!mok)) {
-                        if (tid == 0) {
-                            atomicOr(&ctrl->error, kErrTimeout);
-                            for (int u = t + 1; u < t + kTcStages && u < n_tiles; ++u)
-                                dev::mbar_wait(&sm.full[(tiles_used + u) % kTcStages],
-                                               ((tiles_used + u) / kTcStages) & 1u);
-                        }
-                        failed = true;
-                        break;
-                    }
-                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                    // ---- epilogue: warp w owns rows 32w..32w+31 of both regions -----------
-                    uint2 *buf = sm.tbuf[warp];
-                    int count = sm.tcount[warp];
-                    const int ra = 32 * warp + (int)lane, rb = ra + 128;
-                    // original indices of this lane's two candidates (float 15 of the rows)
-                    const int ja = __float_as_int(tile[3 * kTile + ra].w);
-                    const int jb = __float_as_int(tile[3 * kTile + rb].w);
-#pragma unroll 1
-                    for (int c0 = 0; c0 < kNB; c0 += 32) {
-                        uint32_t r0[32], r1[32];
-                        const uint32_t lanebase = tmem + ((uint32_t)(32 * warp) << 16);
-                        tmem_ld32(lanebase + (uint32_t)c0, r0);
-                        tmem_ld32(lanebase + (uint32_t)(kNB + c0), r1);
-                        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-                        for (int c = 0; c < 32; c += 2) {
-                            const uint32_t sgn = (r0[c] | r1[c] | r0[c + 1] | r1[c + 1]) & 0x80000000u;
-                            if (__any_sync(dev::kFull, sgn != 0u)) {
-#pragma unroll
-                                for (int e = 0; e < 2; ++e) {
-                                    const int col = c0 + c + e;
-                                    const bool pa = (int)r0[c + e] < 0, pb = (int)r1[c + e] < 0;
-                                    if (__any_sync(dev::kFull, pa | pb)) {
-                                        const uint32_t mask = sm.mask[col];
-                                        const float da = pa ? fold_exact(xq, tile, ra, mask) : CUDART_INF_F;
-                                        const float db = pb ? fold_exact(xq, tile, rb, mask) : CUDART_INF_F;
-                                        // eps: counts and exact sums, aggregated per warp
-                                        const float e2 = sm.eps2[col];
-                                        const bool ea = da <= e2, eb = db <= e2;
-                                        const unsigned ba = __ballot_sync(dev::kFull, ea);
-                                        const unsigned bb = __ballot_sync(dev::kFull, eb);
-                                        if (ba | bb) {
-                                            const float scl = sm.escale[col];
-                                            unsigned part = 0;
-                                            if (ea) part += dev::eps_quant(da, scl);
-                                            if (eb) part += dev::eps_quant(db, scl);
-                                            const unsigned sum = __reduce_add_sync(dev::kFull, part);
-                                            if (lane == 0) {
-                                                atomicAdd(&sm.cnt[col], __popc(ba) + __popc(bb));
-                                                atomicAdd(&sm.epart[col], sum);
-                                            }
-                                        }
-                                        // kNN candidates: buffered, inserted under the list lock
-                                        const float T = sm.T[col];
-                                        append(buf, count, da <= T, da, col, ja);
-                                        append(buf, count, db <= T, db, col, jb);
-                                    }
-                                }
-                                if (count > kTcFlushAt) {
-                                    if (lock_lists(sm)) {
-                                        tc_flush<KMAX>(sm, buf, count, k);
-                                        unlock_lists(sm);
-                                    } else if (lane == 0) {
-                                        atomicOr(&ctrl->error, kErrTimeout);
-                                    }
-                                    count = 0;
-                                }
-                            }
-                        }
-                    }
-                    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-                    // ---- each warp inserts its own kNN candidates under the list lock -------
-                    if (count > 0) {
-                        if (lock_lists(sm)) {
-                            tc_flush<KMAX>(sm, buf, count, k);
-                            unlock_lists(sm);
-                        } else if (lane == 0) {
-                            atomicOr(&ctrl->error, kErrTimeout);
-                        }
-                    }
-                    __syncthreads();
-                    if (warp == 0) {
-                        // fold this tile's partial eps sums
-                        for (int c = (int)lane; c < kNB; c += 32) {
-                            sm.esum[c] += sm.epart[c];
-                            sm.epart[c] = 0u;
-                        }
-                        __syncwarp();
-                        if (sm.changed) {
-                            for (int c = (int)lane; c < kNB; c += 32) {
-                                const uint32_t mask = sm.mask[c];
-                                *reinterpret_cast<__half *>(sm.B + op_off(c, 15)) =
-                                    neg_filter(mask ? fmaxf(sm.T[c], eps_up(sm.eps2[c])) : -1.f);
-                            }
-                        }
-                        __syncwarp();
-                        if (lane == 0) sm.changed = 0;
-                        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                    }
-                }
-                __syncthreads();
-                if (tid == 0 && t + kTcStages < n_tiles)
-                    dev::bulk_load(sm.tile[st], x + (int64_t)(t + kTcStages) * kTile * 4, kTile * 64,
-                                   &sm.full[st]);
+                asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                __syncwarp();
+                if (lane == 0) dev::mbar_arrive(&sm.t_empty[b]);
             }
-            if (failed) break;
-            tiles_used += n_tiles;
+            if (!ok) break;
 
-            // ---- this query's results: thread c < 64 reports subspace c ------------------------
-            if (tid < kNB && sm.mask[tid] != 0u && (orig_i < 0 || orig_i >= n)) {
-                // a row that does not carry its index: report, write nothing
-                atomicOr(&ctrl->error, kErrBadRow);
-            } else if (tid < kNB && sm.mask[tid] != 0u) {
-                const int c = tid;
-                const int slot = sm.slot[c];
+            // ---- this item's results: thread s reports the query in subspace s --------------------
+            const int orig_i = __float_as_int(xq[3].w);
+            if (act && (orig_i < 0 || orig_i >= n)) {
+                atomicOr(&ctrl->error, kErrBadRow);  // rows that do not carry their index
+            } else if (act) {
+                const int slot = bk.slot[sidx];
                 float *sc = o.scores + (int64_t)slot * 4 * n;
-                const int cnt = sm.cnt[c];
                 sc[orig_i] = (float)cnt;
-                sc[n + orig_i] = dev::eps_mean(sm.esum[c], cnt, sm.escale[c]);
+                sc[n + orig_i] = dev::eps_mean(qs, cnt, esc);
                 if (o.eps_count) o.eps_count[(int64_t)slot * n + orig_i] = cnt;
                 if (k > 0) {
+                    // sort the list by (distance, index)
+                    for (int p = 1; p < k; ++p) {
+                        const float v = sm.ld[p][tid];
+                        const int j = sm.lj[p][tid];
+                        int q = p;
+                        while (q > 0 && (sm.ld[q - 1][tid] > v || (sm.ld[q - 1][tid] == v && sm.lj[q - 1][tid] > j))) {
+                            sm.ld[q][tid] = sm.ld[q - 1][tid];
+                            sm.lj[q][tid] = sm.lj[q - 1][tid];
+                            --q;
+                        }
+                        sm.ld[q][tid] = v;
+                        sm.lj[q][tid] = j;
+                    }
                     float msum = 0.f;
                     for (int p = 0; p < k; ++p) {
-                        const float dd = sqrtf(sm.ld[c][p]);
-                        const int j = sm.lj[c][p];
+                        const float dd = sqrtf(sm.ld[p][tid]);
+                        const int j = sm.lj[p][tid];
                         msum += dd;
                         if (j >= 0 && j < n) atomicAdd(&sc[2 * n + j], 1.f);
                         if (o.knn_idx) o.knn_idx[((int64_t)slot * n + orig_i) * k + p] = j;
@@ -557,8 +580,8 @@ __global__ void __launch_bounds__(kTcWarps * 32)
                     sc[3 * n + orig_i] = msum / (float)k;
                 }
             }
-            __syncthreads();
         }
+        if (!ok) fail();
     }
 
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -574,20 +597,13 @@ snaps_status launch_tc(const JoinShape &s, const TcBlock *blocks, int n_blocks, 
     const size_t smem = sizeof(TcSmem<KMAX>) + 1024;  // slack for the 1024-byte alignment
     auto kern = join_tc_kernel<KMAX>;
     SNAPS_CHECK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    int dev = 0, sms = 0, per_sm = 0;
+    int dev = 0, sms = 0;
     SNAPS_CHECK_CUDA(cudaGetDevice(&dev));
     SNAPS_CHECK_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    SNAPS_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kTcWarps * 32, smem));
-    if (per_sm < 1) {
-        set_error("tensor-core join does not fit on an SM (smem %zu)", smem);
-        return SNAPS_ECUDA;
-    }
-    per_sm = std::min(per_sm, (int)(512 / kTmemCols));  // tensor memory: 512 columns per SM
-    const long long n_qb = (s.n + kTcQueries - 1) / kTcQueries;
-    const long long total = n_qb * (long long)n_blocks;
-    const long long grid = std::min<long long>(total, (long long)sms * per_sm);
-    SNAPS_CHECK_CUDA(cudaMemsetAsync(&ctrl->next_work, 0, sizeof(unsigned long long), st));
-    kern<<<(unsigned)grid, kTcWarps * 32, smem, st>>>(s, blocks, n_blocks, o, ctrl);
+    const long long total = s.n * (long long)n_blocks;
+    // one CTA per SM: it holds all 512 tensor-memory columns
+    const long long grid = std::min<long long>(total, (long long)sms);
+    kern<<<(unsigned)grid, kCtaThreads, smem, st>>>(s, blocks, n_blocks, o, ctrl);
     SNAPS_CHECK_CUDA(cudaGetLastError());
     return SNAPS_OK;
 }
