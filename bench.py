@@ -43,6 +43,17 @@ SAMPLE_SEED = 1              # the 64-subspace oracle sample of the batching wor
 COMPARES_PER_SM_CLK = 64     # FP32 compare throughput per SM per clock
 
 
+def _load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+PEAKS = _load_peaks()
+
+
 def parse():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -54,7 +65,15 @@ def parse():
                     help="'all', a count of seeded sample subspaces, or 'chunk:H' (H = 10 binary "
                          "digits: the 32 subspaces (H << 5) | L sharing that high part)")
     ap.add_argument("--k", type=int, default=K_DEFAULT)
-    ap.add_argument("--precision", choices=["fp32", "tc_f16"], default="fp32")
+    ap.add_argument("--precision", choices=["fp32", "tc_f16", "both"], default="both",
+                    help="fp32: the plain join; tc_f16: the tensor-core filtered join; both "
+                         "(default): time the plain join as the headline and the tensor-core "
+                         "join beside it on the same workload")
+    ap.add_argument("--index", choices=["auto", "grid", "none"], default="auto",
+                    help="grid index for subspaces of <= 4 features: the library's choice "
+                         "(auto), always, or never")
+    ap.add_argument("--tc-steps", type=int, default=1,
+                    help="timed steps of the tensor-core leg under --precision both")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--serving", type=int, default=0, metavar="R",
@@ -154,7 +173,8 @@ def run_ours(args, rank, world, dist):
     x = snaps_inputs.population(args.n, 0)
     masks = workload_masks(args.masks)
     m, n, k = masks.size, args.n, args.k
-    precision = snaps.SNAPS_FP32 if args.precision == "fp32" else snaps.SNAPS_TC_F16
+    index_flag = {"auto": 0, "grid": snaps.SNAPS_INDEX_GRID, "none": snaps.SNAPS_INDEX_NONE}[args.index]
+    head_prec = (snaps.SNAPS_TC_F16 if args.precision == "tc_f16" else snaps.SNAPS_FP32) | index_flag
     ctx = snaps.snaps_create(local)
     stream = torch.cuda.current_stream()
     x_dev = torch.from_numpy(x).to(dev)
@@ -163,7 +183,7 @@ def run_ours(args, rank, world, dist):
     top = torch.empty((m, 4, 100), dtype=torch.int32, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
 
-    def step():
+    def step(precision):
         pop = snaps.snaps_index(ctx, x_dev, snaps.SNAPS_NORM_MINMAX, stream=stream)
         snaps.snaps_scores(pop, masks, k, precision=precision, scores=scores, norm=norm,
                            top=top, top_n=100, stream=stream)
@@ -174,51 +194,98 @@ def run_ours(args, rank, world, dist):
             dist.barrier()
         torch.cuda.synchronize()
 
-    for w in range(args.warmup):
-        t0 = time.perf_counter()
-        snaps.snaps_release(step())
-        torch.cuda.synchronize()
-        print(f"[bench] warmup {w}: {time.perf_counter() - t0:.3f} s", file=sys.stderr, flush=True)
-    barrier()
-    snaps.snaps_trace(ctx, True)
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-          for _ in range(args.steps)]
-    pops = []
-    with ClockSampler(local) as clk:
+    def timed_leg(precision, steps, warmup):
+        """W untimed steps, then K steps bracketed by barrier + synchronize; CUDA events on
+        the launch stream per step, the library's per-phase trace, clocks sampled."""
+        for w in range(warmup):
+            t0 = time.perf_counter()
+            snaps.snaps_release(step(precision))
+            torch.cuda.synchronize()
+            print(f"[bench] precision {precision} warmup {w}: {time.perf_counter() - t0:.3f} s",
+                  file=sys.stderr, flush=True)
         barrier()
-        for s in range(args.steps):
-            flush.fill_(float(s))                      # evict the previous step from L2
-            ev[s][0].record(stream)
-            pops.append(step())
-            ev[s][1].record(stream)
-        barrier()
-    trace = snaps.snaps_trace_read(ctx)
-    snaps.snaps_trace(ctx, False)
-    for p in pops:
-        snaps.snaps_release(p)
-    step_ms = [a.elapsed_time(b) for a, b in ev]
-    total_ms = sum(step_ms)
-    if dist is not None:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+        snaps.snaps_trace(ctx, True)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(steps)]
+        pops = []
+        with ClockSampler(local) as clk:
+            barrier()
+            for s in range(steps):
+                flush.fill_(float(s))                      # evict the previous step from L2
+                ev[s][0].record(stream)
+                pops.append(step(precision))
+                ev[s][1].record(stream)
+            barrier()
+        trace = snaps.snaps_trace_read(ctx)
+        snaps.snaps_trace(ctx, False)
+        for p in pops:
+            snaps.snaps_release(p)
+        total_ms = sum(a.elapsed_time(b) for a, b in ev)
+        if dist is not None:
+            t = torch.tensor([total_ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            total_ms = float(t.item())
+        return total_ms, trace, clk.summary()
+
+    total_ms, trace, clocks = timed_leg(head_prec, args.steps, args.warmup)
     units = float(n) * m * args.steps * world
     value = units / (total_ms / 1e3)
-
-    # roofline of the dominant kernel (the subspace-batched join)
-    tree_ms, tree_launches = trace["join_tree"]
-    lane_ms, _ = trace["join_lane"]
     evals_per_step = float(n) * (n - 1) * m
     props = torch.cuda.get_device_properties(local)
-    clocks = clk.summary()
     max_mhz = clocks["sm_max_mhz"] or 2032.0
-    peak = props.multi_processor_count * COMPARES_PER_SM_CLK * max_mhz * 1e6 / 1e12
-    dominant = "join_tree" if tree_ms >= lane_ms else "join_lane"
-    dom_ms = max(tree_ms, lane_ms)
-    dom_launches = trace[dominant][1]
-    achieved = evals_per_step * args.steps / (dom_ms / 1e3) / 1e12 if dom_ms > 0 else None
     launches = int(sum(v[1] for v in trace.values()))
-    measured_alu = snaps.snaps_calibrate_alu(local) / 1e12
+
+    def alu_roofline(trace, steps):
+        """ALU roofline of the plain path's dominant join kernel: one FP32 compare per
+        (pair, subspace) evaluation is the algorithmic minimum."""
+        tree_ms = trace["join_tree"][0]
+        lane_ms = trace["join_lane"][0]
+        dominant = "join_tree" if tree_ms >= lane_ms else "join_lane"
+        dom_ms, dom_launches = trace[dominant]
+        peak = props.multi_processor_count * COMPARES_PER_SM_CLK * max_mhz * 1e6 / 1e12
+        achieved = evals_per_step * steps / (dom_ms / 1e3) / 1e12 if dom_ms > 0 else None
+        measured_alu = snaps.snaps_calibrate_alu(local) / 1e12
+        return {"bound": "alu", "kernel": dominant, "achieved": achieved, "peak": peak,
+                "unit": "Tevals/s", "frac": (achieved / peak) if achieved else None, "traffic": None,
+                "peak_basis": f"{props.multi_processor_count} SMs x {COMPARES_PER_SM_CLK} FP32 "
+                              f"compares/clk x {max_mhz:.0f} MHz (one compare per pair-subspace "
+                              f"evaluation)",
+                "kernel_ms_per_launch": dom_ms / max(dom_launches, 1),
+                "measured_alu_peak": measured_alu,
+                "frac_of_measured_alu": (achieved / measured_alu) if achieved else None}
+
+    def tensor_roofline(trace, steps):
+        """Tensor roofline of the tensor-core join: 2 x 16 FLOPs (K = 16, FP16) per
+        (pair, subspace) evaluation against the measured dense BF16 peak (FP16 runs at
+        the same rate)."""
+        tc_ms, tc_launches = trace["join_tc"]
+        flops = 2.0 * 16 * evals_per_step * steps
+        achieved = flops / (tc_ms / 1e3) / 1e12 if tc_ms > 0 else None
+        peak = PEAKS.get("bf16_tflops_sustained") or PEAKS.get("bf16_tflops") or 1400.0
+        return {"bound": "tensor", "kernel": "join_tc", "achieved": achieved, "peak": peak,
+                "unit": "TFLOP/s", "frac": (achieved / peak) if achieved else None, "traffic": None,
+                "peak_basis": "measured dense BF16 GEMM, sustained (MEASURED_PEAKS.json); FP16 "
+                              "has the same dense rate",
+                "evals_per_s": evals_per_step * steps / (tc_ms / 1e3) if tc_ms > 0 else None,
+                "kernel_ms_per_launch": tc_ms / max(tc_launches, 1)}
+
+    roofline = tensor_roofline(trace, args.steps) if (head_prec & 0xFF) == snaps.SNAPS_TC_F16 else \
+        alu_roofline(trace, args.steps)
+
+    tc_leg = None
+    if args.precision == "both":
+        tc_ms, tc_trace, tc_clocks = timed_leg(snaps.SNAPS_TC_F16 | index_flag, args.tc_steps, 1)
+        tc_units = float(n) * m * args.tc_steps * world
+        tc_leg = {"value": tc_units / (tc_ms / 1e3), "unit": "objects*subspaces/s",
+                  "ms_per_step": tc_ms / args.tc_steps, "steps": args.tc_steps, "warmup": 1,
+                  "vs_plain": (tc_units / (tc_ms / 1e3)) / value,
+                  "distance_evals_per_s": evals_per_step * args.tc_steps * world / (tc_ms / 1e3),
+                  "roofline": tensor_roofline(tc_trace, args.tc_steps),
+                  "phase_ms_per_step": {kn: v[0] / args.tc_steps for kn, v in tc_trace.items()},
+                  "gpu_launches": int(sum(v[1] for v in tc_trace.values())),
+                  "clocks": tc_clocks,
+                  "exactness": "bit-identical to the plain FP32 join (FP16 filter, every survivor "
+                               "recomputed in FP32)"}
 
     # end to end through the C ABI with host buffers
     e2e = None
@@ -230,7 +297,7 @@ def run_ours(args, rank, world, dist):
         def e2e_step():
             x_stage.copy_(x_pin, non_blocking=True)     # H2D of this step's input
             pop = snaps.snaps_index(ctx, x_stage, snaps.SNAPS_NORM_MINMAX, stream=stream)
-            snaps.snaps_scores(pop, masks, k, precision=precision, scores=scores, norm=norm,
+            snaps.snaps_scores(pop, masks, k, precision=head_prec, scores=scores, norm=norm,
                                top=top_host, top_n=100, stream=stream)   # D2H of the rankings
             snaps.snaps_release(pop)
 
@@ -263,23 +330,19 @@ def run_ours(args, rank, world, dist):
         "dtype": "f32",
         "data": "synthetic",
         "config": {"workload": workload_name(args, m), "objects": n, "subspaces": int(m), "k": k,
-                   "precision": args.precision, "l2": "flushed before every step (512 MB write)",
+                   "precision": "fp32" if (head_prec & 0xFF) == snaps.SNAPS_FP32 else "tc_f16",
+                   "index": args.index,
+                   "l2": "flushed before every step (512 MB write)",
                    "parallelism": f"replicas x{world}"},
         "distance_evals_per_s": evals_per_step * args.steps * world / (total_ms / 1e3),
-        "roofline": {"bound": "alu", "kernel": dominant,
-                     "achieved": achieved, "peak": peak, "unit": "Tevals/s",
-                     "frac": (achieved / peak) if achieved else None, "traffic": None,
-                     "peak_basis": f"{props.multi_processor_count} SMs x {COMPARES_PER_SM_CLK} "
-                                   f"FP32 compares/clk x {max_mhz:.0f} MHz (one compare per "
-                                   f"pair-subspace evaluation)",
-                     "kernel_ms_per_launch": dom_ms / max(dom_launches, 1),
-                     "measured_alu_peak": measured_alu,
-                     "frac_of_measured_alu": (achieved / measured_alu) if achieved else None},
+        "roofline": roofline,
         "phase_ms_per_step": {kname: v[0] / args.steps for kname, v in trace.items()},
         "clocks": clocks,
         "e2e": e2e,
         "gpu_launches": launches,
     }
+    if tc_leg is not None:
+        result["tc_f16"] = tc_leg
     return result
 
 

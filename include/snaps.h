@@ -69,9 +69,16 @@ typedef enum snaps_status {
 #define SNAPS_NORM_MINMAX 0x1u   /* map every feature onto [0, 1] by its min and max (Sec. 3.3) */
 #define SNAPS_NAN_TO_MEAN 0x2u   /* replace NaN by the feature's mean first (Sec. 2.1) */
 
-/* precision argument of snaps_scores / snaps_request */
+/* precision argument of snaps_scores / snaps_request: one of the two join
+ * forms, optionally OR-ed with one index choice for low-dimensional subspaces */
 #define SNAPS_FP32 0u            /* plain FP32 join */
 #define SNAPS_TC_F16 1u          /* tensor-core FP16 filter, exact FP32 recompute of survivors */
+#define SNAPS_INDEX_GRID 0x100u  /* subspaces of <= 4 features always take the grid index */
+#define SNAPS_INDEX_NONE 0x200u  /* no grid index: every subspace is joined by brute force */
+/* Without either index flag, subspaces of <= 4 features take the grid index
+ * (sort-by-cell over up to 3 of their features, Sec. 3.8.1) when
+ * n >= SNAPS_GRID_AUTO_N.  Every choice gives the same results. */
+#define SNAPS_GRID_AUTO_N 65536
 
 typedef struct snaps_ctx snaps_ctx;
 typedef struct snaps_pop snaps_pop;
@@ -149,7 +156,8 @@ snaps_status snaps_eps_selfjoin(snaps_pop *pop, const uint16_t *masks, int n_mas
  *   (the squared-difference x subspace-mask contraction on the tensor cores
  *   as a conservative FP16 filter, survivors recomputed exactly in FP32: the
  *   same results).  SNAPS_TC_F16 needs every feature to span at most 1, which
- *   SNAPS_NORM_MINMAX guarantees (EINVAL otherwise).
+ *   SNAPS_NORM_MINMAX guarantees (EINVAL otherwise).  Either may be OR-ed with
+ *   SNAPS_INDEX_GRID or SNAPS_INDEX_NONE (see their definitions).
  * scores: n_masks x 4 x n float32 raw metrics (rows SNAPS_SCORE_*), or NULL.
  *   Counts and in-degrees are exact integers stored as float.
  * norm:   n_masks x 4 x n float32, each metric mapped onto [0, 1] with
@@ -263,7 +271,8 @@ snaps_status snaps_calibrate_alu(int device, double *evals_per_s);
 #define SNAPS_PHASE_TOP 4        /* top-n ranking kernel */
 #define SNAPS_PHASE_JOIN_TC 5    /* tensor-core filtered join kernel */
 #define SNAPS_PHASE_ORDER 6      /* per-chunk row orders for the subspace-batched join */
-#define SNAPS_N_PHASES 7
+#define SNAPS_PHASE_GRID 7       /* grid index builds and grid-indexed joins */
+#define SNAPS_N_PHASES 8
 
 /* enable != 0: clear the counters and start recording, around every kernel
  * launch of every later call on this context, a pair of CUDA events on the

@@ -32,12 +32,15 @@ SNAPS_NORM_MINMAX = 0x1
 SNAPS_NAN_TO_MEAN = 0x2
 SNAPS_FP32 = 0
 SNAPS_TC_F16 = 1
+SNAPS_INDEX_GRID = 0x100
+SNAPS_INDEX_NONE = 0x200
+SNAPS_GRID_AUTO_N = 65536
 SNAPS_STATIC_MAX_N = 32768
 SNAPS_STATIC_MAX_MASKS = 32768
 SNAPS_PHASE_INDEX, SNAPS_PHASE_JOIN_TREE, SNAPS_PHASE_JOIN_LANE, SNAPS_PHASE_NORM, SNAPS_PHASE_TOP, \
-    SNAPS_PHASE_JOIN_TC, SNAPS_PHASE_ORDER = range(7)
-SNAPS_N_PHASES = 7
-PHASE_NAMES = ["index", "join_tree", "join_lane", "norm", "top", "join_tc", "order"]
+    SNAPS_PHASE_JOIN_TC, SNAPS_PHASE_ORDER, SNAPS_PHASE_GRID = range(8)
+SNAPS_N_PHASES = 8
+PHASE_NAMES = ["index", "join_tree", "join_lane", "norm", "top", "join_tc", "order", "grid"]
 
 
 class SnapsError(RuntimeError):

@@ -21,6 +21,7 @@
 #include "common.cuh"
 #include "join.cuh"
 #include "prep.cuh"
+#include "grid.cuh"
 
 // ---- error plumbing -----------------------------------------------------------------
 
@@ -239,9 +240,12 @@ snaps_status validate(const JobSpec &j)
              (long long)p->n);
     if (j.top && (j.top_n < 1 || j.top_n > 1024 || j.top_n > p->n))
         FAIL(SNAPS_EINVAL, "top_n must be in 1..min(1024, n) (got %d)", j.top_n);
-    if (j.precision != SNAPS_FP32 && j.precision != SNAPS_TC_F16)
+    const uint32_t form = j.precision & 0xFFu, index = j.precision & ~0xFFu;
+    if (form != SNAPS_FP32 && form != SNAPS_TC_F16)
         FAIL(SNAPS_EINVAL, "unknown precision %u", j.precision);
-    if (j.precision == SNAPS_TC_F16 && !p->unit_range)
+    if (index != 0u && index != SNAPS_INDEX_GRID && index != SNAPS_INDEX_NONE)
+        FAIL(SNAPS_EINVAL, "unknown index choice in precision 0x%x", j.precision);
+    if (form == SNAPS_TC_F16 && !p->unit_range)
         FAIL(SNAPS_EINVAL, "SNAPS_TC_F16 needs every feature to span at most 1 "
                            "(index the population with SNAPS_NORM_MINMAX)");
     return SNAPS_OK;
@@ -253,6 +257,8 @@ struct Plan {
     std::vector<TreeChunk> chunks;
     std::vector<MaskGroup> groups;
     std::vector<TcBlock> blocks;
+    std::vector<GridSpec> grids;  // low-dimensional subspaces on the grid index
+    int grid_max_cells = 0;
     int order_batch = 0;  // chunks whose row orders are built at a time
 };
 
@@ -281,22 +287,76 @@ size_t order_sort_temp(int64_t items, int end_bit)
     return bytes;
 }
 
+// The grid of one low-dimensional subspace: cell width eps (the default radius
+// when there is no eps join or eps is 0) with a 2^-10 margin, widened where
+// needed so that the grid has at most kGridMaxCells cells.
+GridSpec make_grid(const JobSpec &j, int m, float eps2)
+{
+    const snaps_pop *p = j.pop;
+    const uint32_t mask = j.masks[m];
+    GridSpec g{};
+    g.d = popc16(mask);
+    g.D = std::min(g.d, kGridIndexDims);
+    int t = 0;
+    for (int f = 14; f >= 0; --f)
+        if ((mask >> f) & 1u) g.feat[t++] = f;
+    for (; t < 4; ++t) g.feat[t] = -1;
+    const double eps = eps2 > 0.f ? std::sqrt((double)eps2) : std::sqrt(0.0025 * g.d);
+    double w = eps * (1.0 + 1.0 / 1024.0);
+    const int cap = (int)std::floor(std::pow((double)kGridMaxCells, 1.0 / g.D));
+    double span[3];
+    for (int q = 0; q < g.D; ++q) {
+        const int f = g.feat[q];
+        span[q] = p->kr.scale[f] > 0.f ? 1.0 / (double)p->kr.scale[f] : 0.0;
+        g.lo[q] = p->kr.lo[f];
+        w = std::max(w, span[q] / (cap - 1));
+    }
+    g.w = (float)w;
+    g.inv_w = (float)(1.0 / w);
+    g.ncells = 1;
+    for (int q = 0; q < g.D; ++q) {
+        g.nc[q] = std::min(cap, (int)std::floor(span[q] / w) + 1);
+        g.ncells *= g.nc[q];
+    }
+    for (int q = g.D; q < 3; ++q) g.nc[q] = 1;
+    g.eps2 = eps2;
+    g.slot = m;
+    return g;
+}
+
 Plan make_plan(const JobSpec &j)
 {
     Plan pl;
-    if (j.precision == SNAPS_TC_F16) {
+    auto eps2_of = [&](int m) -> float {
+        if (!j.want_eps) return -1.f;
+        if (j.eps) return j.eps[m] * j.eps[m];
+        return default_eps2(popc16(j.masks[m]));
+    };
+    // subspaces of <= kGridMaxDim features on the grid index (sort-by-cell, Sec. 3.8.1)
+    const uint32_t index = j.precision & ~0xFFu;
+    const bool grid = index == SNAPS_INDEX_GRID || (index == 0u && j.pop->n >= SNAPS_GRID_AUTO_N);
+    std::vector<int> rest;
+    for (int m = 0; m < j.n_masks; ++m) {
+        if (grid && popc16(j.masks[m]) <= kGridMaxDim) {
+            pl.grids.push_back(make_grid(j, m, eps2_of(m)));
+            pl.grid_max_cells = std::max(pl.grid_max_cells, pl.grids.back().ncells);
+        } else {
+            rest.push_back(m);
+        }
+    }
+    if ((j.precision & 0xFFu) == SNAPS_TC_F16) {
         // the tensor-core join takes any subspaces, 128 at a time; sorted by
         // dimension, so that the threads of a warp see similar hit rates
-        std::vector<int> order(j.n_masks);
-        for (int m = 0; m < j.n_masks; ++m) order[m] = m;
+        std::vector<int> order = rest;
         std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
             const int da = popc16(j.masks[a]), db = popc16(j.masks[b]);
             return da != db ? da < db : j.masks[a] < j.masks[b];
         });
-        for (int b = 0; b < j.n_masks; b += kTcBlockWidth) {
+        const int nr = (int)order.size();
+        for (int b = 0; b < nr; b += kTcBlockWidth) {
             TcBlock blk{};
             for (int c = 0; c < kTcBlockWidth; ++c) {
-                const int m = b + c < j.n_masks ? order[b + c] : j.n_masks;
+                const int m = b + c < nr ? order[b + c] : j.n_masks;
                 if (m < j.n_masks) {
                     blk.mask[c] = j.masks[m];
                     blk.eps2[c] = !j.want_eps ? -1.f
@@ -318,12 +378,7 @@ Plan make_plan(const JobSpec &j)
     std::vector<int> first(size_t(n_chunk) * kTreeWidth, -1);
     std::vector<int> count(n_chunk, 0);
     std::vector<int> extra;  // duplicates of an already-placed subspace
-    auto eps2_of = [&](int m) -> float {
-        if (!j.want_eps) return -1.f;
-        if (j.eps) return j.eps[m] * j.eps[m];
-        return default_eps2(popc16(j.masks[m]));
-    };
-    for (int m = 0; m < j.n_masks; ++m) {
+    for (int m : rest) {
         const uint32_t v = j.masks[m];
         const uint32_t c = v >> kTreeLowBits, L = v & (kTreeWidth - 1);
         int &slot = first[size_t(c) * kTreeWidth + L];
@@ -389,6 +444,7 @@ struct Layout {
     TreeChunk *chunks = nullptr;
     MaskGroup *groups = nullptr;
     TcBlock *blocks = nullptr;
+    char *grid = nullptr;  // one subspace's grid index at a time
     // per-chunk row orders (one batch)
     float4 *ocopy = nullptr;
     uint64_t *okeys = nullptr, *okeys2 = nullptr;
@@ -414,6 +470,7 @@ Layout layout_job(const JobSpec &j, const Plan &pl, char *base, bool dev_scores,
     L.chunks = cv.take<TreeChunk>(pl.chunks.size());
     L.groups = cv.take<MaskGroup>(pl.groups.size());
     L.blocks = cv.take<TcBlock>(pl.blocks.size());
+    if (!pl.grids.empty()) L.grid = cv.take<char>(grid_scratch_bytes(j.pop->n, pl.grid_max_cells));
     if (pl.order_batch > 0) {
         const size_t g = (size_t)pl.order_batch;
         const int64_t items = (int64_t)g * j.pop->n;
@@ -599,6 +656,17 @@ snaps_status run_job(snaps_ctx *ctx, const JobSpec &j, cudaStream_t st, Scratch 
     if (!pl.blocks.empty()) {
         TraceScope ts(ctx, SNAPS_PHASE_JOIN_TC, st);
         SNAPS_TRY(launch_join_tc(shape, L.blocks, (int)pl.blocks.size(), out, ctrl, st));
+    }
+    if (!pl.grids.empty()) {
+        const GridBufs gb = grid_carve(L.grid, n, pl.grid_max_cells);
+        for (const GridSpec &g : pl.grids) {
+            int sort_kernels = 0;
+            if (tracing_on(ctx))
+                SNAPS_TRY(sort_kernel_count<uint32_t>(ctx, n, grid_key_bits(g), gb.tmp, gb.tmp_bytes, gb.k_in,
+                                                      gb.k_out, gb.v_in, gb.v_out, &sort_kernels));
+            TraceScope ts(ctx, SNAPS_PHASE_GRID, st, 4 + sort_kernels);
+            SNAPS_TRY(run_grid_subspace(shape, g, out, gb, st));
+        }
     }
     if (j.norm) {
         TraceScope ts(ctx, SNAPS_PHASE_NORM, st);
