@@ -112,6 +112,7 @@ struct WarpState {
     unsigned epart[kW];             // this flush's partial sums (<= kTBuf terms of <= 2^20 + 1)
     float T[kW];                    // current k-th squared distance
     float tc[kW];                   // pass threshold max(T, eps) by L
+    float tcmax;                    // the largest of them: a bound for the whole tree
     int cnt[kW];                    // eps-neighbour counts
     float eps2[kW];                 // radii of this chunk
     float escale[kW];               // 2^20 / eps
@@ -143,6 +144,18 @@ __device__ __forceinline__ float next_up(float t) {
     // d2 < next_up(t)  <=>  d2 <= t for finite t >= 0 (a tie with the k-th
     // distance may still enter through a smaller original index); +-inf stay as they are
     return (t >= 0.f && t < CUDART_INF_F) ? __uint_as_float(__float_as_uint(t) + 1u) : t;
+}
+
+// tcmax <- the largest pass threshold of the chunk's subspaces (lane L holds
+// subspace L's).  Thresholds are floats >= 0 or -inf, whose bit patterns order
+// like their values as signed integers.
+template <int KMAX>
+__device__ __forceinline__ void update_tcmax(WarpState<KMAX> &ws)
+{
+    __syncwarp();
+    const int mx = __reduce_max_sync(dev::kFull, __float_as_int(ws.tc[dev::lane_id()]));
+    if (dev::lane_id() == 0) ws.tcmax = __int_as_float(mx);
+    __syncwarp();
 }
 
 // Process the buffered event tuples, 32 at a time with every lane busy: eps
@@ -208,7 +221,7 @@ __device__ __noinline__ bool flush_tuples(int ws_off, int count, int k)
     ws.esum[lane] += ws.epart[lane];
     ws.epart[lane] = 0u;
     if ((changed >> lane) & 1u) ws.tc[lane] = fmaxf(next_up(ws.T[lane]), eps_up(ws.eps2[lane]));
-    __syncwarp();
+    update_tcmax(ws);
     return changed != 0u;
 }
 
@@ -366,6 +379,7 @@ __device__ __noinline__ void setup_phase(int ws_off, const float4 *__restrict__ 
     ws.cnt[L] = cnt;
     ws.esum[L] = qs;
     ws.tc[L] = mine ? fmaxf(next_up(T), eps_up(e2)) : -CUDART_INF_F;
+    update_tcmax(ws);
 }
 
 template <int KMAX, int CW>
@@ -465,6 +479,13 @@ __global__ void __launch_bounds__(CW * 32, kCtasPerSm<CW>)
                 if ((high >> (f - kLB)) & 1u) v[0] = __ffma2_rn(d[f], d[f], v[0]);
             // the next step's rows load while this one is walked
             if (u + 1 < n_steps) load_step(x, (s0 + u + 1) % n_steps, lane, cur);
+            // Every node of the tree is >= its root, the fold over the high features.
+            // When no root of the step's 64 candidates is below the chunk's largest pass
+            // threshold, no subspace can pass and the walk is skipped.  The rows come in
+            // cell order over the high features, so a step's candidates lie together and
+            // far-away steps skip as a whole.
+            const float tmax = ws.tcmax;
+            if (__all_sync(dev::kFull, (v[0].x >= tmax) & (v[0].y >= tmax))) continue;
             unsigned bits = 0u;
             walk<0>(v, d, ws.tc, bits);
             const unsigned hit = __reduce_or_sync(dev::kFull, bits);
