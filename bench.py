@@ -79,6 +79,10 @@ def parse():
     ap.add_argument("--serving", type=int, default=0, metavar="R",
                     help="instead of the batching workload, run a Poisson stream of R scoring "
                          "requests through snaps_submit/snaps_poll and report p50/p99 latency")
+    ap.add_argument("--select", type=int, default=0, metavar="M",
+                    help="instead of the batching workload, time parameter selection (eps grid "
+                         "of 16 values over [0.02, 0.12] sqrt(d), k grid 2..32, top-n = 1 %% of N) "
+                         "on M seeded sample subspaces")
     ap.add_argument("--serving-max-n", type=int, default=100000)
     ap.add_argument("--serving-max-masks", type=int, default=64)
     ap.add_argument("--serving-slots", type=int, default=4)
@@ -371,6 +375,9 @@ def serving_requests(args, rng):
 
 
 def run_serving(args):
+    """The same Poisson stream of requests through the plain form and, under
+    --precision both, through the tensor-core form: identical arrivals (the rate
+    is set from the plain form's service time alone), p50/p99 latency for each."""
     import torch
 
     import paper_2405_20176_b300 as snaps
@@ -383,46 +390,62 @@ def run_serving(args):
     handles = [snaps.snaps_index(ctx, snaps_inputs.population(n, seed)) for n, seed in pops]
     tops = [torch.empty((m.size, 4, 100), dtype=torch.int32, device="cuda") for _, m, _ in reqs]
     torch.cuda.synchronize()
+    head = snaps.SNAPS_TC_F16 if args.precision == "tc_f16" else snaps.SNAPS_FP32
     # service time of one request alone, to set the arrival rate
-    t0 = time.perf_counter()
     n_cal = min(8, len(reqs))
+    for (pi, m, k), tp in zip(reqs[:n_cal], tops[:n_cal]):   # warm-up
+        snaps.snaps_scores(handles[pi], m, k, precision=head, top=tp, top_n=100)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
     for (pi, m, k), tp in zip(reqs[:n_cal], tops[:n_cal]):
-        snaps.snaps_scores(handles[pi], m, k, top=tp, top_n=100)
+        snaps.snaps_scores(handles[pi], m, k, precision=head, top=tp, top_n=100)
     torch.cuda.synchronize()
     mean_service = (time.perf_counter() - t0) / n_cal
     rate = args.serving_load / mean_service
-    gaps = rng.exponential(1.0 / rate, size=len(reqs))
-    arrivals = np.cumsum(gaps)
-    with ClockSampler(0) as clk:
-        start = time.perf_counter()
-        tickets = []
-        for (pi, m, k), tp, at in zip(reqs, tops, arrivals):
-            wait = start + at - time.perf_counter()
-            if wait > 0:
-                time.sleep(wait)
-            tickets.append(snaps.snaps_submit(ctx, handles[pi], m, k, top=tp, top_n=100))
-        results = [snaps.snaps_poll(ctx, t, -1) for t in tickets]
-        makespan = time.perf_counter() - start
-    lat = np.array([r.latency_us for r in results]) / 1e3
-    queue = np.array([r.queue_us for r in results]) / 1e3
-    work = float(sum(r.objects_x_subspaces for r in results))
-    bad = [r.status for r in results if r.status != snaps.SNAPS_OK]
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, size=len(reqs)))
+
+    def stream(precision):
+        with ClockSampler(0) as clk:
+            start = time.perf_counter()
+            tickets = []
+            for (pi, m, k), tp, at in zip(reqs, tops, arrivals):
+                wait = start + at - time.perf_counter()
+                if wait > 0:
+                    time.sleep(wait)
+                tickets.append(snaps.snaps_submit(ctx, handles[pi], m, k, precision=precision, top=tp,
+                                                  top_n=100))
+            results = [snaps.snaps_poll(ctx, t, -1) for t in tickets]
+            makespan = time.perf_counter() - start
+        lat = np.array([r.latency_us for r in results]) / 1e3
+        queue = np.array([r.queue_us for r in results]) / 1e3
+        work = float(sum(r.objects_x_subspaces for r in results))
+        bad = [r.status for r in results if r.status != snaps.SNAPS_OK]
+        return {"value": work / makespan, "unit": "objects*subspaces/s",
+                "p50_latency_ms": float(np.percentile(lat, 50)),
+                "p99_latency_ms": float(np.percentile(lat, 99)),
+                "p50_queue_ms": float(np.percentile(queue, 50)),
+                "p99_queue_ms": float(np.percentile(queue, 99)),
+                "requests": len(results), "failed": len(bad), "makespan_s": makespan,
+                "clocks": clk.summary()}
+
+    main = stream(head)
+    tc = stream(snaps.SNAPS_TC_F16) if args.precision == "both" else None
     for h in handles:
         snaps.snaps_release(h)
     snaps.snaps_destroy(ctx)
-    return {
+    out = {
         "metric": "objects*subspaces/s (serving stream)",
-        "value": work / makespan,
+        "value": main["value"],
         "unit": "objects*subspaces/s",
         "n_gpus": 1,
         "higher_is_better": True,
-        "p50_latency_ms": float(np.percentile(lat, 50)),
-        "p99_latency_ms": float(np.percentile(lat, 99)),
-        "p50_queue_ms": float(np.percentile(queue, 50)),
-        "p99_queue_ms": float(np.percentile(queue, 99)),
-        "requests": len(results),
-        "failed": len(bad),
-        "makespan_s": makespan,
+        "p50_latency_ms": main["p50_latency_ms"],
+        "p99_latency_ms": main["p99_latency_ms"],
+        "p50_queue_ms": main["p50_queue_ms"],
+        "p99_queue_ms": main["p99_queue_ms"],
+        "requests": main["requests"],
+        "failed": main["failed"],
+        "makespan_s": main["makespan_s"],
         "arrival_rate_per_s": rate,
         "mean_service_alone_s": mean_service,
         "dtype": "f32",
@@ -432,9 +455,50 @@ def run_serving(args):
                                f"populations N ~ LogUniform(1e3, {args.serving_max_n}); 1-"
                                f"{args.serving_max_masks} subspaces (d uniform 2..15); "
                                f"k in {{5,10,20}}; eps = 0.05*sqrt(d); top-100 outputs",
-                   "slots": args.serving_slots, "precision": args.precision},
-        "clocks": clk.summary(),
+                   "slots": args.serving_slots,
+                   "precision": "tc_f16" if head == snaps.SNAPS_TC_F16 else "fp32"},
+        "clocks": main["clocks"],
     }
+    if tc is not None:
+        tc["vs_plain"] = tc["value"] / main["value"]
+        out["tc_f16"] = tc
+    return out
+
+
+# ---- parameter selection ------------------------------------------------------------------------
+
+def run_select(args):
+    import torch
+
+    import paper_2405_20176_b300 as snaps
+
+    torch.cuda.set_device(0)
+    x = snaps_inputs.population(args.n, 0)
+    masks = snaps_inputs.mask_sample(args.select, SAMPLE_SEED)
+    d = np.array([bin(int(v)).count("1") for v in masks])
+    emin = (0.02 * np.sqrt(d)).astype(np.float32)
+    emax = (0.12 * np.sqrt(d)).astype(np.float32)
+    k_grid = [2, 3, 4, 6, 8, 12, 16, 24, 32]
+    top_n = max(1, args.n // 100)
+    ctx = snaps.snaps_create(0)
+    pop = snaps.snaps_index(ctx, torch.from_numpy(x).cuda())
+    snaps.snaps_select(pop, masks[:2], emin[:2], emax[:2], 16, k_grid, top_n)   # warm-up
+    torch.cuda.synchronize()
+    snaps.snaps_trace(ctx, True)
+    t0 = time.perf_counter()
+    _, e_sel, _, k_sel = snaps.snaps_select(pop, masks, emin, emax, 16, k_grid, top_n)
+    torch.cuda.synchronize()
+    el = time.perf_counter() - t0
+    tr = snaps.snaps_trace_read(ctx)
+    snaps.snaps_release(pop)
+    snaps.snaps_destroy(ctx)
+    return {"metric": "subspaces selected/s (eps and k grids)", "value": masks.size / el,
+            "unit": "subspaces/s", "n_gpus": 1, "higher_is_better": True,
+            "seconds": el, "phase_ms": {k: v[0] for k, v in tr.items() if v[1]},
+            "eps_select_histogram": np.bincount(e_sel.ravel(), minlength=16).tolist(),
+            "k_select_values": np.bincount(np.asarray(k_grid)[k_sel.ravel()], minlength=33).nonzero()[0].tolist(),
+            "config": {"workload": f"N={args.n} objects, {masks.size} sampled subspaces, eps grid 16 x "
+                                   f"[0.02, 0.12] sqrt(d), k grid {k_grid}, top-n {top_n}"}}
 
 
 # ---- CPU oracle legs -------------------------------------------------------------------------
@@ -517,6 +581,9 @@ def main():
         return 0
     if args.serving:
         print(json.dumps(run_serving(args)))
+        return 0
+    if args.select:
+        print(json.dumps(run_select(args)))
         return 0
     dist = None
     if world > 1:
