@@ -18,7 +18,13 @@ It follows Gowanlock et al., arXiv 2405.20176:
 * :func:`top` -- the first ``n`` objects of each ranking, ties by index;
 * :func:`normalised_scores` -- each metric mapped onto [0, 1] with 1 = most
   outlying, from population min / max.  The paper normalises features, not
-  scores; this output is the library's own, defined here in FP64.
+  scores; this output is the library's own, defined here in FP64;
+* :func:`similarity`, :func:`select_index`, :func:`select_eps`,
+  :func:`select_k` -- the over-/underfitting parameter selection (Sec. 3.5.2,
+  Eq. 2 and 3; Sec. 3.6.2), one full join per grid value;
+* :func:`selectivity`, :func:`eps_for_selectivity` -- the selectivity of
+  Sec. 3.5.3 by its definition, and the radius at which a sampled distance
+  histogram reaches a target selectivity.
 
 Every function states the passage it follows.  Parity: pinned by the Table 2
 worked example, closed-form lattices and duplicates, invariants and an
@@ -244,3 +250,140 @@ def subspace(xn: np.ndarray, mask: int, k: int, eps: float | None = None,
 def default_eps(mask: int) -> float:
     """eps = 0.05 * sqrt(d) for a d-feature subspace."""
     return 0.05 * math.sqrt(popcount(mask))
+
+
+# ---- parameter selection (Sec. 3.5.2, Eq. 2 and 3; Sec. 3.6.2) -------------------------------
+
+def similarity(top_a, top_b) -> float:
+    """Eq. 2: the fraction f of the n objects of top-n list ``top_a`` that are
+    also in top-n list ``top_b`` (both of length n)."""
+    n = len(top_a)
+    return len(set(int(v) for v in top_a) & set(int(v) for v in top_b)) / n
+
+
+def select_index(u_min, u_max) -> int:
+    """Eq. 3: the grid index j minimising |U^min_j - U^max_j| (the smallest j
+    when several minimise it -- the paper does not say; this is the reading)."""
+    gap = np.abs(np.asarray(u_min, dtype=np.float64) - np.asarray(u_max, dtype=np.float64))
+    return int(np.flatnonzero(gap == gap.min())[0])
+
+
+def u_curves(tops) -> tuple[np.ndarray, np.ndarray]:
+    """U^min and U^max (Sec. 3.5.2) of a grid of top-n lists ordered from the
+    smallest to the largest grid value: each list compared with the first and
+    with the last."""
+    u_min = np.array([similarity(tops[0], t) for t in tops])
+    u_max = np.array([similarity(tops[-1], t) for t in tops])
+    return u_min, u_max
+
+
+def eps_grid(eps_min: float, eps_max: float, count: int) -> np.ndarray:
+    """``count`` evenly spaced radii over [eps_min, eps_max] (Sec. 3.5.2),
+    computed in FP64 and rounded to FP32 (the library's radius precision)."""
+    j = np.arange(count, dtype=np.float64)
+    return (eps_min + j * (eps_max - eps_min) / (count - 1)).astype(np.float32)
+
+
+def select_eps(xn: np.ndarray, mask: int, eps_min: float, eps_max: float, count: int, top_n: int):
+    """eps selection for one subspace by definition: a full eps-join at every
+    grid radius (eps^2 = eps * eps in FP32, as the library squares a given
+    radius), the count and mean-distance rankings, their top-n lists, U^min,
+    U^max and the selected index.  Returns (u, sel, tops) with u of shape
+    (2 metrics, 2, count), sel of shape (2,) and tops of shape (count, 2, top_n)."""
+    x64 = np.asarray(xn, dtype=np.float64)
+    n = x64.shape[0]
+    tops = []
+    for e in eps_grid(eps_min, eps_max, count):
+        e2 = float(np.float32(e) * np.float32(e))
+        res = join(x64, mask, 0, e2)
+        s = np.zeros((N_SCORES, n))
+        c = res.eps_count.astype(np.float64)
+        s[EPS_COUNT] = c
+        s[EPS_MEAN] = np.where(c > 0, res.eps_sum / np.where(c > 0, c, 1.0), 0.0)
+        tops.append(top(s, top_n)[[EPS_COUNT, EPS_MEAN]])
+    tops = np.array(tops)
+    u = np.zeros((2, 2, count))
+    sel = np.zeros(2, dtype=np.int64)
+    for r in range(2):
+        u[r, 0], u[r, 1] = u_curves(tops[:, r])
+        sel[r] = select_index(u[r, 0], u[r, 1])
+    return u, sel, tops
+
+
+def select_k(xn: np.ndarray, mask: int, k_grid, top_n: int):
+    """k selection for one subspace by definition (Sec. 3.6.2): a full kNN join
+    at every grid k, the in-degree and mean-distance rankings, their top-n
+    lists, U^min, U^max and the selected index.  Returns (u, sel, tops) shaped
+    (2, 2, len(k_grid)), (2,), (len(k_grid), 2, top_n)."""
+    x64 = np.asarray(xn, dtype=np.float64)
+    n = x64.shape[0]
+    tops = []
+    for kj in k_grid:
+        res = join(x64, mask, int(kj), None)
+        s = np.zeros((N_SCORES, n))
+        s[KNN_INDEG] = np.bincount(res.knn_idx.ravel(), minlength=n).astype(np.float64)
+        s[KNN_MEAN] = np.sqrt(res.knn_d2).mean(axis=1)
+        tops.append(top(s, top_n)[[KNN_INDEG, KNN_MEAN]])
+    tops = np.array(tops)
+    u = np.zeros((2, 2, len(k_grid)))
+    sel = np.zeros(2, dtype=np.int64)
+    for r in range(2):
+        u[r, 0], u[r, 1] = u_curves(tops[:, r])
+        sel[r] = select_index(u[r, 0], u[r, 1])
+    return u, sel, tops
+
+
+# ---- eps range from selectivity (Sec. 3.5.3) ------------------------------------------------
+
+def selectivity(xn: np.ndarray, mask: int, eps: float) -> float:
+    """Sec. 3.5.3: s = (|A| - |D|) / |D|, the mean number of eps-neighbours per
+    object with the object itself excluded, from a full eps-join (FP64,
+    eps^2 = eps * eps)."""
+    res = join(np.asarray(xn, dtype=np.float64), mask, 0, float(eps) * float(eps))
+    return float(res.eps_count.mean())
+
+
+def sample_rows(n: int, m: int) -> np.ndarray:
+    """The m sampled objects of the selectivity estimate: original indices
+    floor(s n / m), s = 0 .. m - 1 (evenly strided; all objects when m = n)."""
+    return (np.arange(m, dtype=np.int64) * n) // m
+
+
+def sample_distances(xn: np.ndarray, mask: int, n_sample: int) -> tuple[np.ndarray, int]:
+    """Distances (FP64) from each of m = min(n_sample, n) sampled objects to
+    every other object, concatenated; returns them and m."""
+    x64 = np.asarray(xn, dtype=np.float64)
+    n = x64.shape[0]
+    m = min(int(n_sample), n)
+    cols = [f for f in range(x64.shape[1]) if (mask >> f) & 1]
+    xs = x64[:, cols]
+    out = []
+    for s in sample_rows(n, m):
+        d = np.sqrt(((xs - xs[s]) ** 2).sum(axis=1))
+        out.append(np.delete(d, s))
+    return np.concatenate(out), m
+
+
+def eps_for_selectivity(xn: np.ndarray, mask: int, targets, n_sample: int = 1024, n_bins: int = 4096):
+    """Sec. 3.5.3, the sampled estimate of the radius for a selectivity, in the
+    steps the paper gives: (1) the distances from a sample of objects to all
+    others; (2) their mean eps_mean, the upper bound of a practical radius;
+    (3) a histogram of the distances below eps_mean (n_bins bins of width
+    w = eps_mean / n_bins, bin floor(d / w)); (4) its cumulative counts, which
+    divided by the sample size m give the mean neighbour count at each bin's
+    upper edge; (5) for every target, the first edge (b + 1) w at which that
+    count reaches the target, eps_mean when none does.  Returns (eps, eps_mean)
+    in FP64; all zeros when every distance is 0."""
+    d, m = sample_distances(xn, mask, n_sample)
+    eps_mean = float(d.mean())
+    targets = np.atleast_1d(np.asarray(targets, dtype=np.float64))
+    if eps_mean == 0.0:
+        return np.zeros(targets.size), 0.0
+    w = eps_mean / n_bins
+    b = np.floor(d / w).astype(np.int64)
+    cum = np.cumsum(np.bincount(b[b < n_bins], minlength=n_bins))
+    eps = np.empty(targets.size)
+    for t, s in enumerate(targets):
+        hit = np.flatnonzero(cum >= s * m)
+        eps[t] = (hit[0] + 1) * w if hit.size else eps_mean
+    return eps, eps_mean
