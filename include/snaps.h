@@ -174,6 +174,69 @@ snaps_status snaps_scores(snaps_pop *pop, const uint16_t *masks, int n_masks, in
                           const float *eps, uint32_t precision, float *scores,
                           float *norm, int32_t *top, int top_n, void *stream);
 
+/* ---- parameter selection: the over- / underfitting trade-off ---- */
+
+#define SNAPS_SELECT_MAX_GRID 64  /* values per parameter grid */
+
+/* Select eps and k for every subspace in `masks` as Sec. 3.5.2 (eps, Eq. 2
+ * and 3) and Sec. 3.6.2 (k) describe.  For each grid value the population is
+ * ranked (Sec. 3.4, as snaps_scores ranks it); U^min_j and U^max_j are the
+ * fractions of the top-n objects that the ranking at grid value j shares with
+ * the ranking at the smallest and at the largest grid value (Eq. 2); the
+ * selected index minimises |U^min_j - U^max_j| (Eq. 3; the smallest such j on
+ * ties).  As in Sec. 3.5.3 and 3.6.2, one join per subspace at the largest
+ * grid value gives the results at all of them.
+ * masks: n_masks host masks.
+ * eps grid (used when u_eps or eps_select is non-NULL): n_eps values
+ *   (2..SNAPS_SELECT_MAX_GRID) evenly spaced over [eps_min[m], eps_max[m]]
+ *   (host arrays, 0 <= eps_min < eps_max): eps_j = eps_min + j (eps_max -
+ *   eps_min) / (n_eps - 1), computed in FP64 and rounded to FP32.  Metrics:
+ *   0 = eps-neighbour count, 1 = mean eps-neighbour distance.
+ * k grid (used when u_k or k_select is non-NULL): n_k (2..64) strictly
+ *   ascending values in 1..min(32, n - 1), host array.  Metrics: 0 = kNN
+ *   in-degree, 1 = mean kNN distance.
+ * top_n: the n of Eq. 2 (the paper uses 1 % of the population), 1..min(n, 1024).
+ * Outputs (host or device, caller-owned, any may be NULL):
+ *   u_eps:      n_masks x 2 metrics x 2 (0 = U^min, 1 = U^max) x n_eps floats;
+ *   eps_select: n_masks x 2 metrics int32, the selected grid index;
+ *   u_k, k_select: the same for the k grid.
+ * The call synchronises `stream`.
+ * Errors: EINVAL (bad masks, grids, top_n, or no output), ENOMEM, ECUDA. */
+snaps_status snaps_select(snaps_pop *pop, const uint16_t *masks, int n_masks,
+                          const float *eps_min, const float *eps_max, int n_eps,
+                          const int32_t *k_grid, int n_k, int top_n,
+                          float *u_eps, int32_t *eps_select, float *u_k, int32_t *k_select,
+                          void *stream);
+
+/* ---- eps range from selectivity ---- */
+
+#define SNAPS_SELECTIVITY_MAX_SAMPLE 65536
+#define SNAPS_SELECTIVITY_MAX_BINS 4096
+
+/* Radii at which the mean number of eps-neighbours per object (itself
+ * excluded: the selectivity of Sec. 3.5.3, s = (|A| - |D|) / |D|) reaches
+ * each target, estimated from a sample as Sec. 3.5.3 describes: m =
+ * min(n_sample, n) objects (original indices floor(s n / m), s < m) against
+ * every other object.  eps_mean, the mean of those m (n - 1) distances, bounds
+ * the search; they are counted in n_bins bins of width eps_mean / n_bins over
+ * [0, eps_mean), and the radius of a target is the first bin edge (b + 1)
+ * eps_mean / n_bins at which the cumulative count reaches target * m, or
+ * eps_mean when none does.  The paper's grid ends are the targets 0.001 n
+ * (eps_min) and 0.15 n (eps_max).  Distances are the library's FP32 ones;
+ * eps_mean comes from an exact sum of distances quantised to 2^-20.
+ * masks: n_masks host masks.  targets: n_targets (1..32) host doubles in
+ *   (0, n - 1], mean neighbours per object.
+ * n_sample: 1..SNAPS_SELECTIVITY_MAX_SAMPLE, with n_sample (n - 1) < 2^41;
+ *   n_bins: 1..SNAPS_SELECTIVITY_MAX_BINS.
+ * Outputs (host or device, caller-owned): eps, n_masks x n_targets floats;
+ *   eps_mean, n_masks floats (may be NULL).
+ * The call synchronises `stream`.
+ * Errors: EINVAL (bad masks, targets, sample or bins; n < 2; eps NULL),
+ * ENOMEM, ECUDA. */
+snaps_status snaps_eps_selectivity(snaps_pop *pop, const uint16_t *masks, int n_masks,
+                                   const double *targets, int n_targets, int n_sample, int n_bins,
+                                   float *eps, float *eps_mean, void *stream);
+
 /* ---- serving: continuous batching of scoring requests ---- */
 
 /* One scoring request: snaps_scores on a resident population.  masks and
@@ -272,7 +335,8 @@ snaps_status snaps_calibrate_alu(int device, double *evals_per_s);
 #define SNAPS_PHASE_JOIN_TC 5    /* tensor-core filtered join kernel */
 #define SNAPS_PHASE_ORDER 6      /* per-chunk row orders for the subspace-batched join */
 #define SNAPS_PHASE_GRID 7       /* grid index builds and grid-indexed joins */
-#define SNAPS_N_PHASES 8
+#define SNAPS_PHASE_SELECT 8     /* parameter-selection joins (snaps_select) */
+#define SNAPS_N_PHASES 9
 
 /* enable != 0: clear the counters and start recording, around every kernel
  * launch of every later call on this context, a pair of CUDA events on the

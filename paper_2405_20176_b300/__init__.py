@@ -38,9 +38,12 @@ SNAPS_GRID_AUTO_N = 65536
 SNAPS_STATIC_MAX_N = 32768
 SNAPS_STATIC_MAX_MASKS = 32768
 SNAPS_PHASE_INDEX, SNAPS_PHASE_JOIN_TREE, SNAPS_PHASE_JOIN_LANE, SNAPS_PHASE_NORM, SNAPS_PHASE_TOP, \
-    SNAPS_PHASE_JOIN_TC, SNAPS_PHASE_ORDER, SNAPS_PHASE_GRID = range(8)
-SNAPS_N_PHASES = 8
-PHASE_NAMES = ["index", "join_tree", "join_lane", "norm", "top", "join_tc", "order", "grid"]
+    SNAPS_PHASE_JOIN_TC, SNAPS_PHASE_ORDER, SNAPS_PHASE_GRID, SNAPS_PHASE_SELECT = range(9)
+SNAPS_N_PHASES = 9
+SNAPS_SELECT_MAX_GRID = 64
+SNAPS_SELECTIVITY_MAX_SAMPLE = 65536
+SNAPS_SELECTIVITY_MAX_BINS = 4096
+PHASE_NAMES = ["index", "join_tree", "join_lane", "norm", "top", "join_tc", "order", "grid", "select"]
 
 
 class SnapsError(RuntimeError):
@@ -96,6 +99,8 @@ def lib():
             "snaps_calibrate_alu": ([i32, p], i32),
             "snaps_scores_static": ([i32, p, i64, i32, u32, p, i32, i32, p, p, p, i32, p], i32),
             "snaps_trace_read": ([p, p, p], i32),
+            "snaps_select": ([p, p, i32, p, p, i32, p, i32, i32, p, p, p, p, p], i32),
+            "snaps_eps_selectivity": ([p, p, i32, p, i32, i32, i32, p, p, p], i32),
         }
         for name, (args, res) in sig.items():
             fn = getattr(L, name)
@@ -226,6 +231,54 @@ def snaps_scores(pop: int, masks, k: int, eps=None, precision: int = SNAPS_FP32,
     _check(lib().snaps_scores(pop, m.ctypes.data, m.size, k, None if e is None else e.ctypes.data,
                               precision, _ptr(scores), _ptr(norm), _ptr(top),
                               top_n if top is not None else 0, _stream(stream)), "snaps_scores")
+
+
+def snaps_select(pop: int, masks, eps_min=None, eps_max=None, n_eps: int = 0, k_grid=None,
+                 top_n: int = 1, stream=None):
+    """Parameter selection (Sec. 3.5.2 Eq. 2-3, Sec. 3.6.2) through the C ABI.
+    eps_min / eps_max: per-subspace grid ends (None skips the eps grid); k_grid:
+    ascending k values (None skips it).  Returns (u_eps, eps_select, u_k,
+    k_select) as NumPy arrays shaped (m, 2, 2, n_eps), (m, 2), (m, 2, 2, n_k),
+    (m, 2); the skipped halves are None."""
+    m = _masks(masks)
+    want_eps = eps_min is not None
+    want_k = k_grid is not None
+    emin = np.ascontiguousarray(np.broadcast_to(np.asarray(eps_min, dtype=np.float32), m.shape)) \
+        if want_eps else None
+    emax = np.ascontiguousarray(np.broadcast_to(np.asarray(eps_max, dtype=np.float32), m.shape)) \
+        if want_eps else None
+    kg = np.ascontiguousarray(np.asarray(k_grid, dtype=np.int32)) if want_k else None
+    n_k = int(kg.size) if want_k else 0
+    u_eps = np.zeros((m.size, 2, 2, n_eps), dtype=np.float32) if want_eps else None
+    e_sel = np.zeros((m.size, 2), dtype=np.int32) if want_eps else None
+    u_k = np.zeros((m.size, 2, 2, n_k), dtype=np.float32) if want_k else None
+    k_sel = np.zeros((m.size, 2), dtype=np.int32) if want_k else None
+    _check(lib().snaps_select(pop, m.ctypes.data, m.size, _ptr(emin), _ptr(emax), n_eps if want_eps else 0,
+                              _ptr(kg), n_k, top_n, _ptr(u_eps), _ptr(e_sel), _ptr(u_k), _ptr(k_sel),
+                              _stream(stream)), "snaps_select")
+    return u_eps, e_sel, u_k, k_sel
+
+
+def snaps_eps_selectivity(pop: int, masks, targets, n_sample: int = 1024, n_bins: int = 4096, stream=None):
+    """Radii at which the sampled mean neighbour count reaches each target
+    (Sec. 3.5.3) through the C ABI.  targets: mean neighbours per object.
+    Returns (eps, eps_mean) as NumPy arrays shaped (m, len(targets)), (m,)."""
+    m = _masks(masks)
+    t = np.ascontiguousarray(np.atleast_1d(np.asarray(targets, dtype=np.float64)))
+    eps = np.zeros((m.size, t.size), dtype=np.float32)
+    mean = np.zeros(m.size, dtype=np.float32)
+    _check(lib().snaps_eps_selectivity(pop, m.ctypes.data, m.size, t.ctypes.data, t.size, n_sample, n_bins,
+                                       eps.ctypes.data, mean.ctypes.data, _stream(stream)),
+           "snaps_eps_selectivity")
+    return eps, mean
+
+
+def snaps_eps_range(pop: int, n: int, masks, s_min: float = 0.001, s_max: float = 0.15, n_sample: int = 1024,
+                    n_bins: int = 4096, stream=None):
+    """The eps grid ends of Sec. 3.5.3: the radii of selectivities s_min n and
+    s_max n.  Returns (eps_min, eps_max), each shaped (m,)."""
+    eps, _ = snaps_eps_selectivity(pop, masks, [s_min * n, s_max * n], n_sample, n_bins, stream)
+    return eps[:, 0].copy(), eps[:, 1].copy()
 
 
 def snaps_scores_static(device: int, feat, masks, k: int, eps=None, flags: int = SNAPS_NORM_MINMAX,

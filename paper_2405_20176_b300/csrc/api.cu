@@ -16,12 +16,14 @@
 #include <mutex>
 #include <thread>
 #include <unordered_map>
+#include <tuple>
 #include <vector>
 
 #include "common.cuh"
 #include "join.cuh"
 #include "prep.cuh"
 #include "grid.cuh"
+#include "select.cuh"
 
 // ---- error plumbing -----------------------------------------------------------------
 
@@ -1087,6 +1089,230 @@ snaps_status snaps_eps_selfjoin(snaps_pop *pop, const uint16_t *masks, int n_mas
     j.eps_mean = mean_dist;
     std::lock_guard<std::mutex> g(pop->ctx->sync_mu);
     return run_job(pop->ctx, j, (cudaStream_t)stream, pop->ctx->scratch, pop->ctx->ctrl, false);
+}
+
+namespace {
+
+// Eq. 2's intersection count of two top-n lists (sorted copies, two-pointer merge).
+int top_overlap(const int32_t *a, const int32_t *b, int n)
+{
+    std::vector<int32_t> x(a, a + n), y(b, b + n);
+    std::sort(x.begin(), x.end());
+    std::sort(y.begin(), y.end());
+    int c = 0;
+    for (size_t p = 0, q = 0; p < x.size() && q < y.size();) {
+        if (x[p] == y[q]) {
+            ++c;
+            ++p;
+            ++q;
+        } else if (x[p] < y[q]) {
+            ++p;
+        } else {
+            ++q;
+        }
+    }
+    return c;
+}
+
+// U^min, U^max (Eq. 2) of one metric over a grid of G top-n lists (list g at
+// tops + g * stride), and the selected index (Eq. 3; the first on ties).
+int select_grid(const int32_t *tops, size_t stride, int G, int top_n, float *u_min, float *u_max)
+{
+    int best = 0, best_gap = INT32_MAX;
+    for (int g = 0; g < G; ++g) {
+        const int cmin = top_overlap(tops, tops + g * stride, top_n);
+        const int cmax = top_overlap(tops + (G - 1) * stride, tops + g * stride, top_n);
+        u_min[g] = (float)cmin / (float)top_n;
+        u_max[g] = (float)cmax / (float)top_n;
+        const int gap = std::abs(cmin - cmax);
+        if (gap < best_gap) {
+            best_gap = gap;
+            best = g;
+        }
+    }
+    return best;
+}
+
+}  // namespace
+
+snaps_status snaps_select(snaps_pop *pop, const uint16_t *masks, int n_masks, const float *eps_min,
+                          const float *eps_max, int n_eps, const int32_t *k_grid, int n_k, int top_n,
+                          float *u_eps, int32_t *eps_select, float *u_k, int32_t *k_select, void *stream)
+{
+    clear_error();
+    if (!pop) FAIL(SNAPS_EINVAL, "pop is NULL");
+    SNAPS_TRY(device_guard(pop->ctx));
+    snaps_ctx *ctx = pop->ctx;
+    const int64_t n = pop->n;
+    if (n_masks < 1 || !masks || is_device_ptr(masks)) FAIL(SNAPS_EINVAL, "masks: a host array of >= 1 masks");
+    for (int m = 0; m < n_masks; ++m)
+        if (popc16(masks[m]) < 2 || (masks[m] >> pop->f) != 0)
+            FAIL(SNAPS_EINVAL, "mask %d (0x%x) must have 2..%d bits, all below feature %d", m, masks[m], pop->f,
+                 pop->f);
+    const bool want_eps = u_eps || eps_select, want_k = u_k || k_select;
+    if (!want_eps && !want_k) FAIL(SNAPS_EINVAL, "no output requested");
+    if (want_eps) {
+        if (n_eps < 2 || n_eps > kSelectMaxGrid) FAIL(SNAPS_EINVAL, "n_eps must be in 2..%d", kSelectMaxGrid);
+        if (!eps_min || !eps_max || is_device_ptr(eps_min) || is_device_ptr(eps_max))
+            FAIL(SNAPS_EINVAL, "eps_min / eps_max: host arrays of n_masks values");
+        for (int m = 0; m < n_masks; ++m)
+            if (!(eps_min[m] >= 0.f && eps_max[m] > eps_min[m] && eps_max[m] < 1e18f))
+                FAIL(SNAPS_EINVAL, "subspace %d: need 0 <= eps_min < eps_max (finite)", m);
+    }
+    if (want_k) {
+        if (n_k < 2 || n_k > kSelectMaxGrid) FAIL(SNAPS_EINVAL, "n_k must be in 2..%d", kSelectMaxGrid);
+        if (!k_grid || is_device_ptr(k_grid)) FAIL(SNAPS_EINVAL, "k_grid: a host array");
+        for (int g = 0; g < n_k; ++g)
+            if (k_grid[g] < 1 || (g > 0 && k_grid[g] <= k_grid[g - 1]))
+                FAIL(SNAPS_EINVAL, "k_grid must be strictly ascending from >= 1");
+        if (k_grid[n_k - 1] > SNAPS_MAX_K || k_grid[n_k - 1] > n - 1)
+            FAIL(SNAPS_EINVAL, "k_grid values must be <= min(%d, n - 1)", SNAPS_MAX_K);
+    }
+    if (top_n < 1 || top_n > 1024 || top_n > n) FAIL(SNAPS_EINVAL, "top_n must be in 1..min(1024, n)");
+    const int G = want_eps ? n_eps : 0, K = want_k ? n_k : 0;
+    const int kmax = want_k ? k_grid[n_k - 1] : 0;
+    const int slots = std::max(G, K);
+    cudaStream_t st = (cudaStream_t)stream;
+
+    std::lock_guard<std::mutex> lock(ctx->sync_mu);
+    Carver cv;
+    auto layout = [&](char *base) {
+        cv = Carver();
+        cv.base = base;
+        float *es = cv.take<float>((size_t)std::max(G, 1) * 4 * n);
+        float *ks = cv.take<float>((size_t)std::max(K, 1) * 4 * n);
+        int32_t *ki = cv.take<int32_t>((size_t)n * std::max(kmax, 1));
+        float *kd = cv.take<float>((size_t)n * std::max(kmax, 1));
+        int32_t *tp = cv.take<int32_t>((size_t)slots * 4 * top_n);
+        return std::make_tuple(es, ks, ki, kd, tp);
+    };
+    layout(nullptr);
+    SNAPS_TRY(scratch_reserve(ctx, ctx->scratch, cv.off + 256));
+    auto [eps_scores, k_scores, knn_idx, knn_d2, tops_dev] = layout((char *)ctx->scratch.ptr);
+    std::vector<int32_t> tops((size_t)slots * 4 * top_n);
+    std::vector<float> ue((size_t)n_masks * 4 * std::max(G, 1)), uk((size_t)n_masks * 4 * std::max(K, 1));
+    std::vector<int32_t> es((size_t)n_masks * 2), kse((size_t)n_masks * 2);
+
+    for (int m = 0; m < n_masks; ++m) {
+        SelectSpec sp{};
+        sp.mask = masks[m];
+        sp.n_eps = G;
+        if (G > 0) {
+            for (int g = 0; g < G; ++g) {
+                const float e = (float)((double)eps_min[m] + g * ((double)eps_max[m] - (double)eps_min[m]) / (G - 1));
+                sp.e2[g] = e * e;
+            }
+            sp.qscale = (float)(16777216.0 / (double)eps_max[m]);
+        }
+        sp.kmax = kmax;
+        SNAPS_CHECK_CUDA(cudaMemsetAsync(eps_scores, 0, (size_t)std::max(G, 1) * 4 * n * sizeof(float), st));
+        SNAPS_CHECK_CUDA(cudaMemsetAsync(k_scores, 0, (size_t)std::max(K, 1) * 4 * n * sizeof(float), st));
+        {
+            TraceScope ts(ctx, SNAPS_PHASE_SELECT, st, 1 + (K > 0 ? 1 : 0));
+            SNAPS_TRY(launch_select_join(pop->x, n, sp, eps_scores, knn_idx, knn_d2, st));
+            if (K > 0) {
+                KGrid kg{};
+                kg.n = K;
+                for (int g = 0; g < K; ++g) kg.k[g] = k_grid[g];
+                SNAPS_TRY(launch_select_k(knn_idx, knn_d2, n, kmax, kg, k_scores, st));
+            }
+        }
+        for (int half = 0; half < 2; ++half) {
+            const int S = half == 0 ? G : K;
+            if (S == 0) continue;
+            {
+                TraceScope ts(ctx, SNAPS_PHASE_TOP, st);
+                SNAPS_TRY(launch_top(half == 0 ? eps_scores : k_scores, n, S, top_n, tops_dev, st));
+            }
+            SNAPS_CHECK_CUDA(cudaMemcpyAsync(tops.data(), tops_dev, (size_t)S * 4 * top_n * sizeof(int32_t),
+                                             cudaMemcpyDeviceToHost, st));
+            SNAPS_CHECK_CUDA(cudaStreamSynchronize(st));
+            for (int r = 0; r < 2; ++r) {
+                const int row = half == 0 ? r : 2 + r;  // eps: count, mean; k: in-degree, mean
+                float *u = (half == 0 ? ue.data() : uk.data()) + ((size_t)m * 2 + r) * 2 * S;
+                const int sel = select_grid(tops.data() + (size_t)row * top_n, (size_t)4 * top_n, S, top_n, u,
+                                            u + S);
+                (half == 0 ? es : kse)[(size_t)m * 2 + r] = sel;
+            }
+        }
+    }
+    auto put = [&](void *dst, const void *src, size_t bytes) -> snaps_status {
+        if (!dst) return SNAPS_OK;
+        const cudaMemcpyKind kind = is_device_ptr(dst) ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost;
+        SNAPS_CHECK_CUDA(cudaMemcpyAsync(dst, src, bytes, kind, st));
+        return SNAPS_OK;
+    };
+    if (G > 0) {
+        SNAPS_TRY(put(u_eps, ue.data(), (size_t)n_masks * 4 * G * sizeof(float)));
+        SNAPS_TRY(put(eps_select, es.data(), (size_t)n_masks * 2 * sizeof(int32_t)));
+    }
+    if (K > 0) {
+        SNAPS_TRY(put(u_k, uk.data(), (size_t)n_masks * 4 * K * sizeof(float)));
+        SNAPS_TRY(put(k_select, kse.data(), (size_t)n_masks * 2 * sizeof(int32_t)));
+    }
+    SNAPS_CHECK_CUDA(cudaStreamSynchronize(st));
+    return SNAPS_OK;
+}
+
+static_assert(SNAPS_SELECTIVITY_MAX_BINS == kSelectHistBins, "histogram bins of the C ABI and the kernel");
+
+snaps_status snaps_eps_selectivity(snaps_pop *pop, const uint16_t *masks, int n_masks, const double *targets,
+                                   int n_targets, int n_sample, int n_bins, float *eps, float *eps_mean,
+                                   void *stream)
+{
+    clear_error();
+    if (!pop) FAIL(SNAPS_EINVAL, "pop is NULL");
+    SNAPS_TRY(device_guard(pop->ctx));
+    snaps_ctx *ctx = pop->ctx;
+    const int64_t n = pop->n;
+    if (n < 2) FAIL(SNAPS_EINVAL, "need at least 2 objects");
+    if (n_masks < 1 || !masks || is_device_ptr(masks)) FAIL(SNAPS_EINVAL, "masks: a host array of >= 1 masks");
+    for (int m = 0; m < n_masks; ++m)
+        if (popc16(masks[m]) < 2 || (masks[m] >> pop->f) != 0)
+            FAIL(SNAPS_EINVAL, "mask %d (0x%x) must have 2..%d bits, all below feature %d", m, masks[m], pop->f,
+                 pop->f);
+    if (n_targets < 1 || n_targets > kSelectMaxTargets)
+        FAIL(SNAPS_EINVAL, "n_targets must be in 1..%d", kSelectMaxTargets);
+    if (!targets || is_device_ptr(targets)) FAIL(SNAPS_EINVAL, "targets: a host array");
+    for (int t = 0; t < n_targets; ++t)
+        if (!(targets[t] > 0.0 && targets[t] <= (double)(n - 1)))
+            FAIL(SNAPS_EINVAL, "target %d must be in (0, n - 1]", t);
+    if (n_sample < 1 || n_sample > SNAPS_SELECTIVITY_MAX_SAMPLE)
+        FAIL(SNAPS_EINVAL, "n_sample must be in 1..%d", SNAPS_SELECTIVITY_MAX_SAMPLE);
+    if (n_bins < 1 || n_bins > SNAPS_SELECTIVITY_MAX_BINS)
+        FAIL(SNAPS_EINVAL, "n_bins must be in 1..%d", SNAPS_SELECTIVITY_MAX_BINS);
+    if (!eps) FAIL(SNAPS_EINVAL, "eps is NULL");
+    SelectivityTargets tg{};
+    tg.n = n_targets;
+    tg.m = (int)std::min<int64_t>(n_sample, n);
+    if ((double)tg.m * (double)(n - 1) > 2199023255552.0)  // 2^41 distances keep the u64 sum exact
+        FAIL(SNAPS_EINVAL, "n_sample * (n - 1) must stay below 2^41");
+    for (int t = 0; t < n_targets; ++t) tg.target[t] = targets[t];
+    cudaStream_t st = (cudaStream_t)stream;
+
+    std::lock_guard<std::mutex> lock(ctx->sync_mu);
+    const size_t work = (selectivity_scratch_bytes(n) + 255) & ~(size_t)255;
+    const size_t outs = sizeof(float) * (size_t)n_masks * (n_targets + 1);
+    SNAPS_TRY(scratch_reserve(ctx, ctx->scratch, work + outs + 256));
+    char *base = (char *)ctx->scratch.ptr;
+    float *eps_dev = (float *)(base + work);
+    float *mean_dev = eps_dev + (size_t)n_masks * n_targets;
+    {
+        TraceScope ts(ctx, SNAPS_PHASE_SELECT, st, 4 * n_masks);
+        for (int m = 0; m < n_masks; ++m)
+            SNAPS_TRY(launch_selectivity(pop->x, n, masks[m], n_bins, tg, base, eps_dev + (size_t)m * n_targets,
+                                         mean_dev + m, st));
+    }
+    auto put = [&](void *dst, const void *src, size_t bytes) -> snaps_status {
+        if (!dst) return SNAPS_OK;
+        const cudaMemcpyKind kind = is_device_ptr(dst) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+        SNAPS_CHECK_CUDA(cudaMemcpyAsync(dst, src, bytes, kind, st));
+        return SNAPS_OK;
+    };
+    SNAPS_TRY(put(eps, eps_dev, sizeof(float) * (size_t)n_masks * n_targets));
+    SNAPS_TRY(put(eps_mean, mean_dev, sizeof(float) * (size_t)n_masks));
+    SNAPS_CHECK_CUDA(cudaStreamSynchronize(st));
+    return SNAPS_OK;
 }
 
 snaps_status snaps_scores(snaps_pop *pop, const uint16_t *masks, int n_masks, int k,
