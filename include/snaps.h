@@ -177,6 +177,7 @@ snaps_status snaps_scores(snaps_pop *pop, const uint16_t *masks, int n_masks, in
 /* ---- parameter selection: the over- / underfitting trade-off ---- */
 
 #define SNAPS_SELECT_MAX_GRID 64  /* values per parameter grid */
+#define SNAPS_SELECT_MAX_K 4096   /* largest k of a k grid */
 
 /* Select eps and k for every subspace in `masks` as Sec. 3.5.2 (eps, Eq. 2
  * and 3) and Sec. 3.6.2 (k) describe.  For each grid value the population is
@@ -193,8 +194,9 @@ snaps_status snaps_scores(snaps_pop *pop, const uint16_t *masks, int n_masks, in
  *   eps_min) / (n_eps - 1), computed in FP64 and rounded to FP32.  Metrics:
  *   0 = eps-neighbour count, 1 = mean eps-neighbour distance.
  * k grid (used when u_k or k_select is non-NULL): n_k (2..64) strictly
- *   ascending values in 1..min(32, n - 1), host array.  Metrics: 0 = kNN
- *   in-degree, 1 = mean kNN distance.
+ *   ascending values in 1..min(SNAPS_SELECT_MAX_K, n - 1), host array.
+ *   Metrics: 0 = kNN in-degree, 1 = mean kNN distance, the latter from an
+ *   exact sum of the k_j FP32 distances quantised to 2^-30.
  * top_n: the n of Eq. 2 (the paper uses 1 % of the population), 1..min(n, 1024).
  * Outputs (host or device, caller-owned, any may be NULL):
  *   u_eps:      n_masks x 2 metrics x 2 (0 = U^min, 1 = U^max) x n_eps floats;

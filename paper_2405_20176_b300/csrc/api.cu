@@ -1165,8 +1165,8 @@ snaps_status snaps_select(snaps_pop *pop, const uint16_t *masks, int n_masks, co
         for (int g = 0; g < n_k; ++g)
             if (k_grid[g] < 1 || (g > 0 && k_grid[g] <= k_grid[g - 1]))
                 FAIL(SNAPS_EINVAL, "k_grid must be strictly ascending from >= 1");
-        if (k_grid[n_k - 1] > SNAPS_MAX_K || k_grid[n_k - 1] > n - 1)
-            FAIL(SNAPS_EINVAL, "k_grid values must be <= min(%d, n - 1)", SNAPS_MAX_K);
+        if (k_grid[n_k - 1] > SNAPS_SELECT_MAX_K || k_grid[n_k - 1] > n - 1)
+            FAIL(SNAPS_EINVAL, "k_grid values must be <= min(%d, n - 1)", SNAPS_SELECT_MAX_K);
     }
     if (top_n < 1 || top_n > 1024 || top_n > n) FAIL(SNAPS_EINVAL, "top_n must be in 1..min(1024, n)");
     const int G = want_eps ? n_eps : 0, K = want_k ? n_k : 0;
@@ -1181,14 +1181,12 @@ snaps_status snaps_select(snaps_pop *pop, const uint16_t *masks, int n_masks, co
         cv.base = base;
         float *es = cv.take<float>((size_t)std::max(G, 1) * 4 * n);
         float *ks = cv.take<float>((size_t)std::max(K, 1) * 4 * n);
-        int32_t *ki = cv.take<int32_t>((size_t)n * std::max(kmax, 1));
-        float *kd = cv.take<float>((size_t)n * std::max(kmax, 1));
         int32_t *tp = cv.take<int32_t>((size_t)slots * 4 * top_n);
-        return std::make_tuple(es, ks, ki, kd, tp);
+        return std::make_tuple(es, ks, tp);
     };
     layout(nullptr);
     SNAPS_TRY(scratch_reserve(ctx, ctx->scratch, cv.off + 256));
-    auto [eps_scores, k_scores, knn_idx, knn_d2, tops_dev] = layout((char *)ctx->scratch.ptr);
+    auto [eps_scores, k_scores, tops_dev] = layout((char *)ctx->scratch.ptr);
     std::vector<int32_t> tops((size_t)slots * 4 * top_n);
     std::vector<float> ue((size_t)n_masks * 4 * std::max(G, 1)), uk((size_t)n_masks * 4 * std::max(K, 1));
     std::vector<int32_t> es((size_t)n_masks * 2), kse((size_t)n_masks * 2);
@@ -1204,18 +1202,20 @@ snaps_status snaps_select(snaps_pop *pop, const uint16_t *masks, int n_masks, co
             }
             sp.qscale = (float)(16777216.0 / (double)eps_max[m]);
         }
-        sp.kmax = kmax;
+        KGrid kg{};
+        kg.n = K;
+        for (int g = 0; g < K; ++g) kg.k[g] = k_grid[g];
+        const bool wide_k = K > 0 && kmax > kSelectWarpK;
         SNAPS_CHECK_CUDA(cudaMemsetAsync(eps_scores, 0, (size_t)std::max(G, 1) * 4 * n * sizeof(float), st));
         SNAPS_CHECK_CUDA(cudaMemsetAsync(k_scores, 0, (size_t)std::max(K, 1) * 4 * n * sizeof(float), st));
         {
-            TraceScope ts(ctx, SNAPS_PHASE_SELECT, st, 1 + (K > 0 ? 1 : 0));
-            SNAPS_TRY(launch_select_join(pop->x, n, sp, eps_scores, knn_idx, knn_d2, st));
-            if (K > 0) {
-                KGrid kg{};
-                kg.n = K;
-                for (int g = 0; g < K; ++g) kg.k[g] = k_grid[g];
-                SNAPS_TRY(launch_select_k(knn_idx, knn_d2, n, kmax, kg, k_scores, st));
+            TraceScope ts(ctx, SNAPS_PHASE_SELECT, st, (G > 0 || !wide_k ? 1 : 0) + (K > 0 ? 1 : 0) + wide_k);
+            if (G > 0 || !wide_k) {
+                KGrid none{};
+                SNAPS_TRY(launch_select_join(pop->x, n, sp, wide_k ? none : kg, eps_scores, k_scores, st));
             }
+            if (wide_k) SNAPS_TRY(launch_select_knn(pop->x, n, masks[m], kg, k_scores, st));
+            if (K > 0) SNAPS_TRY(launch_select_k_finish(n, kg, k_scores, st));
         }
         for (int half = 0; half < 2; ++half) {
             const int S = half == 0 ? G : K;

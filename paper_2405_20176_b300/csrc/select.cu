@@ -10,10 +10,14 @@
 // eps-neighbour at eps_max lands in the histogram bin of the smallest grid
 // radius that holds it (count and exact quantised distance, shared-memory
 // atomics), and the k_max list is kept warp-cooperatively.  The prefix sums of
-// the bins give the count and mean distance at every eps_j.
-// `select_k_kernel` turns the k_max lists into the in-degree and mean distance
-// at every k_j.  Rankings and top-n lists come from the library's top-n kernel
-// (Sec. 3.4), and the host computes Eq. 2 and Eq. 3 from those lists.
+// the bins give the count and mean distance at every eps_j.  For k_max <= 32
+// the same pass keeps the k_max nearest warp-cooperatively; for larger k_max
+// (the paper's k grids reach 4096) `select_knn_kernel` gives each object a CTA
+// that keeps its k_max nearest in shared memory.  Either way a neighbour at
+// rank t counts toward the in-degree at every k_j > t, and the mean distance
+// at k_j is an exact sum of the first k_j distances, each quantised to 2^-30.
+// Rankings and top-n lists come from the library's top-n kernel (Sec. 3.4),
+// and the host computes Eq. 2 and Eq. 3 from those lists.
 
 #include <math_constants.h>
 
@@ -50,9 +54,23 @@ __device__ __forceinline__ void load_row16(const float4 *__restrict__ x, int64_t
     }
 }
 
+// First grid index g with k_g > t: a neighbour at rank t is one of the k_g
+// nearest for g and every later grid value.
+__device__ __forceinline__ int first_grid_above(const KGrid &kg, int t)
+{
+    int g = 0;
+    while (g < kg.n - 1 && kg.k[g] <= t) ++g;
+    return g;
+}
+
+__device__ __forceinline__ unsigned long long knn_quant(float d2)
+{
+    return __float2ull_rn(sqrtf(d2) * (float)(1.0 / kKnnQuantum));
+}
+
 __global__ void __launch_bounds__(kSelWarps * 32)
-    select_join_kernel(const float4 *__restrict__ x, int n, SelectSpec sp, float *eps_scores,
-                       int32_t *knn_idx, float *knn_d2)
+    select_join_kernel(const float4 *__restrict__ x, int n, SelectSpec sp, KGrid kg, float *eps_scores,
+                       float *k_scores)
 {
     __shared__ unsigned s_cnt[kSelWarps][kSelectMaxGrid];
     __shared__ unsigned long long s_sum[kSelWarps][kSelectMaxGrid];
@@ -70,7 +88,7 @@ __global__ void __launch_bounds__(kSelWarps * 32)
     const int qorig = __float_as_int(q[15]);
     const int G = sp.n_eps;
     const float e2max = G > 0 ? sp.e2[G - 1] : -1.f;
-    const int k = sp.kmax;
+    const int k = kg.n > 0 && kg.k[kg.n - 1] <= kSelectWarpK ? kg.k[kg.n - 1] : 0;
     float T = k > 0 ? CUDART_INF_F : -CUDART_INF_F;
     float my_d = CUDART_INF_F;
     int my_j = 0x7fffffff;
@@ -110,50 +128,190 @@ __global__ void __launch_bounds__(kSelWarps * 32)
         row[qorig] = (float)c;
         row[n + qorig] = c > 0 ? (float)(((double)s / (double)sp.qscale) / (double)c) : 0.f;
     }
-    if (k > 0 && lane < (unsigned)k) {
-        knn_idx[(int64_t)qorig * k + lane] = my_j;
-        knn_d2[(int64_t)qorig * k + lane] = my_d;
-    }
-}
-
-// In-degree (row 2) and mean distance (row 3) at every k_j from the k_max lists.
-__global__ void select_k_kernel(const int32_t *__restrict__ knn_idx, const float *__restrict__ knn_d2, int n,
-                                int kmax, KGrid kg, float *k_scores)
-{
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const int32_t *li = knn_idx + (int64_t)i * kmax;
-        const float *ld = knn_d2 + (int64_t)i * kmax;
-        for (int g = 0; g < kg.n; ++g) {
-            const int kj = kg.k[g];
-            float *slot = k_scores + (int64_t)g * 4 * n;
-            float msum = 0.f;
-            for (int t = 0; t < kj; ++t) {
-                msum += sqrtf(ld[t]);
-                const int j = li[t];
-                if (j >= 0 && j < n) atomicAdd(&slot[2 * n + j], 1.f);
-            }
-            slot[3 * n + i] = msum / (float)kj;
+    if (k > 0) {
+        // lane t holds the neighbour of rank t; prefix sums of the quantised
+        // distances give the mean over the k_g nearest at lane k_g - 1
+        unsigned long long qs = (int)lane < k ? knn_quant(my_d) : 0ull;
+        for (int off = 1; off < 32; off <<= 1) {
+            const unsigned long long v = __shfl_up_sync(dev::kFull, qs, off);
+            if ((int)lane >= off) qs += v;
+        }
+        if ((int)lane < k) {
+            const int g0 = first_grid_above(kg, (int)lane);
+            if (my_j >= 0 && my_j < n) atomicAdd(&k_scores[(int64_t)g0 * 4 * n + 2 * n + my_j], 1.f);
+            for (int g = g0; g < kg.n && kg.k[g] <= (int)lane + 1; ++g)
+                if (kg.k[g] == (int)lane + 1)
+                    k_scores[(int64_t)g * 4 * n + 3 * n + qorig] = (float)((double)qs * kKnnQuantum / (lane + 1));
         }
     }
 }
 
+// ---- the k grid for k_max > 32: one CTA per object -----------------------------------------
+
+constexpr int kKnnThreads = 256;
+
+// Ascending bitonic sort of len (a power of two) keys by the whole CTA; ends synchronised.
+__device__ void bitonic_sort(unsigned long long *a, int len)
+{
+    for (int size = 2; size <= len; size <<= 1)
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (int t = threadIdx.x; t < (len >> 1); t += blockDim.x) {
+                const int lo = ((t & ~(stride - 1)) << 1) | (t & (stride - 1));
+                const int hi = lo + stride;
+                const bool up = (lo & size) == 0;
+                const unsigned long long a0 = a[lo], a1 = a[hi];
+                if ((a0 > a1) == up) {
+                    a[lo] = a1;
+                    a[hi] = a0;
+                }
+            }
+            __syncthreads();
+        }
+}
+
+// Keys (squared distance bits << 32 | original index) order neighbours by
+// (distance, index); every key is distinct.  buf holds cap keys (a power of
+// two >= 2 k_max and >= 2 kKnnThreads): candidates below the current k_max-th
+// key are appended, and when a round could overflow the buffer it is sorted
+// and cut back to its k_max smallest.
+__global__ void __launch_bounds__(kKnnThreads)
+    select_knn_kernel(const float4 *__restrict__ x, int n, uint32_t mask, KGrid kg, int cap, float *k_scores)
+{
+    extern __shared__ unsigned long long buf[];
+    __shared__ float sq[16];
+    __shared__ int s_fill;
+    __shared__ unsigned long long s_T;
+    __shared__ unsigned long long s_warp[kKnnThreads / 32];
+    const int p = blockIdx.x;
+    const int tid = threadIdx.x;
+    const int kmax = kg.k[kg.n - 1];
+    if (tid < 16) {
+        const float4 q4 = x[row_quad(p, tid >> 2)];
+        sq[tid] = (tid & 3) == 0 ? q4.x : (tid & 3) == 1 ? q4.y : (tid & 3) == 2 ? q4.z : q4.w;
+    }
+    if (tid == 0) {
+        s_fill = 0;
+        s_T = ~0ull;
+    }
+    __syncthreads();
+    const int qorig = __float_as_int(sq[15]);
+    for (int base = 0; base < n; base += kKnnThreads) {
+        const int fill0 = s_fill;  // after the last round's barrier: the same in every thread
+        __syncthreads();           // ... and read by all before anyone appends again
+        if (fill0 > cap - kKnnThreads) {
+            for (int t = fill0 + tid; t < cap; t += kKnnThreads) buf[t] = ~0ull;
+            __syncthreads();
+            bitonic_sort(buf, cap);
+            if (tid == 0) {
+                s_fill = kmax;
+                s_T = buf[kmax - 1];
+            }
+            __syncthreads();
+        }
+        const int j = base + tid;
+        if (j < n && j != p) {
+            float c[16];
+            load_row16(x, j, c);
+            float acc = 0.f;
+#pragma unroll
+            for (int f = 14; f >= 0; --f) {
+                const float d = c[f] - sq[f];
+                acc = fmaf(((mask >> f) & 1u) ? d : 0.f, d, acc);
+            }
+            const unsigned long long key =
+                ((unsigned long long)__float_as_uint(acc) << 32) | (unsigned)__float_as_int(c[15]);
+            if (key < s_T) buf[atomicAdd(&s_fill, 1)] = key;
+        }
+        __syncthreads();
+    }
+    const int fill = s_fill;  // >= kmax: every other object was a candidate
+    int len = 2 * kKnnThreads;
+    while (len < fill) len <<= 1;
+    for (int t = fill + tid; t < len; t += kKnnThreads) buf[t] = ~0ull;
+    __syncthreads();
+    bitonic_sort(buf, len);
+    // in-degree contributions and the exact distance sums at every k_g
+    const int per = (kmax + kKnnThreads - 1) / kKnnThreads;
+    const int t0 = tid * per, t1 = min(kmax, t0 + per);
+    unsigned long long local = 0ull;
+    for (int t = t0; t < t1; ++t) {
+        const unsigned long long key = buf[t];
+        const int j = (int)(unsigned)(key & 0xffffffffull);
+        local += knn_quant(__uint_as_float((unsigned)(key >> 32)));
+        if (j >= 0 && j < n) atomicAdd(&k_scores[(int64_t)first_grid_above(kg, t) * 4 * n + 2 * n + j], 1.f);
+    }
+    // exclusive prefix of the per-thread sums
+    unsigned long long inc = local;
+    const unsigned lane = dev::lane_id();
+    for (int off = 1; off < 32; off <<= 1) {
+        const unsigned long long v = __shfl_up_sync(dev::kFull, inc, off);
+        if ((int)lane >= off) inc += v;
+    }
+    if (lane == 31) s_warp[tid >> 5] = inc;
+    __syncthreads();
+    unsigned long long before = inc - local;
+    for (int w = 0; w < (tid >> 5); ++w) before += s_warp[w];
+    // the thread whose range ends a k_g writes its mean
+    for (int g = 0; g < kg.n; ++g) {
+        const int last = kg.k[g] - 1;
+        if (last < t0 || last >= t1) continue;
+        unsigned long long s = before;
+        for (int t = t0; t <= last; ++t) s += knn_quant(__uint_as_float((unsigned)(buf[t] >> 32)));
+        k_scores[(int64_t)g * 4 * n + 3 * n + qorig] = (float)((double)s * kKnnQuantum / kg.k[g]);
+    }
+}
+
+// In-degree at k_g: row 2 summed over slots 0..g.
+__global__ void select_k_finish_kernel(int n, int K, float *k_scores)
+{
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+        float acc = 0.f;
+        for (int g = 0; g < K; ++g) {
+            float *r = k_scores + (int64_t)g * 4 * n + 2 * n + j;
+            acc += *r;
+            *r = acc;
+        }
+    }
+}
+
+int knn_cap(int kmax)
+{
+    int cap = 2 * kKnnThreads;
+    while (cap < 2 * kmax) cap <<= 1;
+    return cap;
+}
+
 }  // namespace
 
-snaps_status launch_select_join(const float4 *x, int64_t n, const SelectSpec &sp, float *eps_scores,
-                                int32_t *knn_idx, float *knn_d2, cudaStream_t st)
+snaps_status launch_select_join(const float4 *x, int64_t n, const SelectSpec &sp, const KGrid &kg,
+                                float *eps_scores, float *k_scores, cudaStream_t st)
 {
     const unsigned blocks = (unsigned)((n + kSelWarps - 1) / kSelWarps);
-    select_join_kernel<<<blocks, kSelWarps * 32, 0, st>>>(x, (int)n, sp, eps_scores, knn_idx, knn_d2);
+    select_join_kernel<<<blocks, kSelWarps * 32, 0, st>>>(x, (int)n, sp, kg, eps_scores, k_scores);
     SNAPS_CHECK_CUDA(cudaGetLastError());
     return SNAPS_OK;
 }
 
-snaps_status launch_select_k(const int32_t *knn_idx, const float *knn_d2, int64_t n, int kmax, const KGrid &kg,
-                             float *k_scores, cudaStream_t st)
+snaps_status launch_select_knn(const float4 *x, int64_t n, uint32_t mask, const KGrid &kg, float *k_scores,
+                               cudaStream_t st)
 {
-    const int threads = 256;
-    const unsigned blocks = (unsigned)std::min<int64_t>((n + threads - 1) / threads, 148 * 8);
-    select_k_kernel<<<blocks, threads, 0, st>>>(knn_idx, knn_d2, (int)n, kmax, kg, k_scores);
+    const int kmax = kg.k[kg.n - 1];
+    if (kg.n < 1 || kmax > kSelectMaxK || kmax > n - 1) {
+        set_error("k_max must be in 1..min(%d, n - 1)", kSelectMaxK);
+        return SNAPS_EINVAL;
+    }
+    const int cap = knn_cap(kmax);
+    const size_t smem = sizeof(unsigned long long) * (size_t)cap;
+    SNAPS_CHECK_CUDA(cudaFuncSetAttribute(select_knn_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    select_knn_kernel<<<(unsigned)n, kKnnThreads, smem, st>>>(x, (int)n, mask, kg, cap, k_scores);
+    SNAPS_CHECK_CUDA(cudaGetLastError());
+    return SNAPS_OK;
+}
+
+snaps_status launch_select_k_finish(int64_t n, const KGrid &kg, float *k_scores, cudaStream_t st)
+{
+    const unsigned blocks = (unsigned)std::min<int64_t>((n + 255) / 256, 148 * 8);
+    select_k_finish_kernel<<<blocks, 256, 0, st>>>((int)n, kg.n, k_scores);
     SNAPS_CHECK_CUDA(cudaGetLastError());
     return SNAPS_OK;
 }

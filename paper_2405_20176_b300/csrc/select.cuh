@@ -13,31 +13,40 @@ namespace snaps {
 constexpr int kSelectMaxGrid = 64;  // grid values per parameter
 constexpr int kSelectHistBins = 4096;  // bins of the selectivity histogram
 
-// One subspace's eps grid and k_max, as the select join kernel takes them.
+constexpr int kSelectMaxK = 4096;       // largest k of a k grid
+constexpr int kSelectWarpK = 32;        // k_max up to this: warp-held lists
+constexpr double kKnnQuantum = 1.0 / 1073741824.0;  // 2^-30: quantum of the exact kNN distance sums
+
+// One subspace's eps grid, as the select join kernel takes it.
 struct SelectSpec {
     uint32_t mask;
     int n_eps;                    // 0: no eps grid
     float e2[kSelectMaxGrid];     // ascending squared radii eps_j^2
     float qscale;                 // 2^24 / eps_max: quantisation of the distance sums
-    int kmax;                     // 0: no kNN lists
 };
 
 struct KGrid {
-    int n;
-    int k[kSelectMaxGrid];        // ascending, <= kmax
+    int n;                        // 0: no k grid
+    int k[kSelectMaxGrid];        // strictly ascending; k[n - 1] = k_max
 };
 
-// eps_scores: n_eps slots x 4 rows x n (rows 0 and 1 written: eps-neighbour
-// count and mean distance at eps_j, by original index); knn_idx / knn_d2:
-// n x kmax, the k_max nearest (original indices, squared distances) of every
-// object, nearest first.
-snaps_status launch_select_join(const float4 *x, int64_t n, const SelectSpec &sp, float *eps_scores,
-                                int32_t *knn_idx, float *knn_d2, cudaStream_t st);
+// One pass over all candidates of every object for the eps grid and, when
+// k_max <= kSelectWarpK, the k grid.  eps_scores: n_eps slots x 4 rows x n
+// (rows 0 and 1: eps-neighbour count and mean distance at eps_j, by original
+// index).  k_scores: kg.n slots x 4 rows x n; row 2 of slot g receives, per
+// object, the number of lists that hold it at a rank in [k_{g-1}, k_g) (must
+// start at zero; launch_select_k_finish turns them into in-degrees); row 3 is
+// the mean distance to the k_g nearest.
+snaps_status launch_select_join(const float4 *x, int64_t n, const SelectSpec &sp, const KGrid &kg,
+                                float *eps_scores, float *k_scores, cudaStream_t st);
 
-// k_scores: kg.n slots x 4 rows x n; rows 2 (in-degree, added to: must start
-// at zero) and 3 (mean kNN distance) at every k_j.
-snaps_status launch_select_k(const int32_t *knn_idx, const float *knn_d2, int64_t n, int kmax, const KGrid &kg,
-                             float *k_scores, cudaStream_t st);
+// The k grid when k_max > kSelectWarpK: one CTA per object keeps its k_max
+// nearest in shared memory; writes rows 2 and 3 of k_scores as above.
+snaps_status launch_select_knn(const float4 *x, int64_t n, uint32_t mask, const KGrid &kg, float *k_scores,
+                               cudaStream_t st);
+
+// Row 2 of every k slot: prefix sums over the slots, giving the in-degree at k_g.
+snaps_status launch_select_k_finish(int64_t n, const KGrid &kg, float *k_scores, cudaStream_t st);
 
 // Radii for target selectivities of one subspace (Sec. 3.5.3): m sampled
 // objects (original indices floor(s n / m)) against all others; eps_mean is

@@ -1,8 +1,8 @@
 """Parameter selection through the C ABI (snaps_select; Sec. 3.5.2, Eq. 2 and
 3; Sec. 3.6.2) against the FP64 oracle, which runs one full join per grid
 value: the same U^min / U^max curves and the same selected grid index per
-metric, for subspaces of 2, 6 and 15 features; and the invalid requests it
-must reject."""
+metric, for subspaces of 2, 6 and 15 features and k grids up to 4096; and the
+invalid requests it must reject."""
 import numpy as np
 import pytest
 
@@ -46,6 +46,25 @@ def test_select_matches_oracle(ctx, n, seed):
         np.testing.assert_array_equal(k_sel[s], selk)
 
 
+@pytest.mark.parametrize("n,seed,k_grid", [(1500, 4, [2, 8, 64, 256, 1024, 1499]),
+                                           (4200, 6, [33, 1024, 4096])])
+def test_select_large_k_matches_oracle(ctx, n, seed, k_grid):
+    # k grids beyond 32 (the paper's reach 4096) take the CTA-per-object path
+    x = snaps_inputs.population(n, seed)
+    masks = np.array([0b110000, 0b111111100000000], dtype=np.uint16)[: 2 if n < 2000 else 1]
+    top_n = max(1, n // 100)
+    pop = snaps.snaps_index(ctx, x)
+    try:
+        _, _, u_k, k_sel = snaps.snaps_select(pop, masks, k_grid=k_grid, top_n=top_n)
+    finally:
+        snaps.snaps_release(pop)
+    xn = oracle.normalise(x)
+    for s, m in enumerate(masks):
+        uk, selk, _ = oracle.select_k(xn, int(m), k_grid, top_n)
+        np.testing.assert_allclose(u_k[s], uk, atol=1e-6, err_msg=f"k U, mask {int(m):#x}")
+        np.testing.assert_array_equal(k_sel[s], selk)
+
+
 def test_select_one_grid_only(ctx):
     x = snaps_inputs.population(600, 1)
     masks = np.array([0b110], dtype=np.uint16)
@@ -68,7 +87,8 @@ def test_select_rejects_bad_grids(ctx):
                    dict(eps_min=0.1, eps_max=0.2, n_eps=1),         # one value
                    dict(eps_min=0.1, eps_max=0.2, n_eps=65),        # too many
                    dict(k_grid=[4, 2]),                             # not ascending
-                   dict(k_grid=[2, 33]),                            # beyond SNAPS_MAX_K
+                   dict(k_grid=[2, 4097]),                          # beyond SNAPS_SELECT_MAX_K
+                   dict(k_grid=[2, 300]),                           # beyond n - 1
                    dict(k_grid=[2, 4], top_n=0)):
             kw.setdefault("top_n", 3)
             with pytest.raises(snaps.SnapsError) as e:
