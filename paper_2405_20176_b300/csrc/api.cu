@@ -271,7 +271,8 @@ constexpr size_t kOrderBytes = size_t(4) << 30;
 
 size_t order_chunk_bytes(const snaps_pop *p)
 {
-    return (size_t)p->n_pad * kRowFloats * sizeof(float) + (size_t)p->n * 2 * (sizeof(uint64_t) + sizeof(int32_t));
+    return (size_t)p->n_pad * kRowFloats * sizeof(float) + (size_t)p->n * 2 * (sizeof(uint64_t) + sizeof(int32_t)) +
+           (size_t)(p->n_pad / 64) * 10 * sizeof(float2);
 }
 
 int order_end_bit(int batch)
@@ -449,6 +450,7 @@ struct Layout {
     char *grid = nullptr;  // one subspace's grid index at a time
     // per-chunk row orders (one batch)
     float4 *ocopy = nullptr;
+    float2 *obox = nullptr;  // step boxes of the copies
     uint64_t *okeys = nullptr, *okeys2 = nullptr;
     int32_t *ovals = nullptr, *ovals2 = nullptr;
     void *otmp = nullptr;
@@ -477,6 +479,7 @@ Layout layout_job(const JobSpec &j, const Plan &pl, char *base, bool dev_scores,
         const size_t g = (size_t)pl.order_batch;
         const int64_t items = (int64_t)g * j.pop->n;
         L.ocopy = cv.take<float4>(g * (size_t)j.pop->n_pad * 4);
+        L.obox = cv.take<float2>(g * (size_t)(j.pop->n_pad / 64) * 10);
         L.okeys = cv.take<uint64_t>((size_t)items);
         L.okeys2 = cv.take<uint64_t>((size_t)items);
         L.ovals = cv.take<int32_t>((size_t)items);
@@ -638,16 +641,19 @@ snaps_status run_job(snaps_ctx *ctx, const JobSpec &j, cudaStream_t st, Scratch 
             SNAPS_TRY(sort_kernel_count<uint64_t>(ctx, items, end_bit, L.otmp, L.otmp_bytes, L.okeys, L.okeys2,
                                                   L.ovals, L.ovals2, &sort_kernels));
         {
-            TraceScope ts(ctx, SNAPS_PHASE_ORDER, st, 2 + sort_kernels);
+            TraceScope ts(ctx, SNAPS_PHASE_ORDER, st, 3 + sort_kernels);
             SNAPS_TRY(launch_chunk_keys(p->x, n, p->f, L.chunks + b0, g, p->kr, L.okeys, L.ovals, st));
             size_t tb = L.otmp_bytes;
             SNAPS_CHECK_CUDA(cub::DeviceRadixSort::SortPairs(L.otmp, tb, L.okeys, L.okeys2, L.ovals, L.ovals2,
                                                              (int)items, 0, end_bit, st));
             SNAPS_TRY(launch_gather_chunks(p->x, L.ovals2, n, p->n_pad, g, L.ocopy, st));
+            SNAPS_TRY(launch_chunk_boxes(L.ocopy, p->n_pad, g, L.obox, st));
         }
         JoinShape cs = shape;
         cs.x = L.ocopy;
         cs.chunk_stride = p->n_pad * 4;
+        cs.box = L.obox;
+        cs.box_stride = (p->n_pad / 64) * 10;
         TraceScope ts(ctx, SNAPS_PHASE_JOIN_TREE, st);
         SNAPS_TRY(launch_join_tree(cs, L.chunks + b0, g, out, ctrl, st));
     }

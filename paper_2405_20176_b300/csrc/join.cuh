@@ -56,6 +56,11 @@ struct JoinShape {
     // subspace-batched join only: float4 offset between the row copies of
     // consecutive chunks (each chunk's rows in its own order); 0 = one shared copy
     int64_t chunk_stride = 0;
+    // subspace-batched join only, optional: per chunk, the (min, max) of each
+    // high feature 5 + b over the 64 rows of every step of its row copy, at
+    // box[chunk * box_stride + b * (n_pad / 64) + step]
+    const float2 *box = nullptr;
+    int64_t box_stride = 0;
 };
 
 // Launch the lane-per-subspace join over `n_groups` groups (device array).

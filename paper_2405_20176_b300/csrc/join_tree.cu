@@ -13,17 +13,25 @@
 // claims from an atomic counter.  Each lane owns two candidates per step of
 // 64 rows, packed so that the f32x2 instructions (FADD2/FFMA2) process both;
 // the rows are read straight from global memory (the population stays in L2),
-// the next step's while the current one is walked.  The walk spends, per
+// the next live step's while the current one is walked.  The walk spends, per
 // subspace, one FFMA2 and two compares against the subspace's pass threshold,
 // max(current k-th distance, eps), which sits in shared memory (warp-uniform,
-// broadcast).  The step's 32 subspace votes end in one warp OR-reduction; on
-// the few steps where it is non-zero, an out-of-line handler recomputes the
-// triggered subspaces' distances and appends (squared distance, subspace,
-// candidate) tuples to the warp's buffer.  Once enough tuples wait (or the
-// buffer fills), a flush processes 32 tuples at a time with every lane busy:
-// eps counts and exact fixed-point distance sums by shared-memory atomics,
-// then kNN insertions, lanes holding different subspaces inserting into their
-// lists at the same time.
+// broadcast).  On steps where some lane's candidates pass somewhere, an
+// out-of-line handler recomputes the triggered subspaces' distances, each lane
+// its own subspaces, and appends (squared distance, subspace, candidate)
+// tuples to the warp's buffer.  Once enough tuples wait (or the buffer fills),
+// a flush processes 32 tuples at a time with every lane busy: eps counts and
+// exact fixed-point distance sums by shared-memory atomics, then kNN
+// insertions, lanes holding different subspaces inserting into their lists at
+// the same time.
+//
+// Skipping: every node of a chunk's tree is at least its root, the fold over
+// the high features, so a step none of whose roots is below the chunk's
+// largest pass threshold cannot produce an event.  Each step of a chunk's row
+// copy carries the box (min, max) of its rows' high features; the warp bounds
+// 32 steps at a time from the boxes, one lane per step, and only loads and
+// walks the steps whose bound stays under the threshold.  Loaded steps are
+// then tested on their exact roots before the walk.
 //
 // Row order: each chunk gets its own copy of the rows, sorted by a Morton key
 // over the chunk's high features (the features all 32 of its subspaces share)
@@ -265,30 +273,33 @@ __device__ __forceinline__ void fold_store(float2 (&v)[kW], const float2 (&d)[15
     }
 }
 
-// Append the kNN / eps tuples of the subspaces in `hit` (a warp-uniform
-// mask).  Each node's distances are recomputed from the root with the walk's
-// own FFMA2 chain (the low features of L folded from the highest down), so
-// they are bit-identical to the walk's.  A nearly full buffer is flushed.
-// Out of line: it runs on a minority of steps, and inlined its registers would
-// count against the walk's.  Returns the new tuple count.
+// Append the kNN / eps tuples of this lane's triggered subspaces (bit L of
+// `bits`: either candidate fell below subspace L's pass threshold in the
+// walk).  Every round each lane takes its lowest remaining subspace, so the
+// rounds number the most subspaces any one lane triggered.  The node's
+// distances are recomputed from the root with the walk's own FFMA2 chain (the
+// low features of L folded from the highest down), so they are bit-identical
+// to the walk's; a round appends at most 64 tuples, and a nearly full buffer
+// is flushed.  Out of line: it runs on a minority of steps, and inlined its
+// registers would count against the walk's.  Returns the new tuple count.
 template <int KMAX>
-__device__ __noinline__ int append_hits(int ws_off, unsigned hit, float2 root, float2 d0, float2 d1,
+__device__ __noinline__ int append_hits(int ws_off, unsigned bits, float2 root, float2 d0, float2 d1,
                                         float2 d2, float2 d3, float2 d4, int count, int ja, int jb, int k)
 {
     WarpState<KMAX> &ws = *reinterpret_cast<WarpState<KMAX> *>(tree_smem + ws_off);
-    const float2 d[5] = {d0, d1, d2, d3, d4};
     const unsigned lower = (1u << dev::lane_id()) - 1u;
-    while (hit) {
-        const int L = __ffs(hit) - 1;
-        hit &= hit - 1;
+    while (__any_sync(dev::kFull, bits != 0u)) {
+        const bool has = bits != 0u;
+        const int L = has ? __ffs(bits) - 1 : 0;
+        bits &= bits - 1u;
         float2 v = root;
-        if (L & 16) v = __ffma2_rn(d[4], d[4], v);
-        if (L & 8) v = __ffma2_rn(d[3], d[3], v);
-        if (L & 4) v = __ffma2_rn(d[2], d[2], v);
-        if (L & 2) v = __ffma2_rn(d[1], d[1], v);
-        if (L & 1) v = __ffma2_rn(d[0], d[0], v);
+        if (L & 16) v = __ffma2_rn(d4, d4, v);
+        if (L & 8) v = __ffma2_rn(d3, d3, v);
+        if (L & 4) v = __ffma2_rn(d2, d2, v);
+        if (L & 2) v = __ffma2_rn(d1, d1, v);
+        if (L & 1) v = __ffma2_rn(d0, d0, v);
         const float tc = ws.tc[L];
-        const bool pa = v.x < tc, pb = v.y < tc;
+        const bool pa = has && v.x < tc, pb = has && v.y < tc;
         const unsigned ba = __ballot_sync(dev::kFull, pa);
         const unsigned bb = __ballot_sync(dev::kFull, pb);
         if (pa) ws.tbuf[count + __popc(ba & lower)] = make_uint2(__float_as_uint(v.x), (L << 24) | (ja & 0xffffff));
@@ -448,13 +459,47 @@ __global__ void __launch_bounds__(CW * 32, kCtasPerSm<CW>)
         setup_phase<KMAX>(ws_off, x, i, n, high, active, s0, n_steps, k);
         __syncwarp();
 
-        // ---- main loop: the rest of the stream, 64 candidates a step, the next
-        // step's rows loaded while this one is walked --------------------------------
+        // ---- main loop: the rest of the stream, 64 candidates a step -----------------
+        // Steps go in windows of 32.  Lane l bounds the roots of window step l from
+        // below by the box of its rows' high features (folded in the root's order,
+        // so the bound is <= every row's FP32 root); a step whose bound reaches the
+        // chunk's largest pass threshold cannot pass anywhere and is neither loaded
+        // nor walked.  The next live step's rows load while one is walked.
         int tcount = 0;  // buffered event tuples (warp-uniform)
-        StepRows cur;
         const int init_steps = std::min(kInit / 64, n_steps);
-        if (init_steps < n_steps) load_step(x, (s0 + init_steps) % n_steps, lane, cur);
-        for (int u = init_steps; u < n_steps; ++u) {
+        const float2 *box = s.box ? s.box + (w / n) * s.box_stride : nullptr;
+        int wbase = init_steps, next_w = init_steps;
+        unsigned live = 0u;
+        auto take = [&]() -> int {
+            while (live == 0u) {
+                if (next_w >= n_steps) return -1;
+                const int u = next_w + (int)lane;
+                bool ok = u < n_steps;
+                if (ok && box) {
+                    const int step = (s0 + u) % n_steps;
+                    float lb = 0.f;
+#pragma unroll
+                    for (int b = 9; b >= 0; --b)
+                        if ((high >> b) & 1u) {
+                            const float2 mm = box[(int64_t)b * n_steps + step];
+                            const float q = -nxq[kLB + b].x;
+                            const float g = fmaxf(fmaxf(mm.x - q, q - mm.y), 0.f);
+                            lb = fmaf(g, g, lb);
+                        }
+                    ok = lb < ws.tcmax;
+                }
+                live = __ballot_sync(dev::kFull, ok);
+                wbase = next_w;
+                next_w += 32;
+            }
+            const int b = __ffs(live) - 1;
+            live &= live - 1u;
+            return wbase + b;
+        };
+        StepRows cur;
+        int u = take();
+        if (u >= 0) load_step(x, (s0 + u) % n_steps, lane, cur);
+        while (u >= 0) {
             const int step = (s0 + u) % n_steps;
             const int ja = step * 64 + (int)lane;
             const int jb = ja + 32;
@@ -477,27 +522,28 @@ __global__ void __launch_bounds__(CW * 32, kCtasPerSm<CW>)
 #pragma unroll
             for (int f = 14; f >= kLB; --f)
                 if ((high >> (f - kLB)) & 1u) v[0] = __ffma2_rn(d[f], d[f], v[0]);
-            // the next step's rows load while this one is walked
-            if (u + 1 < n_steps) load_step(x, (s0 + u + 1) % n_steps, lane, cur);
+            // the next live step's rows load while this one is walked
+            const int un = take();
+            if (un >= 0) load_step(x, (s0 + un) % n_steps, lane, cur);
             // Every node of the tree is >= its root, the fold over the high features.
             // When no root of the step's 64 candidates is below the chunk's largest pass
-            // threshold, no subspace can pass and the walk is skipped.  The rows come in
-            // cell order over the high features, so a step's candidates lie together and
-            // far-away steps skip as a whole.
+            // threshold, no subspace can pass and the walk is skipped.
             const float tmax = ws.tcmax;
-            if (__all_sync(dev::kFull, (v[0].x >= tmax) & (v[0].y >= tmax))) continue;
-            unsigned bits = 0u;
-            walk<0>(v, d, ws.tc, bits);
-            const unsigned hit = __reduce_or_sync(dev::kFull, bits);
-            if (hit) {
-                tcount = append_hits<KMAX>(ws_off, hit, v[0], d[0], d[1], d[2], d[3], d[4], tcount, oa, ob, k);
-                // flushing once a batch is waiting keeps the kNN thresholds fresh
-                // without paying a flush per step
-                if (tcount >= kFlushMin) {
-                    flush_tuples<KMAX>(ws_off, tcount, k);
-                    tcount = 0;
+            if (!__all_sync(dev::kFull, (v[0].x >= tmax) & (v[0].y >= tmax))) {
+                unsigned bits = 0u;
+                walk<0>(v, d, ws.tc, bits);
+                if (__any_sync(dev::kFull, bits != 0u)) {
+                    tcount = append_hits<KMAX>(ws_off, bits, v[0], d[0], d[1], d[2], d[3], d[4], tcount, oa, ob,
+                                               k);
+                    // flushing once a batch is waiting keeps the kNN thresholds fresh
+                    // without paying a flush per step
+                    if (tcount >= kFlushMin) {
+                        flush_tuples<KMAX>(ws_off, tcount, k);
+                        tcount = 0;
+                    }
                 }
             }
+            u = un;
         }
         if (tcount > 0) flush_tuples<KMAX>(ws_off, tcount, k);
 

@@ -234,6 +234,32 @@ __global__ void gather_chunks_kernel(const float4 *__restrict__ x, const int32_t
     }
 }
 
+// One warp per (copy, step): lane l holds rows 64s + l and 64s + 32 + l.
+__global__ void chunk_boxes_kernel(const float4 *__restrict__ copies, int64_t n_pad, int n_chunks,
+                                   float2 *__restrict__ boxes)
+{
+    const int64_t n_steps = n_pad / 64;
+    const int64_t total = n_steps * n_chunks;
+    const unsigned lane = threadIdx.x & 31u;
+    const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t e = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; e < total; e += warps) {
+        const int64_t g = e / n_steps, st = e - g * n_steps;
+        const float4 *src = copies + g * n_pad * 4;
+#pragma unroll
+        for (int b = 0; b < 10; ++b) {
+            const int f = 5 + b;
+            const float4 v = src[pair_plane(st * 64 + lane, f >> 1)];
+            float lo = (f & 1) ? fminf(v.z, v.w) : fminf(v.x, v.y);
+            float hi = (f & 1) ? fmaxf(v.z, v.w) : fmaxf(v.x, v.y);
+            for (int o = 16; o > 0; o >>= 1) {
+                lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+                hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+            }
+            if (lane == 0) boxes[(g * 10 + b) * n_steps + st] = make_float2(lo, hi);
+        }
+    }
+}
+
 // Sorted row p <- original row perm[p]; padding rows are +inf.
 __global__ void gather_rows_kernel(const float4 *__restrict__ src, const int32_t *__restrict__ perm,
                                    int64_t n, int64_t n_pad, float4 *__restrict__ dst)
@@ -475,6 +501,16 @@ snaps_status launch_chunk_keys(const float4 *x, int64_t n, int f, const TreeChun
     const int64_t total = n * (int64_t)n_chunks;
     const int64_t blocks = std::min<int64_t>((total + 255) / 256, 148 * 16);
     chunk_key_kernel<<<(unsigned)blocks, 256, 0, st>>>(x, n, f, chunks, n_chunks, kr, keys, vals);
+    SNAPS_CHECK_CUDA(cudaGetLastError());
+    return SNAPS_OK;
+}
+
+snaps_status launch_chunk_boxes(const float4 *copies, int64_t n_pad, int n_chunks, float2 *boxes,
+                                cudaStream_t st)
+{
+    const int64_t warps = (n_pad / 64) * n_chunks;
+    const unsigned blocks = (unsigned)std::min<int64_t>((warps * 32 + 255) / 256, 148 * 16);
+    chunk_boxes_kernel<<<blocks, 256, 0, st>>>(copies, n_pad, n_chunks, boxes);
     SNAPS_CHECK_CUDA(cudaGetLastError());
     return SNAPS_OK;
 }

@@ -47,6 +47,12 @@ snaps_status launch_chunk_keys(const float4 *x, int64_t n, int f, const TreeChun
 snaps_status launch_gather_chunks(const float4 *x, const int32_t *perm, int64_t n, int64_t n_pad,
                                   int n_chunks, float4 *out, cudaStream_t st);
 
+// Step boxes of chunk row copies: boxes[(g * 10 + b) * (n_pad / 64) + s] =
+// (min, max) of feature 5 + b over the 64 rows of step s of copy g (padding
+// rows count as +inf).
+snaps_status launch_chunk_boxes(const float4 *copies, int64_t n_pad, int n_chunks, float2 *boxes,
+                                cudaStream_t st);
+
 // Copy the first f features of the n population rows out as n x f row-major,
 // in the objects' original order.
 snaps_status launch_unpack(const float4 *x, int64_t n, int f, float *out, cudaStream_t st);
