@@ -646,13 +646,14 @@ snaps_status run_job(snaps_ctx *ctx, const JobSpec &j, cudaStream_t st, Scratch 
             size_t tb = L.otmp_bytes;
             SNAPS_CHECK_CUDA(cub::DeviceRadixSort::SortPairs(L.otmp, tb, L.okeys, L.okeys2, L.ovals, L.ovals2,
                                                              (int)items, 0, end_bit, st));
-            SNAPS_TRY(launch_gather_chunks(p->x, L.ovals2, n, p->n_pad, g, L.ocopy, st));
+            SNAPS_TRY(launch_gather_chunks(p->x, L.ovals2, L.chunks + b0, n, p->n_pad, g, L.ocopy, st));
             SNAPS_TRY(launch_chunk_boxes(L.ocopy, p->n_pad, g, L.obox, st));
         }
         JoinShape cs = shape;
         cs.x = L.ocopy;
         cs.chunk_stride = p->n_pad * 4;
         cs.box = L.obox;
+        cs.compact = true;
         cs.box_stride = (p->n_pad / 64) * 10;
         TraceScope ts(ctx, SNAPS_PHASE_JOIN_TREE, st);
         SNAPS_TRY(launch_join_tree(cs, L.chunks + b0, g, out, ctrl, st));

@@ -61,6 +61,10 @@ struct JoinShape {
     // box[chunk * box_stride + b * (n_pad / 64) + step]
     const float2 *box = nullptr;
     int64_t box_stride = 0;
+    // subspace-batched join only: every chunk's copy holds its high features
+    // compacted, the highest first, in floats 5.. (0 after them); the boxes
+    // then follow the same order
+    bool compact = false;
 };
 
 // Launch the lane-per-subspace join over `n_groups` groups (device array).

@@ -105,6 +105,17 @@ constexpr DfsTable make_dfs() {
     return t;
 }
 constexpr DfsTable kDfs = make_dfs();
+
+// DFS position of every node L (the inverse of kDfs.node).
+struct DfsPos {
+    int pos[kW];
+};
+constexpr DfsPos make_dfs_pos() {
+    DfsPos t{};
+    for (int p = 0; p < kW; ++p) t.pos[kDfs.node[p]] = p;
+    return t;
+}
+__constant__ DfsPos kDfsPos = make_dfs_pos();
 static_assert(kTBuf * 2 >= kW * 64, "the set-up transpose fits the tuple buffer");
 static_assert(kTBuf * ((1u << 20) + 1u) < (1ull << 32), "a flush's eps partial sums fit 32 bits");
 static_assert(kDfs.node[1] == 16 && kDfs.parent[kW / 2] > 0, "DFS order as expected");
@@ -120,6 +131,7 @@ struct WarpState {
     unsigned epart[kW];             // this flush's partial sums (<= kTBuf terms of <= 2^20 + 1)
     float T[kW];                    // current k-th squared distance
     float tc[kW];                   // pass threshold max(T, eps) by L
+    alignas(16) float tcd[kW];      // the same in DFS order, read four at a time by the walk
     float tcmax;                    // the largest of them: a bound for the whole tree
     int cnt[kW];                    // eps-neighbour counts
     float eps2[kW];                 // radii of this chunk
@@ -228,17 +240,22 @@ __device__ __noinline__ bool flush_tuples(int ws_off, int count, int k)
     __syncwarp();
     ws.esum[lane] += ws.epart[lane];
     ws.epart[lane] = 0u;
-    if ((changed >> lane) & 1u) ws.tc[lane] = fmaxf(next_up(ws.T[lane]), eps_up(ws.eps2[lane]));
+    if ((changed >> lane) & 1u) {
+        const float t = fmaxf(next_up(ws.T[lane]), eps_up(ws.eps2[lane]));
+        ws.tc[lane] = t;
+        ws.tcd[kDfsPos.pos[lane]] = t;
+    }
     update_tcmax(ws);
     return changed != 0u;
 }
 
 // The walk: the 32 subspace distances of this lane's two candidates in DFS
 // order (one FFMA2 per node), and the set of subspaces L in which either
-// candidate fell below its pass threshold (bit L of `bits`).  No branches.
+// candidate fell below its pass threshold (bit L of the OR of `bits`).  No
+// branches; four partial masks keep the ORs from forming one serial chain.
 template <int P>
-__device__ __forceinline__ void walk(float2 (&v)[kW], const float2 (&d)[15], const float *tc,
-                                     unsigned &bits)
+__device__ __forceinline__ void walk(float2 (&v)[kW], const float2 (&d)[15], const float4 *tcd, float4 tq,
+                                     unsigned (&bits)[4])
 {
     if constexpr (P < kW) {
         if constexpr (P > 0) {
@@ -246,10 +263,11 @@ __device__ __forceinline__ void walk(float2 (&v)[kW], const float2 (&d)[15], con
             constexpr int par = kDfs.parent[P];
             v[P] = __ffma2_rn(d[b], d[b], v[par]);
         }
+        if constexpr ((P & 3) == 0) tq = tcd[P >> 2];  // thresholds of nodes P .. P + 3
         constexpr int L = kDfs.node[P];
-        const float t = tc[L];
-        bits |= ((v[P].x < t) | (v[P].y < t)) ? (1u << L) : 0u;
-        walk<P + 1>(v, d, tc, bits);
+        const float t = (P & 3) == 0 ? tq.x : (P & 3) == 1 ? tq.y : (P & 3) == 2 ? tq.z : tq.w;
+        bits[P & 3] |= ((v[P].x < t) | (v[P].y < t)) ? (1u << L) : 0u;
+        walk<P + 1>(v, d, tcd, tq, bits);
     }
 }
 
@@ -335,9 +353,28 @@ __device__ __forceinline__ float2 feat_pair(const StepRows &r, int f)
     return (f & 1) ? make_float2(v.z, v.w) : make_float2(v.x, v.y);
 }
 
+// The root of a step's two candidates: the fold over the chunk's high
+// features, the highest first.  In a compacted copy those sit in floats 5..
+// in that order, followed by zeros whose FMAs leave the fold unchanged, so the
+// fold needs no branches.
+template <bool CMP>
+__device__ __forceinline__ float2 root_fold(const float2 (&d)[15], uint32_t high)
+{
+    float2 v = f2(0.f, 0.f);
+    if constexpr (CMP) {
+#pragma unroll
+        for (int f = kLB; f < 15; ++f) v = __ffma2_rn(d[f], d[f], v);
+    } else {
+#pragma unroll
+        for (int f = 14; f >= kLB; --f)
+            if ((high >> (f - kLB)) & 1u) v = __ffma2_rn(d[f], d[f], v);
+    }
+    return v;
+}
+
 // Set-up phase (see the kernel), kept out of line so that its registers do
 // not add to the main loop's.
-template <int KMAX>
+template <int KMAX, bool CMP>
 __device__ __noinline__ void setup_phase(int ws_off, const float4 *__restrict__ x, int64_t i, int64_t n,
                                          uint32_t high, uint32_t active, int64_t s0, int64_t n_steps, int k)
 {
@@ -364,10 +401,7 @@ __device__ __noinline__ void setup_phase(int ws_off, const float4 *__restrict__ 
         // the next step's rows load while this one is folded and scanned
         if (u + 1 < init_steps) load_step(x, (s0 + u + 1) % n_steps, lane, r);
         float2 v[kW];
-        v[0] = f2(0.f, 0.f);
-#pragma unroll
-        for (int f = 14; f >= kLB; --f)
-            if ((high >> (f - kLB)) & 1u) v[0] = __ffma2_rn(d[f], d[f], v[0]);
+        v[0] = root_fold<CMP>(d, high);
         __syncwarp();
         fold_store<0>(v, d, stg, lane);
         __syncwarp();
@@ -390,10 +424,11 @@ __device__ __noinline__ void setup_phase(int ws_off, const float4 *__restrict__ 
     ws.cnt[L] = cnt;
     ws.esum[L] = qs;
     ws.tc[L] = mine ? fmaxf(next_up(T), eps_up(e2)) : -CUDART_INF_F;
+    ws.tcd[kDfsPos.pos[L]] = ws.tc[L];
     update_tcmax(ws);
 }
 
-template <int KMAX, int CW>
+template <int KMAX, int CW, bool CMP>
 __global__ void __launch_bounds__(CW * 32, kCtasPerSm<CW>)
     join_tree_kernel(JoinShape s, const TreeChunk *__restrict__ chunks, int n_chunks, JoinOut o,
                      DeviceControl *ctrl)
@@ -456,7 +491,7 @@ __global__ void __launch_bounds__(CW * 32, kCtasPerSm<CW>)
         constexpr int kSteps = kTile / 64;  // steps per tile
         const int n_steps = n_tiles * kSteps;
         const int s0 = t0 * kSteps;
-        setup_phase<KMAX>(ws_off, x, i, n, high, active, s0, n_steps, k);
+        setup_phase<KMAX, CMP>(ws_off, x, i, n, high, active, s0, n_steps, k);
         __syncwarp();
 
         // ---- main loop: the rest of the stream, 64 candidates a step -----------------
@@ -468,6 +503,7 @@ __global__ void __launch_bounds__(CW * 32, kCtasPerSm<CW>)
         int tcount = 0;  // buffered event tuples (warp-uniform)
         const int init_steps = std::min(kInit / 64, n_steps);
         const float2 *box = s.box ? s.box + (w / n) * s.box_stride : nullptr;
+        const int n_high = __popc(high);
         int wbase = init_steps, next_w = init_steps;
         unsigned live = 0u;
         auto take = [&]() -> int {
@@ -478,14 +514,23 @@ __global__ void __launch_bounds__(CW * 32, kCtasPerSm<CW>)
                 if (ok && box) {
                     const int step = (s0 + u) % n_steps;
                     float lb = 0.f;
-#pragma unroll
-                    for (int b = 9; b >= 0; --b)
-                        if ((high >> b) & 1u) {
+                    if constexpr (CMP) {
+                        for (int b = 0; b < n_high; ++b) {
                             const float2 mm = box[(int64_t)b * n_steps + step];
                             const float q = -nxq[kLB + b].x;
                             const float g = fmaxf(fmaxf(mm.x - q, q - mm.y), 0.f);
                             lb = fmaf(g, g, lb);
                         }
+                    } else {
+#pragma unroll
+                        for (int b = 9; b >= 0; --b)
+                            if ((high >> b) & 1u) {
+                                const float2 mm = box[(int64_t)b * n_steps + step];
+                                const float q = -nxq[kLB + b].x;
+                                const float g = fmaxf(fmaxf(mm.x - q, q - mm.y), 0.f);
+                                lb = fmaf(g, g, lb);
+                            }
+                    }
                     ok = lb < ws.tcmax;
                 }
                 live = __ballot_sync(dev::kFull, ok);
@@ -518,10 +563,7 @@ __global__ void __launch_bounds__(CW * 32, kCtasPerSm<CW>)
                 }
             }
             float2 v[kW];
-            v[0] = f2(0.f, 0.f);
-#pragma unroll
-            for (int f = 14; f >= kLB; --f)
-                if ((high >> (f - kLB)) & 1u) v[0] = __ffma2_rn(d[f], d[f], v[0]);
+            v[0] = root_fold<CMP>(d, high);
             // the next live step's rows load while this one is walked
             const int un = take();
             if (un >= 0) load_step(x, (s0 + un) % n_steps, lane, cur);
@@ -530,8 +572,9 @@ __global__ void __launch_bounds__(CW * 32, kCtasPerSm<CW>)
             // threshold, no subspace can pass and the walk is skipped.
             const float tmax = ws.tcmax;
             if (!__all_sync(dev::kFull, (v[0].x >= tmax) & (v[0].y >= tmax))) {
-                unsigned bits = 0u;
-                walk<0>(v, d, ws.tc, bits);
+                unsigned part[4] = {0u, 0u, 0u, 0u};
+                walk<0>(v, d, reinterpret_cast<const float4 *>(ws.tcd), make_float4(0.f, 0.f, 0.f, 0.f), part);
+                const unsigned bits = (part[0] | part[1]) | (part[2] | part[3]);
                 if (__any_sync(dev::kFull, bits != 0u)) {
                     tcount = append_hits<KMAX>(ws_off, bits, v[0], d[0], d[1], d[2], d[3], d[4], tcount, oa, ob,
                                                k);
@@ -575,12 +618,12 @@ __global__ void __launch_bounds__(CW * 32, kCtasPerSm<CW>)
     }
 }
 
-template <int KMAX, int CW>
+template <int KMAX, int CW, bool CMP>
 snaps_status launch_tree(const JoinShape &s, const TreeChunk *chunks, int n_chunks,
                          const JoinOut &o, DeviceControl *ctrl, cudaStream_t st)
 {
     const size_t smem = sizeof(TreeSmem<KMAX, CW>);
-    auto kern = join_tree_kernel<KMAX, CW>;
+    auto kern = join_tree_kernel<KMAX, CW, CMP>;
     SNAPS_CHECK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int dev = 0, sms = 0, per_sm = 0;
     SNAPS_CHECK_CUDA(cudaGetDevice(&dev));
@@ -604,8 +647,11 @@ snaps_status launch_join_tree(const JoinShape &s, const TreeChunk *chunks, int n
                               const JoinOut &o, DeviceControl *ctrl, cudaStream_t st)
 {
     if (n_chunks <= 0) return SNAPS_OK;
-    if (s.k <= 16) return launch_tree<16, 8>(s, chunks, n_chunks, o, ctrl, st);
-    return launch_tree<32, 6>(s, chunks, n_chunks, o, ctrl, st);
+    if (s.k <= 16)
+        return s.compact ? launch_tree<16, 8, true>(s, chunks, n_chunks, o, ctrl, st)
+                         : launch_tree<16, 8, false>(s, chunks, n_chunks, o, ctrl, st);
+    return s.compact ? launch_tree<32, 6, true>(s, chunks, n_chunks, o, ctrl, st)
+                     : launch_tree<32, 6, false>(s, chunks, n_chunks, o, ctrl, st);
 }
 
 }  // namespace snaps

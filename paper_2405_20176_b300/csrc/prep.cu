@@ -205,7 +205,8 @@ __global__ void chunk_key_kernel(const float4 *__restrict__ x, int64_t n, int f,
 // out[g] <- the rows x[perm[g * n + p]], p = 0..n_pad-1, in the pair-planar
 // layout (one thread per row pair a = 64s + l, b = a + 32); padding rows +inf.
 __global__ void gather_chunks_kernel(const float4 *__restrict__ x, const int32_t *__restrict__ perm,
-                                     int64_t n, int64_t n_pad, int n_chunks, float4 *__restrict__ out)
+                                     const TreeChunk *__restrict__ chunks, int64_t n, int64_t n_pad, int n_chunks,
+                                     float4 *__restrict__ out)
 {
     const int64_t pairs = n_pad / 2;  // per chunk
     const int64_t total = pairs * (int64_t)n_chunks;
@@ -223,10 +224,33 @@ __global__ void gather_chunks_kernel(const float4 *__restrict__ x, const int32_t
             ra[q] = oa >= 0 ? x[row_quad(oa, q)] : make_float4(inf, inf, inf, inf);
             rb[q] = ob >= 0 ? x[row_quad(ob, q)] : make_float4(inf, inf, inf, inf);
         }
-        const float va[16] = {ra[0].x, ra[0].y, ra[0].z, ra[0].w, ra[1].x, ra[1].y, ra[1].z, ra[1].w,
-                              ra[2].x, ra[2].y, ra[2].z, ra[2].w, ra[3].x, ra[3].y, ra[3].z, ra[3].w};
-        const float vb[16] = {rb[0].x, rb[0].y, rb[0].z, rb[0].w, rb[1].x, rb[1].y, rb[1].z, rb[1].w,
-                              rb[2].x, rb[2].y, rb[2].z, rb[2].w, rb[3].x, rb[3].y, rb[3].z, rb[3].w};
+        float va[16] = {ra[0].x, ra[0].y, ra[0].z, ra[0].w, ra[1].x, ra[1].y, ra[1].z, ra[1].w,
+                        ra[2].x, ra[2].y, ra[2].z, ra[2].w, ra[3].x, ra[3].y, ra[3].z, ra[3].w};
+        float vb[16] = {rb[0].x, rb[0].y, rb[0].z, rb[0].w, rb[1].x, rb[1].y, rb[1].z, rb[1].w,
+                        rb[2].x, rb[2].y, rb[2].z, rb[2].w, rb[3].x, rb[3].y, rb[3].z, rb[3].w};
+        if (chunks) {
+            // compact the chunk's high features into floats 5.. in descending
+            // feature order; the floats after them are 0 (padding rows: +inf)
+            const uint32_t high = chunks[g].high;
+            float ca[10], cb[10];
+            int r = 0;
+#pragma unroll
+            for (int f = 14; f >= 5; --f)
+                if ((high >> (f - 5)) & 1u) {
+                    ca[r] = va[f];
+                    cb[r] = vb[f];
+                    ++r;
+                }
+            for (; r < 10; ++r) {
+                ca[r] = oa >= 0 ? 0.f : inf;
+                cb[r] = ob >= 0 ? 0.f : inf;
+            }
+#pragma unroll
+            for (int c = 0; c < 10; ++c) {
+                va[5 + c] = ca[c];
+                vb[5 + c] = cb[c];
+            }
+        }
         float4 *dst = out + g * n_pad * 4;
 #pragma unroll
         for (int q = 0; q < 8; ++q)
@@ -515,12 +539,12 @@ snaps_status launch_chunk_boxes(const float4 *copies, int64_t n_pad, int n_chunk
     return SNAPS_OK;
 }
 
-snaps_status launch_gather_chunks(const float4 *x, const int32_t *perm, int64_t n, int64_t n_pad,
-                                  int n_chunks, float4 *out, cudaStream_t st)
+snaps_status launch_gather_chunks(const float4 *x, const int32_t *perm, const TreeChunk *chunks, int64_t n,
+                                  int64_t n_pad, int n_chunks, float4 *out, cudaStream_t st)
 {
     const int64_t total = n_pad / 2 * (int64_t)n_chunks;
     const int64_t blocks = std::min<int64_t>((total + 255) / 256, 148 * 16);
-    gather_chunks_kernel<<<(unsigned)blocks, 256, 0, st>>>(x, perm, n, n_pad, n_chunks, out);
+    gather_chunks_kernel<<<(unsigned)blocks, 256, 0, st>>>(x, perm, chunks, n, n_pad, n_chunks, out);
     SNAPS_CHECK_CUDA(cudaGetLastError());
     return SNAPS_OK;
 }

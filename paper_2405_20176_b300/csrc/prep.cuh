@@ -44,11 +44,13 @@ snaps_status launch_chunk_keys(const float4 *x, int64_t n, int f, const TreeChun
 
 // out[g] (n_pad rows each, pair-planar layout) <- the rows of x in chunk g's
 // sorted order perm[g * n ..] (perm NULL: x's own order); padding rows are +inf.
-snaps_status launch_gather_chunks(const float4 *x, const int32_t *perm, int64_t n, int64_t n_pad,
-                                  int n_chunks, float4 *out, cudaStream_t st);
+// chunks non-NULL: each copy holds its chunk's high features compacted, the
+// highest first, in floats 5.., and 0 after them (+inf in padding rows).
+snaps_status launch_gather_chunks(const float4 *x, const int32_t *perm, const TreeChunk *chunks, int64_t n,
+                                  int64_t n_pad, int n_chunks, float4 *out, cudaStream_t st);
 
 // Step boxes of chunk row copies: boxes[(g * 10 + b) * (n_pad / 64) + s] =
-// (min, max) of feature 5 + b over the 64 rows of step s of copy g (padding
+// (min, max) of float 5 + b over the 64 rows of step s of copy g (padding
 // rows count as +inf).
 snaps_status launch_chunk_boxes(const float4 *copies, int64_t n_pad, int n_chunks, float2 *boxes,
                                 cudaStream_t st);

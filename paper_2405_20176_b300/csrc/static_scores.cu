@@ -208,7 +208,7 @@ extern "C" snaps_status snaps_scores_static(int device, const float *feat, int64
     JoinOut out{scores, nullptr, nullptr, nullptr};
     if (n_chunks > 0) {
         // the tree join reads the rows in the pair-planar layout (one copy, input order)
-        SNAPS_TRY(launch_gather_chunks(pop, nullptr, n, n_pad, 1, pair, st));
+        SNAPS_TRY(launch_gather_chunks(pop, nullptr, nullptr, n, n_pad, 1, pair, st));
         JoinShape ts = shape;
         ts.x = pair;
         SNAPS_TRY(launch_join_tree(ts, d_chunks, n_chunks, out, ctrl, st));
