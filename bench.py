@@ -41,6 +41,14 @@ K_DEFAULT = 10
 L2_FLUSH_BYTES = 512 << 20   # > 126 MB L2
 SAMPLE_SEED = 1              # the 64-subspace oracle sample of the batching workload
 COMPARES_PER_SM_CLK = 64     # FP32 compare throughput per SM per clock
+# DRAM bytes (read + write) per pair-subspace evaluation, from one ncu capture
+# of each kernel (dram__bytes_read.sum + dram__bytes_write.sum): the tree join
+# on one 32-subspace chunk at N = 31,693 (7.83 MB + 3.97 MB), the tensor-core
+# join on one block of 256 subspaces at N = 31,693 (0.35 MB + 0.98 MB).  Both
+# kernels read their candidates from L2, so DRAM traffic grows with the
+# evaluations only through the outputs and the row copies.
+TREE_DRAM_BYTES_PER_EVAL = (7.829248e6 + 3.973376e6) / (31693 * 31692 * 32)
+TC_DRAM_BYTES_PER_EVAL = (0.35e6 + 0.98e6) / (31693 * 31692 * 256)
 
 
 def _load_peaks():
@@ -249,8 +257,11 @@ def run_ours(args, rank, world, dist):
         peak = props.multi_processor_count * COMPARES_PER_SM_CLK * max_mhz * 1e6 / 1e12
         achieved = evals_per_step * steps / (dom_ms / 1e3) / 1e12 if dom_ms > 0 else None
         measured_alu = snaps.snaps_calibrate_alu(local) / 1e12
+        traffic = TREE_DRAM_BYTES_PER_EVAL * evals_per_step if dominant == "join_tree" else None
         return {"bound": "alu", "kernel": dominant, "achieved": achieved, "peak": peak,
-                "unit": "Tevals/s", "frac": (achieved / peak) if achieved else None, "traffic": None,
+                "unit": "Tevals/s", "frac": (achieved / peak) if achieved else None, "traffic": traffic,
+                "traffic_basis": "DRAM bytes per launch: an ncu capture of one 32-subspace chunk (11.8 MB for "
+                                 "3.2e10 evaluations) scaled by the launch's evaluations",
                 "peak_basis": f"{props.multi_processor_count} SMs x {COMPARES_PER_SM_CLK} FP32 "
                               f"compares/clk x {max_mhz:.0f} MHz (one compare per pair-subspace "
                               f"evaluation)",
@@ -267,7 +278,10 @@ def run_ours(args, rank, world, dist):
         achieved = flops / (tc_ms / 1e3) / 1e12 if tc_ms > 0 else None
         peak = PEAKS.get("bf16_tflops_sustained") or PEAKS.get("bf16_tflops") or 1400.0
         return {"bound": "tensor", "kernel": "join_tc", "achieved": achieved, "peak": peak,
-                "unit": "TFLOP/s", "frac": (achieved / peak) if achieved else None, "traffic": None,
+                "unit": "TFLOP/s", "frac": (achieved / peak) if achieved else None,
+                "traffic": TC_DRAM_BYTES_PER_EVAL * evals_per_step,
+                "traffic_basis": "DRAM bytes per launch: an ncu capture of one 256-subspace block (1.33 MB "
+                                 "for 2.6e11 evaluations) scaled by the launch's evaluations",
                 "peak_basis": "measured dense BF16 GEMM, sustained (MEASURED_PEAKS.json); FP16 "
                               "has the same dense rate",
                 "evals_per_s": evals_per_step * steps / (tc_ms / 1e3) if tc_ms > 0 else None,
