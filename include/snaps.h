@@ -239,6 +239,43 @@ snaps_status snaps_eps_selectivity(snaps_pop *pop, const uint16_t *masks, int n_
                                    const double *targets, int n_targets, int n_sample, int n_bins,
                                    float *eps, float *eps_mean, void *stream);
 
+/* ---- autotuning of the index route ---- */
+
+#define SNAPS_TUNE_CELLS 3       /* grid cell widths tried: 1, 2 and 4 x eps */
+#define SNAPS_TUNE_MAX_N 65536   /* larger populations are timed on a sample */
+
+/* One subspace dimension's measurements and choice. */
+typedef struct snaps_tune_entry {
+    int d;                            /* subspace dimension, 2..4 */
+    int grid;                         /* 1: the grid index, 0: brute force */
+    float cell_mult;                  /* the grid's cell width in units of eps */
+    double ms_brute;                  /* ms per subspace, brute force */
+    double ms_grid[SNAPS_TUNE_CELLS]; /* ms per subspace, grid at 1, 2, 4 x eps */
+} snaps_tune_entry;
+
+/* Choose how subspaces of 2, 3 and 4 features are joined on populations of
+ * this one's size class.  For each dimension d it times two subspaces of d
+ * features (the lowest and the highest features) with this k and the default
+ * radius: by brute force, and on the grid index (sort-by-cell, Sec. 3.8.1)
+ * with cells 1, 2 and 4 times eps wide (any width >= eps finds every
+ * neighbour).  Populations of more than SNAPS_TUNE_MAX_N objects are timed on
+ * an evenly strided sample of that many.  The fastest choice is recorded in
+ * the context under (floor(log2 n), d, k <= 16 or not).  Calls without an
+ * index flag then follow it for the subspaces that are joined on their own:
+ * those alone among the requested ones in their 32-subspace chunk, and all of
+ * them in the SNAPS_TC_F16 form.  Subspaces that share a chunk keep the
+ * built-in rule (the grid from SNAPS_GRID_AUTO_N objects on), because there
+ * the subspace-batched join shares its arithmetic and a subspace costs far
+ * less than on its own.  SNAPS_INDEX_GRID uses the recorded cell width.  Every
+ * route returns the same results; only the time changes.
+ * k: 1..min(SNAPS_MAX_K, n - 1).  out: 3 entries (d = 2, 3, 4; host), or NULL.
+ * The call synchronises `stream`.
+ * Errors: EINVAL, ENOMEM, ECUDA. */
+snaps_status snaps_autotune(snaps_pop *pop, int k, snaps_tune_entry *out, void *stream);
+
+/* Forget every recorded choice (the built-in rule applies again). */
+snaps_status snaps_autotune_clear(snaps_ctx *ctx);
+
 /* ---- serving: continuous batching of scoring requests ---- */
 
 /* One scoring request: snaps_scores on a resident population.  masks and

@@ -41,6 +41,8 @@ SNAPS_PHASE_INDEX, SNAPS_PHASE_JOIN_TREE, SNAPS_PHASE_JOIN_LANE, SNAPS_PHASE_NOR
     SNAPS_PHASE_JOIN_TC, SNAPS_PHASE_ORDER, SNAPS_PHASE_GRID, SNAPS_PHASE_SELECT = range(9)
 SNAPS_N_PHASES = 9
 SNAPS_SELECT_MAX_GRID = 64
+SNAPS_TUNE_CELLS = 3
+SNAPS_TUNE_MAX_N = 65536
 SNAPS_SELECTIVITY_MAX_SAMPLE = 65536
 SNAPS_SELECTIVITY_MAX_BINS = 4096
 PHASE_NAMES = ["index", "join_tree", "join_lane", "norm", "top", "join_tc", "order", "grid", "select"]
@@ -58,6 +60,11 @@ class snaps_request(ctypes.Structure):
                 ("k", ctypes.c_int), ("eps", ctypes.c_void_p), ("precision", ctypes.c_uint32),
                 ("scores", ctypes.c_void_p), ("norm", ctypes.c_void_p), ("top", ctypes.c_void_p),
                 ("top_n", ctypes.c_int)]
+
+
+class snaps_tune_entry(ctypes.Structure):
+    _fields_ = [("d", ctypes.c_int), ("grid", ctypes.c_int), ("cell_mult", ctypes.c_float),
+                ("ms_brute", ctypes.c_double), ("ms_grid", ctypes.c_double * 3)]
 
 
 class snaps_result(ctypes.Structure):
@@ -101,6 +108,8 @@ def lib():
             "snaps_trace_read": ([p, p, p], i32),
             "snaps_select": ([p, p, i32, p, p, i32, p, i32, i32, p, p, p, p, p], i32),
             "snaps_eps_selectivity": ([p, p, i32, p, i32, i32, i32, p, p, p], i32),
+            "snaps_autotune": ([p, i32, p, p], i32),
+            "snaps_autotune_clear": ([p], i32),
         }
         for name, (args, res) in sig.items():
             fn = getattr(L, name)
@@ -279,6 +288,19 @@ def snaps_eps_range(pop: int, n: int, masks, s_min: float = 0.001, s_max: float 
     s_max n.  Returns (eps_min, eps_max), each shaped (m,)."""
     eps, _ = snaps_eps_selectivity(pop, masks, [s_min * n, s_max * n], n_sample, n_bins, stream)
     return eps[:, 0].copy(), eps[:, 1].copy()
+
+
+def snaps_autotune(pop: int, k: int, stream=None):
+    """Time the index routes for subspaces of 2-4 features on this population
+    and record the fastest in its context.  Returns one dict per dimension."""
+    out = (snaps_tune_entry * 3)()
+    _check(lib().snaps_autotune(pop, k, out, _stream(stream)), "snaps_autotune")
+    return [{"d": e.d, "grid": bool(e.grid), "cell_mult": e.cell_mult, "ms_brute": e.ms_brute,
+             "ms_grid": list(e.ms_grid)} for e in out]
+
+
+def snaps_autotune_clear(ctx: int) -> None:
+    _check(lib().snaps_autotune_clear(ctx), "snaps_autotune_clear")
 
 
 def snaps_scores_static(device: int, feat, masks, k: int, eps=None, flags: int = SNAPS_NORM_MINMAX,

@@ -103,6 +103,11 @@ struct snaps_ctx {
     cudaStream_t cap_stream = nullptr;
     std::unordered_map<int64_t, int> sort_kernels;
 
+    // index route per (population size class, subspace dimension, k class),
+    // recorded by snaps_autotune
+    std::mutex tune_mu;
+    std::unordered_map<uint32_t, snaps_tune_entry> tune;
+
     // tracing
     std::mutex tr_mu;
     bool tracing = false;
@@ -293,7 +298,25 @@ size_t order_sort_temp(int64_t items, int end_bit)
 // The grid of one low-dimensional subspace: cell width eps (the default radius
 // when there is no eps join or eps is 0) with a 2^-10 margin, widened where
 // needed so that the grid has at most kGridMaxCells cells.
-GridSpec make_grid(const JobSpec &j, int m, float eps2)
+// Key of the autotuner's table: floor(log2 n), the dimension, and whether the
+// kNN lists take the k <= 16 or the k <= 32 form of the joins.
+uint32_t tune_key(int64_t n, int d, int k)
+{
+    int nb = 0;
+    while ((int64_t(1) << (nb + 1)) <= n) ++nb;
+    return ((uint32_t)nb << 16) | ((uint32_t)d << 8) | (k > 16 ? 1u : 0u);
+}
+
+bool tune_lookup(snaps_ctx *ctx, int64_t n, int d, int k, snaps_tune_entry *e)
+{
+    std::lock_guard<std::mutex> g(ctx->tune_mu);
+    auto it = ctx->tune.find(tune_key(n, d, k));
+    if (it == ctx->tune.end()) return false;
+    *e = it->second;
+    return true;
+}
+
+GridSpec make_grid(const JobSpec &j, int m, float eps2, float cell_mult)
 {
     const snaps_pop *p = j.pop;
     const uint32_t mask = j.masks[m];
@@ -305,7 +328,7 @@ GridSpec make_grid(const JobSpec &j, int m, float eps2)
         if ((mask >> f) & 1u) g.feat[t++] = f;
     for (; t < 4; ++t) g.feat[t] = -1;
     const double eps = eps2 > 0.f ? std::sqrt((double)eps2) : std::sqrt(0.0025 * g.d);
-    double w = eps * (1.0 + 1.0 / 1024.0);
+    double w = eps * (1.0 + 1.0 / 1024.0) * std::max(1.0, (double)cell_mult);
     const int cap = (int)std::floor(std::pow((double)kGridMaxCells, 1.0 / g.D));
     double span[3];
     for (int q = 0; q < g.D; ++q) {
@@ -337,11 +360,30 @@ Plan make_plan(const JobSpec &j)
     };
     // subspaces of <= kGridMaxDim features on the grid index (sort-by-cell, Sec. 3.8.1)
     const uint32_t index = j.precision & ~0xFFu;
-    const bool grid = index == SNAPS_INDEX_GRID || (index == 0u && j.pop->n >= SNAPS_GRID_AUTO_N);
+    // requested subspaces per 32-subspace chunk: a subspace that shares its
+    // chunk rides the tree kernel's shared walk; a lone one (and every one in
+    // the tensor-core form) is joined on its own
+    const bool tc_form = (j.precision & 0xFFu) == SNAPS_TC_F16;
+    std::unordered_map<uint32_t, int> per_chunk;
+    for (int m = 0; m < j.n_masks; ++m) ++per_chunk[(uint32_t)j.masks[m] >> kTreeLowBits];
     std::vector<int> rest;
     for (int m = 0; m < j.n_masks; ++m) {
-        if (grid && popc16(j.masks[m]) <= kGridMaxDim) {
-            pl.grids.push_back(make_grid(j, m, eps2_of(m)));
+        const int d = popc16(j.masks[m]);
+        bool grid = false;
+        float mult = 1.f;
+        if (d <= kGridMaxDim && index != SNAPS_INDEX_NONE) {
+            // the built-in rule: the index pays from SNAPS_GRID_AUTO_N objects on.
+            // snaps_autotune's choice (grid against a subspace joined on its own)
+            // decides for the subspaces that would be joined on their own.
+            snaps_tune_entry te;
+            const bool tuned = tune_lookup(j.pop->ctx, j.pop->n, d, j.k, &te);
+            const bool alone = tc_form || per_chunk[(uint32_t)j.masks[m] >> kTreeLowBits] < 2;
+            if (tuned) mult = te.cell_mult;
+            grid = index == SNAPS_INDEX_GRID ||
+                   (tuned && alone ? te.grid != 0 : j.pop->n >= SNAPS_GRID_AUTO_N);
+        }
+        if (grid) {
+            pl.grids.push_back(make_grid(j, m, eps2_of(m), mult));
             pl.grid_max_cells = std::max(pl.grid_max_cells, pl.grids.back().ncells);
         } else {
             rest.push_back(m);
@@ -1258,6 +1300,125 @@ snaps_status snaps_select(snaps_pop *pop, const uint16_t *masks, int n_masks, co
         SNAPS_TRY(put(k_select, kse.data(), (size_t)n_masks * 2 * sizeof(int32_t)));
     }
     SNAPS_CHECK_CUDA(cudaStreamSynchronize(st));
+    return SNAPS_OK;
+}
+
+snaps_status snaps_autotune(snaps_pop *pop, int k, snaps_tune_entry *out, void *stream)
+{
+    clear_error();
+    if (!pop) FAIL(SNAPS_EINVAL, "pop is NULL");
+    SNAPS_TRY(device_guard(pop->ctx));
+    snaps_ctx *ctx = pop->ctx;
+    const int64_t n = pop->n;
+    const int f = pop->f;
+    if (k < 1 || k > SNAPS_MAX_K || k > n - 1) FAIL(SNAPS_EINVAL, "k must be in 1..min(%d, n - 1)", SNAPS_MAX_K);
+    if (f < 2) FAIL(SNAPS_EINVAL, "the population needs >= 2 features");
+    cudaStream_t st = (cudaStream_t)stream;
+    static const float kMults[SNAPS_TUNE_CELLS] = {1.f, 2.f, 4.f};
+
+    // the population it times: this one, or an evenly strided sample of it
+    snaps_pop *tp = pop;
+    float *feat = nullptr, *sample = nullptr;
+    auto cleanup = [&]() {
+        if (tp != pop) snaps_release(tp);
+        if (feat) cudaFree(feat);
+        if (sample) cudaFree(sample);
+    };
+    const int64_t m = std::min<int64_t>(n, SNAPS_TUNE_MAX_N);
+    if (m < n) {
+        const int64_t stride = n / m;
+        if (cudaMalloc(&feat, sizeof(float) * (size_t)n * f) != cudaSuccess ||
+            cudaMalloc(&sample, sizeof(float) * (size_t)m * f) != cudaSuccess) {
+            cleanup();
+            FAIL(SNAPS_ENOMEM, "no device memory for the tuning sample");
+        }
+        snaps_status r = snaps_pop_features(pop, feat, stream);
+        if (r == SNAPS_OK &&
+            cudaMemcpy2DAsync(sample, sizeof(float) * f, feat, sizeof(float) * f * stride, sizeof(float) * f,
+                              (size_t)m, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+            r = SNAPS_ECUDA;
+        if (r == SNAPS_OK) r = snaps_index(ctx, sample, m, f, 0u, stream, &tp);
+        if (r != SNAPS_OK) {
+            tp = pop;
+            cleanup();
+            FAIL(r == SNAPS_ECUDA ? SNAPS_ECUDA : r, "building the tuning sample failed");
+        }
+    }
+    const int kk = (int)std::min<int64_t>(k, m - 1);
+    float *scores = nullptr;
+    if (cudaMalloc(&scores, sizeof(float) * 2 * 4 * (size_t)m) != cudaSuccess) {
+        cleanup();
+        FAIL(SNAPS_ENOMEM, "no device memory for the tuning scores");
+    }
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    snaps_tune_entry res[3] = {};
+    snaps_status r = SNAPS_OK;
+    // ms of one call over `masks` with `precision`, after one untimed call
+    auto timed = [&](const uint16_t *masks, uint32_t precision, double *ms) -> snaps_status {
+        for (int rep = 0; rep < 2; ++rep) {
+            if (rep == 1 && cudaEventRecord(e0, st) != cudaSuccess) return SNAPS_ECUDA;
+            const snaps_status q = snaps_scores(tp, masks, 2, kk, nullptr, precision, scores, nullptr, nullptr, 0,
+                                                stream);
+            if (q != SNAPS_OK) return q;
+        }
+        float t = 0.f;
+        if (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+            cudaEventElapsedTime(&t, e0, e1) != cudaSuccess)
+            return SNAPS_ECUDA;
+        *ms = t / 2.0;  // per subspace
+        return SNAPS_OK;
+    };
+    for (int d = 2; d <= kGridMaxDim && d <= f && r == SNAPS_OK; ++d) {
+        // two subspaces of d features: the lowest and the highest features
+        const uint16_t masks[2] = {(uint16_t)((1u << d) - 1u), (uint16_t)(((1u << d) - 1u) << (f - d))};
+        snaps_tune_entry &e = res[d - 2];
+        e.d = d;
+        r = timed(masks, SNAPS_FP32 | SNAPS_INDEX_NONE, &e.ms_brute);
+        for (int c = 0; c < SNAPS_TUNE_CELLS && r == SNAPS_OK; ++c) {
+            // the grid at this cell width, through the table the planner reads
+            snaps_tune_entry probe = e;
+            probe.grid = 1;
+            probe.cell_mult = kMults[c];
+            {
+                std::lock_guard<std::mutex> g(ctx->tune_mu);
+                ctx->tune[tune_key(tp->n, d, kk)] = probe;
+            }
+            r = timed(masks, SNAPS_FP32 | SNAPS_INDEX_GRID, &e.ms_grid[c]);
+        }
+        if (r != SNAPS_OK) break;
+        int best = 0;
+        for (int c = 1; c < SNAPS_TUNE_CELLS; ++c)
+            if (e.ms_grid[c] < e.ms_grid[best]) best = c;
+        e.grid = e.ms_grid[best] < e.ms_brute ? 1 : 0;
+        e.cell_mult = kMults[best];
+    }
+    {
+        // the choices hold for populations of this one's size class; a sample's
+        // probe entries are dropped
+        std::lock_guard<std::mutex> g(ctx->tune_mu);
+        for (int d = 2; d <= kGridMaxDim; ++d) {
+            if (tp != pop) ctx->tune.erase(tune_key(tp->n, d, kk));
+            if (r == SNAPS_OK && res[d - 2].d == d) ctx->tune[tune_key(n, d, k)] = res[d - 2];
+            else ctx->tune.erase(tune_key(n, d, k));
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(scores);
+    cleanup();
+    if (r != SNAPS_OK) return r;
+    if (out) std::memcpy(out, res, sizeof(res));
+    return SNAPS_OK;
+}
+
+snaps_status snaps_autotune_clear(snaps_ctx *ctx)
+{
+    clear_error();
+    if (!ctx) FAIL(SNAPS_EINVAL, "ctx is NULL");
+    std::lock_guard<std::mutex> g(ctx->tune_mu);
+    ctx->tune.clear();
     return SNAPS_OK;
 }
 
