@@ -134,8 +134,11 @@ __device__ __forceinline__ float fold4(float4 a, float4 q)
 }
 
 // Per-warp state of one query's join.
+constexpr int kScanUnroll = 4;  // candidate batches of 32 loaded ahead in a scan
+
 struct QueryState {
     float4 q;
+    int qrow;                // the query's position in cell order
     int qorig;
     float e2;
     float esc;
@@ -152,26 +155,37 @@ __device__ __forceinline__ void scan_range(const float4 *__restrict__ pts, const
                                            int beg, int end, QueryState &st, bool do_eps)
 {
     const unsigned lane = dev::lane_id();
-    for (int b = beg; b < end; b += 32) {
-        const int j = b + (int)lane;
-        const bool valid = j < end;
-        float d2 = CUDART_INF_F;
-        int oj = 0x7fffffff;
-        if (valid) {
-            oj = orig[j];
-            d2 = oj == st.qorig ? CUDART_INF_F : fold4(pts[j], st.q);  // never its own neighbour
+    for (int b0 = beg; b0 < end; b0 += 32 * kScanUnroll) {
+        // the rows of kScanUnroll batches are in flight before any is used
+        float4 pv[kScanUnroll];
+#pragma unroll
+        for (int u = 0; u < kScanUnroll; ++u) {
+            const int j = b0 + 32 * u + (int)lane;
+            pv[u] = j < end ? pts[j] : make_float4(0.f, 0.f, 0.f, 0.f);
         }
+#pragma unroll
+        for (int u = 0; u < kScanUnroll; ++u) {
+        const int j = b0 + 32 * u + (int)lane;
+        const bool valid = j < end && j != st.qrow;  // never its own neighbour
+        const float d2 = valid ? fold4(pv[u], st.q) : CUDART_INF_F;
         if (do_eps) {
             const bool e = d2 <= st.e2;
             st.cnt += __popc(__ballot_sync(dev::kFull, e));
             if (e) st.qs += dev::eps_quant(d2, st.esc);
         }
         if (st.k > 0) {
-            // every lane takes part in the shuffle (it is not inside the || below)
-            const int jk = __shfl_sync(dev::kFull, st.my_j, st.k - 1);
-            const bool want = d2 < st.T || (d2 == st.T && oj < jk);
-            const unsigned bal = __ballot_sync(dev::kFull, want);
-            if (bal) dev::list_insert(bal, d2, oj, st.my_d, st.my_j, st.k, st.T);
+            // candidates at or below the k-th distance are rare once the list
+            // is full: their original indices and the exact rule (a tie goes
+            // to the smaller original index) are taken only then
+            const bool cand = valid && d2 <= st.T;
+            if (__ballot_sync(dev::kFull, cand)) {
+                const int oj = cand ? orig[j] : 0x7fffffff;
+                const int jk = __shfl_sync(dev::kFull, st.my_j, st.k - 1);
+                const bool want = cand && (d2 < st.T || oj < jk);
+                const unsigned bal = __ballot_sync(dev::kFull, want);
+                if (bal) dev::list_insert(bal, d2, oj, st.my_d, st.my_j, st.k, st.T);
+            }
+        }
         }
     }
 }
@@ -190,7 +204,7 @@ __device__ __forceinline__ void scan_cells(const GridSpec &g, const float4 *pts,
     scan_range(pts, orig, start[la], start[la + (b - a) + 1], st, do_eps);
 }
 
-__global__ void __launch_bounds__(kGridWarps * 32)
+__global__ void __launch_bounds__(kGridWarps * 32, 2)
     grid_join_kernel(const float4 *__restrict__ pts, const int32_t *__restrict__ orig,
                      const int32_t *__restrict__ start, int n, GridSpec g, int k, JoinOut o)
 {
@@ -200,6 +214,7 @@ __global__ void __launch_bounds__(kGridWarps * 32)
     if (p >= n) return;
     QueryState st;
     st.q = pts[p];
+    st.qrow = p;
     st.qorig = orig[p];
     st.e2 = g.eps2;
     st.esc = dev::eps_scale(g.eps2).scale;
