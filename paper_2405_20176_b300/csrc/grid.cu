@@ -113,7 +113,11 @@ __global__ void grid_gather_kernel(const float4 *__restrict__ x, const int32_t *
 {
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
         const int64_t i = perm[p];
-        pts[p] = gather_point(x, i, g);
+        const float4 v = gather_point(x, i, g);
+        if (g.d <= 2)
+            reinterpret_cast<float2 *>(pts)[p] = make_float2(v.x, v.y);  // 8-byte points
+        else
+            pts[p] = v;
         orig[p] = __float_as_int(x[row_quad(i, 3)].w);
     }
 }
@@ -133,11 +137,29 @@ __device__ __forceinline__ float fold4(float4 a, float4 q)
     return acc;
 }
 
+// Subspaces of <= 2 features keep 8-byte points; the fold is the float4 fold
+// without the two padding FMAs, which add exact zeros.
+__device__ __forceinline__ float fold4(float2 a, float2 q)
+{
+    float acc = 0.f;
+    float d = a.x - q.x;
+    acc = fmaf(d, d, acc);
+    d = a.y - q.y;
+    acc = fmaf(d, d, acc);
+    return acc;
+}
+
+__device__ __forceinline__ void point_cell(const GridSpec &g, float2 p, int (&c)[3])
+{
+    point_cell(g, make_float4(p.x, p.y, 0.f, 0.f), c);
+}
+
 // Per-warp state of one query's join.
 constexpr int kScanUnroll = 4;  // candidate batches of 32 loaded ahead in a scan
 
+template <typename V>
 struct QueryState {
-    float4 q;
+    V q;
     int qrow;                // the query's position in cell order
     int qorig;
     float e2;
@@ -151,17 +173,18 @@ struct QueryState {
 };
 
 // Scan sorted positions [beg, end) for the eps join (when do_eps) and the kNN list.
-__device__ __forceinline__ void scan_range(const float4 *__restrict__ pts, const int32_t *__restrict__ orig,
-                                           int beg, int end, QueryState &st, bool do_eps)
+template <typename V>
+__device__ __forceinline__ void scan_range(const V *__restrict__ pts, const int32_t *__restrict__ orig,
+                                           int beg, int end, QueryState<V> &st, bool do_eps)
 {
     const unsigned lane = dev::lane_id();
     for (int b0 = beg; b0 < end; b0 += 32 * kScanUnroll) {
         // the rows of kScanUnroll batches are in flight before any is used
-        float4 pv[kScanUnroll];
+        V pv[kScanUnroll];
 #pragma unroll
         for (int u = 0; u < kScanUnroll; ++u) {
             const int j = b0 + 32 * u + (int)lane;
-            pv[u] = j < end ? pts[j] : make_float4(0.f, 0.f, 0.f, 0.f);
+            pv[u] = j < end ? pts[j] : V{};
         }
 #pragma unroll
         for (int u = 0; u < kScanUnroll; ++u) {
@@ -192,9 +215,10 @@ __device__ __forceinline__ void scan_range(const float4 *__restrict__ pts, const
 
 // Scan the cells of index-space row (c0, c1) [the leading D - 1 coordinates]
 // from last-dimension cell a to b (inclusive, clipped).
-__device__ __forceinline__ void scan_cells(const GridSpec &g, const float4 *pts, const int32_t *orig,
+template <typename V>
+__device__ __forceinline__ void scan_cells(const GridSpec &g, const V *pts, const int32_t *orig,
                                            const int32_t *start, int i0, int i1, int a, int b,
-                                           QueryState &st, bool do_eps)
+                                           QueryState<V> &st, bool do_eps)
 {
     const int nl = g.D == 2 ? g.nc[1] : g.nc[2];
     a = max(a, 0);
@@ -204,15 +228,16 @@ __device__ __forceinline__ void scan_cells(const GridSpec &g, const float4 *pts,
     scan_range(pts, orig, start[la], start[la + (b - a) + 1], st, do_eps);
 }
 
+template <typename V>
 __global__ void __launch_bounds__(kGridWarps * 32, 2)
-    grid_join_kernel(const float4 *__restrict__ pts, const int32_t *__restrict__ orig,
+    grid_join_kernel(const V *__restrict__ pts, const int32_t *__restrict__ orig,
                      const int32_t *__restrict__ start, int n, GridSpec g, int k, JoinOut o)
 {
     const int warp = threadIdx.x >> 5;
     const unsigned lane = dev::lane_id();
     const int p = blockIdx.x * kGridWarps + warp;
     if (p >= n) return;
-    QueryState st;
+    QueryState<V> st;
     st.q = pts[p];
     st.qrow = p;
     st.qorig = orig[p];
@@ -375,7 +400,11 @@ snaps_status run_grid_subspace(const JoinShape &s, const GridSpec &g, const Join
     grid_gather_kernel<<<blocks, threads, 0, st>>>(s.x, b.v_out, n, g, b.pts, b.orig);
     SNAPS_CHECK_CUDA(cudaGetLastError());
     const unsigned jb = (unsigned)((n + kGridWarps - 1) / kGridWarps);
-    grid_join_kernel<<<jb, kGridWarps * 32, 0, st>>>(b.pts, b.orig, b.start, (int)n, g, s.k, o);
+    if (g.d <= 2)
+        grid_join_kernel<float2><<<jb, kGridWarps * 32, 0, st>>>(reinterpret_cast<const float2 *>(b.pts), b.orig,
+                                                                  b.start, (int)n, g, s.k, o);
+    else
+        grid_join_kernel<float4><<<jb, kGridWarps * 32, 0, st>>>(b.pts, b.orig, b.start, (int)n, g, s.k, o);
     SNAPS_CHECK_CUDA(cudaGetLastError());
     return SNAPS_OK;
 }
