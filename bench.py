@@ -95,6 +95,8 @@ def parse():
                     help="Rubin-scale leg: P of the 105 two-feature subspaces (evenly spaced) at --rubin-n "
                          "objects through the grid index")
     ap.add_argument("--rubin-n", type=int, default=5_000_000)
+    ap.add_argument("--rubin-cells", type=int, default=0, metavar="R",
+                    help="grid cells 1/R of eps wide for the Rubin leg (0: the library's choice)")
     ap.add_argument("--serving-max-n", type=int, default=100000)
     ap.add_argument("--serving-max-masks", type=int, default=64)
     ap.add_argument("--serving-slots", type=int, default=4)
@@ -546,6 +548,8 @@ def run_rubin(args):
     masks = pairs[np.unique(sel)]
     x = snaps_inputs.population(n, 0)
     ctx = snaps.snaps_create(0)
+    if args.rubin_cells:
+        snaps.snaps_autotune_set(ctx, n, args.k, 2, True, 1.0 / args.rubin_cells)
     stream = torch.cuda.current_stream()
     t0 = time.perf_counter()
     pop = snaps.snaps_index(ctx, torch.from_numpy(x).cuda(), snaps.SNAPS_NORM_MINMAX, stream=stream)
@@ -579,7 +583,8 @@ def run_rubin(args):
             "clocks": clk.summary(), "dtype": "f32", "data": "synthetic",
             "config": {"workload": f"N={n} objects (seed 0), {masks.size} of the 105 two-feature subspaces "
                                    f"(evenly spaced), k={args.k}, eps=0.05*sqrt(2); grid index over both "
-                                   f"features; scores and top-100 on the device",
+                                   f"features, cells {'eps/3 (the library default)' if not args.rubin_cells else f'eps/{args.rubin_cells}'} "
+                                   f"wide; scores and top-100 on the device",
                        "full_subspace": "not run: 2.5e13 brute-force evaluations, and a 3-feature grid "
                                         "prunes little in 15 dimensions"}}
 

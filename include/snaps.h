@@ -77,7 +77,9 @@ typedef enum snaps_status {
 #define SNAPS_INDEX_NONE 0x200u  /* no grid index: every subspace is joined by brute force */
 /* Without either index flag, subspaces of <= 4 features take the grid index
  * (sort-by-cell over up to 3 of their features, Sec. 3.8.1) when
- * n >= SNAPS_GRID_AUTO_N.  Every choice gives the same results. */
+ * n >= SNAPS_GRID_AUTO_N.  Its cells are a third of eps wide for two-feature
+ * subspaces and eps wide otherwise, unless snaps_autotune recorded another
+ * choice.  Every choice gives the same results. */
 #define SNAPS_GRID_AUTO_N 65536
 
 typedef struct snaps_ctx snaps_ctx;
@@ -241,24 +243,26 @@ snaps_status snaps_eps_selectivity(snaps_pop *pop, const uint16_t *masks, int n_
 
 /* ---- autotuning of the index route ---- */
 
-#define SNAPS_TUNE_CELLS 3       /* grid cell widths tried: 1, 2 and 4 x eps */
+#define SNAPS_TUNE_CELLS 3       /* grid cell widths tried: 1, 1/2 and 1/3 x eps */
 #define SNAPS_TUNE_MAX_N 65536   /* larger populations are timed on a sample */
 
 /* One subspace dimension's measurements and choice. */
 typedef struct snaps_tune_entry {
     int d;                            /* subspace dimension, 2..4 */
     int grid;                         /* 1: the grid index, 0: brute force */
-    float cell_mult;                  /* the grid's cell width in units of eps */
+    float cell_mult;                  /* the grid's cell width in units of eps: 1 / R
+                                         (R = 1, 2, 3: a (2R + 1)^D block of cells),
+                                         or >= 1 (one cell that wide, a 3^D block) */
     double ms_brute;                  /* ms per subspace, brute force */
-    double ms_grid[SNAPS_TUNE_CELLS]; /* ms per subspace, grid at 1, 2, 4 x eps */
+    double ms_grid[SNAPS_TUNE_CELLS]; /* ms per subspace, grid at 1, 1/2, 1/3 x eps */
 } snaps_tune_entry;
 
 /* Choose how subspaces of 2, 3 and 4 features are joined on populations of
  * this one's size class.  For each dimension d it times two subspaces of d
  * features (the lowest and the highest features) with this k and the default
  * radius: by brute force, and on the grid index (sort-by-cell, Sec. 3.8.1)
- * with cells 1, 2 and 4 times eps wide (any width >= eps finds every
- * neighbour).  Populations of more than SNAPS_TUNE_MAX_N objects are timed on
+ * with cells 1, 1/2 and 1/3 of eps wide, whose search blocks are 3, 5 and 7
+ * cells across per index dimension (every neighbour lies within them).  Populations of more than SNAPS_TUNE_MAX_N objects are timed on
  * an evenly strided sample of that many.  The fastest choice is recorded in
  * the context under (floor(log2 n), d, k <= 16 or not).  Calls without an
  * index flag then follow it for the subspaces that are joined on their own:
@@ -272,6 +276,11 @@ typedef struct snaps_tune_entry {
  * The call synchronises `stream`.
  * Errors: EINVAL, ENOMEM, ECUDA. */
 snaps_status snaps_autotune(snaps_pop *pop, int k, snaps_tune_entry *out, void *stream);
+
+/* Record a choice without timing it, for populations of n's size class and
+ * this k class: e->d (2..4), e->grid, e->cell_mult (in (0, 64]; the times are
+ * ignored).  Errors: EINVAL. */
+snaps_status snaps_autotune_set(snaps_ctx *ctx, int64_t n, int k, const snaps_tune_entry *e);
 
 /* Forget every recorded choice (the built-in rule applies again). */
 snaps_status snaps_autotune_clear(snaps_ctx *ctx);

@@ -110,6 +110,7 @@ def lib():
             "snaps_eps_selectivity": ([p, p, i32, p, i32, i32, i32, p, p, p], i32),
             "snaps_autotune": ([p, i32, p, p], i32),
             "snaps_autotune_clear": ([p], i32),
+            "snaps_autotune_set": ([p, i64, i32, p], i32),
         }
         for name, (args, res) in sig.items():
             fn = getattr(L, name)
@@ -297,6 +298,12 @@ def snaps_autotune(pop: int, k: int, stream=None):
     _check(lib().snaps_autotune(pop, k, out, _stream(stream)), "snaps_autotune")
     return [{"d": e.d, "grid": bool(e.grid), "cell_mult": e.cell_mult, "ms_brute": e.ms_brute,
              "ms_grid": list(e.ms_grid)} for e in out]
+
+
+def snaps_autotune_set(ctx: int, n: int, k: int, d: int, grid: bool, cell_mult: float) -> None:
+    """Record an index choice for populations of n's size class without timing it."""
+    e = snaps_tune_entry(d=d, grid=1 if grid else 0, cell_mult=cell_mult)
+    _check(lib().snaps_autotune_set(ctx, n, k, ctypes.byref(e)), "snaps_autotune_set")
 
 
 def snaps_autotune_clear(ctx: int) -> None:

@@ -328,7 +328,11 @@ GridSpec make_grid(const JobSpec &j, int m, float eps2, float cell_mult)
         if ((mask >> f) & 1u) g.feat[t++] = f;
     for (; t < 4; ++t) g.feat[t] = -1;
     const double eps = eps2 > 0.f ? std::sqrt((double)eps2) : std::sqrt(0.0025 * g.d);
-    double w = eps * (1.0 + 1.0 / 1024.0) * std::max(1.0, (double)cell_mult);
+    // cells eps (1 + 2^-10) * cell_mult wide: for cell_mult = 1 / R, R cells
+    // per eps and a (2R + 1)^D block; for cell_mult >= 1, one cell and a 3^D block
+    const double e1 = eps * (1.0 + 1.0 / 1024.0);
+    const int r_req = cell_mult < 1.f ? std::max(1, (int)std::lround(1.0 / (double)cell_mult)) : 1;
+    double w = cell_mult < 1.f ? e1 / r_req : e1 * std::max(1.0, (double)cell_mult);
     const int cap = (int)std::floor(std::pow((double)kGridMaxCells, 1.0 / g.D));
     double span[3];
     for (int q = 0; q < g.D; ++q) {
@@ -339,6 +343,8 @@ GridSpec make_grid(const JobSpec &j, int m, float eps2, float cell_mult)
     }
     g.w = (float)w;
     g.inv_w = (float)(1.0 / w);
+    // cells widened to respect the cell cap need fewer of them per eps
+    g.R = std::max(1, std::min(r_req, (int)std::ceil(e1 / w - 1e-9)));
     g.ncells = 1;
     for (int q = 0; q < g.D; ++q) {
         g.nc[q] = std::min(cap, (int)std::floor(span[q] / w) + 1);
@@ -370,7 +376,10 @@ Plan make_plan(const JobSpec &j)
     for (int m = 0; m < j.n_masks; ++m) {
         const int d = popc16(j.masks[m]);
         bool grid = false;
-        float mult = 1.f;
+        // built-in cell width: a third of eps for a two-feature index (the 7 x 7
+        // block covers 5.4 eps^2 around the eps-disk instead of 9 eps^2), eps
+        // for a three-feature one
+        float mult = d <= 2 ? 1.f / 3.f : 1.f;
         if (d <= kGridMaxDim && index != SNAPS_INDEX_NONE) {
             // the built-in rule: the index pays from SNAPS_GRID_AUTO_N objects on.
             // snaps_autotune's choice (grid against a subspace joined on its own)
@@ -1314,7 +1323,7 @@ snaps_status snaps_autotune(snaps_pop *pop, int k, snaps_tune_entry *out, void *
     if (k < 1 || k > SNAPS_MAX_K || k > n - 1) FAIL(SNAPS_EINVAL, "k must be in 1..min(%d, n - 1)", SNAPS_MAX_K);
     if (f < 2) FAIL(SNAPS_EINVAL, "the population needs >= 2 features");
     cudaStream_t st = (cudaStream_t)stream;
-    static const float kMults[SNAPS_TUNE_CELLS] = {1.f, 2.f, 4.f};
+    static const float kMults[SNAPS_TUNE_CELLS] = {1.f, 0.5f, 1.f / 3.f};
 
     // the population it times: this one, or an evenly strided sample of it
     snaps_pop *tp = pop;
@@ -1410,6 +1419,18 @@ snaps_status snaps_autotune(snaps_pop *pop, int k, snaps_tune_entry *out, void *
     cleanup();
     if (r != SNAPS_OK) return r;
     if (out) std::memcpy(out, res, sizeof(res));
+    return SNAPS_OK;
+}
+
+snaps_status snaps_autotune_set(snaps_ctx *ctx, int64_t n, int k, const snaps_tune_entry *e)
+{
+    clear_error();
+    if (!ctx || !e) FAIL(SNAPS_EINVAL, "ctx and e must not be NULL");
+    if (n < 2 || k < 0 || k > SNAPS_MAX_K) FAIL(SNAPS_EINVAL, "need n >= 2 and 0 <= k <= %d", SNAPS_MAX_K);
+    if (e->d < 2 || e->d > kGridMaxDim) FAIL(SNAPS_EINVAL, "d must be in 2..%d", kGridMaxDim);
+    if (!(e->cell_mult > 0.f && e->cell_mult <= 64.f)) FAIL(SNAPS_EINVAL, "cell_mult must be in (0, 64]");
+    std::lock_guard<std::mutex> g(ctx->tune_mu);
+    ctx->tune[tune_key(n, e->d, k)] = *e;
     return SNAPS_OK;
 }
 

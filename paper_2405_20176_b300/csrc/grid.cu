@@ -253,34 +253,35 @@ __global__ void __launch_bounds__(kGridWarps * 32, 2)
     point_cell(g, st.q, c);
     const bool do_eps = g.eps2 >= 0.f;
     const int D = g.D;
-    // the 3^D block: every eps-neighbour is inside it.  The query's own cell goes
-    // first, so that the kNN threshold is tight before the rest is scanned.
+    // the (2R + 1)^D block: every eps-neighbour is inside it.  The query's own
+    // cell goes first, so that the kNN threshold is tight before the rest is scanned.
+    const int R = g.R;
     const int cl = D == 2 ? c[1] : c[2];
     scan_cells(g, pts, orig, start, c[0], c[1], cl, cl, st, do_eps);
     if (D == 2) {
-        for (int i0 = max(c[0] - 1, 0); i0 <= min(c[0] + 1, g.nc[0] - 1); ++i0) {
+        for (int i0 = max(c[0] - R, 0); i0 <= min(c[0] + R, g.nc[0] - 1); ++i0) {
             if (i0 == c[0]) {
-                scan_cells(g, pts, orig, start, i0, 0, cl - 1, cl - 1, st, do_eps);
-                scan_cells(g, pts, orig, start, i0, 0, cl + 1, cl + 1, st, do_eps);
+                scan_cells(g, pts, orig, start, i0, 0, cl - R, cl - 1, st, do_eps);
+                scan_cells(g, pts, orig, start, i0, 0, cl + 1, cl + R, st, do_eps);
             } else {
-                scan_cells(g, pts, orig, start, i0, 0, cl - 1, cl + 1, st, do_eps);
+                scan_cells(g, pts, orig, start, i0, 0, cl - R, cl + R, st, do_eps);
             }
         }
     } else {
-        for (int i0 = max(c[0] - 1, 0); i0 <= min(c[0] + 1, g.nc[0] - 1); ++i0)
-            for (int i1 = max(c[1] - 1, 0); i1 <= min(c[1] + 1, g.nc[1] - 1); ++i1) {
+        for (int i0 = max(c[0] - R, 0); i0 <= min(c[0] + R, g.nc[0] - 1); ++i0)
+            for (int i1 = max(c[1] - R, 0); i1 <= min(c[1] + R, g.nc[1] - 1); ++i1) {
                 if (i0 == c[0] && i1 == c[1]) {
-                    scan_cells(g, pts, orig, start, i0, i1, cl - 1, cl - 1, st, do_eps);
-                    scan_cells(g, pts, orig, start, i0, i1, cl + 1, cl + 1, st, do_eps);
+                    scan_cells(g, pts, orig, start, i0, i1, cl - R, cl - 1, st, do_eps);
+                    scan_cells(g, pts, orig, start, i0, i1, cl + 1, cl + R, st, do_eps);
                 } else {
-                    scan_cells(g, pts, orig, start, i0, i1, cl - 1, cl + 1, st, do_eps);
+                    scan_cells(g, pts, orig, start, i0, i1, cl - R, cl + R, st, do_eps);
                 }
             }
     }
     // kNN rings: objects in ring r are at least (r - 1) w away
     if (k > 0) {
         const int span = max(g.nc[0], max(D > 1 ? g.nc[1] : 0, D > 2 ? g.nc[2] : 0));
-        for (int r = 2; r <= span; ++r) {
+        for (int r = R + 1; r <= span; ++r) {
             const float reach = (float)(r - 1) * g.w * (1.f - 1.f / 1024.f);
             if (reach * reach > st.T) break;
             if (D == 2) {

@@ -24,7 +24,8 @@ struct GridSpec {
     int D;            // index dimensions: min(d, kGridIndexDims)
     int feat[4];      // the subspace's features, highest first; -1 past d
     float lo[3];      // grid origin per index dimension (stored feature units)
-    float w, inv_w;   // cell width (>= eps, with a 2^-10 margin) and its inverse
+    float w, inv_w;   // cell width and its inverse: R w >= eps, with a 2^-10 margin
+    int R;            // block radius in cells: every eps-neighbour is within R cells per dimension
     int nc[3];        // cells per index dimension
     int ncells;       // product of nc
     float eps2;       // squared radius; < 0: no eps join

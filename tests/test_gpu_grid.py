@@ -136,3 +136,22 @@ def test_grid_chosen_at_scale_matches_oracle(ctx):
         check_knn(x64, mask, idx[s][q], dist[s][q], r.knn_idx, r.knn_d2, queries=q)
         lo, hi = eps_bounds(x64, mask, e2, queries=q)
         check_eps(cnt[s][q], mean[s][q], r, lo, hi)
+
+
+@pytest.mark.parametrize("cells", [2, 3])
+def test_finer_cells_equal_brute_force(ctx, cells):
+    # cells 1/R of eps wide search a (2R + 1)^D block; the same bits as brute
+    # force, including the kNN rings of scattered points and a radius of zero
+    try:
+        for n, k in ((2000, 10), (900, 20)):
+            for d in (2, 3, 4):
+                snaps.snaps_autotune_set(ctx, n, k, d, True, 1.0 / cells)
+        assert_grid_equals_brute(ctx, snaps_inputs.population(2000, 11), low_d_masks(16, 11), 10)
+        rng = np.random.default_rng(8)
+        x = np.clip(rng.normal(0.5, 0.01, size=(900, 15)), 0, 1)
+        x[:40] = rng.random((40, 15))
+        masks = low_d_masks(8, 8)
+        assert_grid_equals_brute(ctx, x.astype(np.float32), masks, 20)
+        assert_grid_equals_brute(ctx, x.astype(np.float32), masks, 20, eps=np.zeros(masks.size, np.float32))
+    finally:
+        snaps.snaps_autotune_clear(ctx)
