@@ -73,10 +73,11 @@ def parse():
                     help="'all', a count of seeded sample subspaces, or 'chunk:H' (H = 10 binary "
                          "digits: the 32 subspaces (H << 5) | L sharing that high part)")
     ap.add_argument("--k", type=int, default=K_DEFAULT)
-    ap.add_argument("--precision", choices=["fp32", "tc_f16", "both"], default="both",
-                    help="fp32: the plain join; tc_f16: the tensor-core filtered join; both "
-                         "(default): time the plain join as the headline and the tensor-core "
-                         "join beside it on the same workload")
+    ap.add_argument("--precision", choices=["fp32", "tc_f16", "tc_bf16", "both", "all"], default="both",
+                    help="fp32: the plain join; tc_f16 / tc_bf16: the tensor-core filtered join "
+                         "with FP16 / BF16 operands; both (default): time the plain join as the "
+                         "headline and the FP16 tensor-core join beside it on the same workload; "
+                         "all: the BF16 tensor-core join beside those two")
     ap.add_argument("--index", choices=["auto", "grid", "none"], default="auto",
                     help="grid index for subspaces of <= 4 features: the library's choice "
                          "(auto), always, or never")
@@ -192,7 +193,9 @@ def run_ours(args, rank, world, dist):
     masks = workload_masks(args.masks)
     m, n, k = masks.size, args.n, args.k
     index_flag = {"auto": 0, "grid": snaps.SNAPS_INDEX_GRID, "none": snaps.SNAPS_INDEX_NONE}[args.index]
-    head_prec = (snaps.SNAPS_TC_F16 if args.precision == "tc_f16" else snaps.SNAPS_FP32) | index_flag
+    head_prec = {"tc_f16": snaps.SNAPS_TC_F16, "tc_bf16": snaps.SNAPS_TC_BF16}.get(
+        args.precision, snaps.SNAPS_FP32) | index_flag
+    form_name = {snaps.SNAPS_FP32: "fp32", snaps.SNAPS_TC_F16: "tc_f16", snaps.SNAPS_TC_BF16: "tc_bf16"}
     ctx = snaps.snaps_create(local)
     stream = torch.cuda.current_stream()
     x_dev = torch.from_numpy(x).to(dev)
@@ -276,9 +279,9 @@ def run_ours(args, rank, world, dist):
                 "frac_of_measured_alu": (achieved / measured_alu) if achieved else None}
 
     def tensor_roofline(trace, steps):
-        """Tensor roofline of the tensor-core join: 2 x 16 FLOPs (K = 16, FP16) per
-        (pair, subspace) evaluation against the measured dense BF16 peak (FP16 runs at
-        the same rate)."""
+        """Tensor roofline of the tensor-core join: 2 x 16 FLOPs (K = 16, FP16 or BF16)
+        per (pair, subspace) evaluation against the measured dense BF16 peak (FP16 runs
+        at the same rate)."""
         tc_ms, tc_launches = trace["join_tc"]
         flops = 2.0 * 16 * evals_per_step * steps
         achieved = flops / (tc_ms / 1e3) / 1e12 if tc_ms > 0 else None
@@ -293,14 +296,15 @@ def run_ours(args, rank, world, dist):
                 "evals_per_s": evals_per_step * steps / (tc_ms / 1e3) if tc_ms > 0 else None,
                 "kernel_ms_per_launch": tc_ms / max(tc_launches, 1)}
 
-    roofline = tensor_roofline(trace, args.steps) if (head_prec & 0xFF) == snaps.SNAPS_TC_F16 else \
+    roofline = tensor_roofline(trace, args.steps) if (head_prec & 0xFF) != snaps.SNAPS_FP32 else \
         alu_roofline(trace, args.steps)
 
-    tc_leg = None
-    if args.precision == "both":
-        tc_ms, tc_trace, tc_clocks = timed_leg(snaps.SNAPS_TC_F16 | index_flag, args.tc_steps, 1)
+    tc_legs = {}
+    for form in {"both": [snaps.SNAPS_TC_F16], "all": [snaps.SNAPS_TC_F16, snaps.SNAPS_TC_BF16]}.get(
+            args.precision, []):
+        tc_ms, tc_trace, tc_clocks = timed_leg(form | index_flag, args.tc_steps, 1)
         tc_units = float(n) * m * args.tc_steps * world
-        tc_leg = {"value": tc_units / (tc_ms / 1e3), "unit": "objects*subspaces/s",
+        tc_legs[form_name[form]] = {"value": tc_units / (tc_ms / 1e3), "unit": "objects*subspaces/s",
                   "ms_per_step": tc_ms / args.tc_steps, "steps": args.tc_steps, "warmup": 1,
                   "vs_plain": (tc_units / (tc_ms / 1e3)) / value,
                   "distance_evals_per_s": evals_per_step * args.tc_steps * world / (tc_ms / 1e3),
@@ -308,8 +312,8 @@ def run_ours(args, rank, world, dist):
                   "phase_ms_per_step": {kn: v[0] / args.tc_steps for kn, v in tc_trace.items()},
                   "gpu_launches": int(sum(v[1] for v in tc_trace.values())),
                   "clocks": tc_clocks,
-                  "exactness": "bit-identical to the plain FP32 join (FP16 filter, every survivor "
-                               "recomputed in FP32)"}
+                  "exactness": f"bit-identical to the plain FP32 join ({form_name[form][3:].upper()} "
+                               f"filter, every survivor recomputed in FP32)"}
 
     # end to end through the C ABI with host buffers
     e2e = None
@@ -354,7 +358,7 @@ def run_ours(args, rank, world, dist):
         "dtype": "f32",
         "data": "synthetic",
         "config": {"workload": workload_name(args, m), "objects": n, "subspaces": int(m), "k": k,
-                   "precision": "fp32" if (head_prec & 0xFF) == snaps.SNAPS_FP32 else "tc_f16",
+                   "precision": form_name[head_prec & 0xFF],
                    "index": args.index,
                    "l2": "flushed before every step (512 MB write)",
                    "parallelism": f"replicas x{world}"},
@@ -365,8 +369,7 @@ def run_ours(args, rank, world, dist):
         "e2e": e2e,
         "gpu_launches": launches,
     }
-    if tc_leg is not None:
-        result["tc_f16"] = tc_leg
+    result.update(tc_legs)
     return result
 
 
@@ -410,7 +413,7 @@ def run_serving(args):
     handles = [snaps.snaps_index(ctx, snaps_inputs.population(n, seed)) for n, seed in pops]
     tops = [torch.empty((m.size, 4, 100), dtype=torch.int32, device="cuda") for _, m, _ in reqs]
     torch.cuda.synchronize()
-    head = snaps.SNAPS_TC_F16 if args.precision == "tc_f16" else snaps.SNAPS_FP32
+    head = {"tc_f16": snaps.SNAPS_TC_F16, "tc_bf16": snaps.SNAPS_TC_BF16}.get(args.precision, snaps.SNAPS_FP32)
     # service time of one request alone, to set the arrival rate
     n_cal = min(8, len(reqs))
     for (pi, m, k), tp in zip(reqs[:n_cal], tops[:n_cal]):   # warm-up
@@ -476,7 +479,7 @@ def run_serving(args):
                                f"{args.serving_max_masks} subspaces (d uniform 2..15); "
                                f"k in {{5,10,20}}; eps = 0.05*sqrt(d); top-100 outputs",
                    "slots": args.serving_slots,
-                   "precision": "tc_f16" if head == snaps.SNAPS_TC_F16 else "fp32"},
+                   "precision": {snaps.SNAPS_TC_F16: "tc_f16", snaps.SNAPS_TC_BF16: "tc_bf16"}.get(head, "fp32")},
         "clocks": main["clocks"],
     }
     if tc is not None:

@@ -69,10 +69,11 @@ typedef enum snaps_status {
 #define SNAPS_NORM_MINMAX 0x1u   /* map every feature onto [0, 1] by its min and max (Sec. 3.3) */
 #define SNAPS_NAN_TO_MEAN 0x2u   /* replace NaN by the feature's mean first (Sec. 2.1) */
 
-/* precision argument of snaps_scores / snaps_request: one of the two join
+/* precision argument of snaps_scores / snaps_request: one of the three join
  * forms, optionally OR-ed with one index choice for low-dimensional subspaces */
 #define SNAPS_FP32 0u            /* plain FP32 join */
 #define SNAPS_TC_F16 1u          /* tensor-core FP16 filter, exact FP32 recompute of survivors */
+#define SNAPS_TC_BF16 2u         /* the same with BF16 operands: a 4x wider filter margin, more survivors */
 #define SNAPS_INDEX_GRID 0x100u  /* subspaces of <= 4 features always take the grid index */
 #define SNAPS_INDEX_NONE 0x200u  /* no grid index: every subspace is joined by brute force */
 /* Without either index flag, subspaces of <= 4 features take the grid index
@@ -154,12 +155,13 @@ snaps_status snaps_eps_selfjoin(snaps_pop *pop, const uint16_t *masks, int n_mas
                                 void *stream);
 
 /* Both joins and the four outlier metrics per object and subspace (Table 2).
- * k, eps: as above.  precision: SNAPS_FP32 (plain FP32 joins) or SNAPS_TC_F16
- *   (the squared-difference x subspace-mask contraction on the tensor cores
- *   as a conservative FP16 filter, survivors recomputed exactly in FP32: the
- *   same results).  SNAPS_TC_F16 needs every feature to span at most 1, which
- *   SNAPS_NORM_MINMAX guarantees (EINVAL otherwise).  Either may be OR-ed with
- *   SNAPS_INDEX_GRID or SNAPS_INDEX_NONE (see their definitions).
+ * k, eps: as above.  precision: SNAPS_FP32 (plain FP32 joins), SNAPS_TC_F16
+ *   or SNAPS_TC_BF16 (the squared-difference x subspace-mask contraction on
+ *   the tensor cores as a conservative FP16 or BF16 filter, survivors
+ *   recomputed exactly in FP32: the same results).  The tensor-core forms need
+ *   every feature to span at most 1, which SNAPS_NORM_MINMAX guarantees
+ *   (EINVAL otherwise).  Each may be OR-ed with SNAPS_INDEX_GRID or
+ *   SNAPS_INDEX_NONE (see their definitions).
  * scores: n_masks x 4 x n float32 raw metrics (rows SNAPS_SCORE_*), or NULL.
  *   Counts and in-degrees are exact integers stored as float.
  * norm:   n_masks x 4 x n float32, each metric mapped onto [0, 1] with
@@ -267,7 +269,7 @@ typedef struct snaps_tune_entry {
  * the context under (floor(log2 n), d, k <= 16 or not).  Calls without an
  * index flag then follow it for the subspaces that are joined on their own:
  * those alone among the requested ones in their 32-subspace chunk, and all of
- * them in the SNAPS_TC_F16 form.  Subspaces that share a chunk keep the
+ * them in the tensor-core forms.  Subspaces that share a chunk keep the
  * built-in rule (the grid from SNAPS_GRID_AUTO_N objects on), because there
  * the subspace-batched join shares its arithmetic and a subspace costs far
  * less than on its own.  SNAPS_INDEX_GRID uses the recorded cell width.  Every

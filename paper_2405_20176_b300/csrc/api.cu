@@ -248,12 +248,12 @@ snaps_status validate(const JobSpec &j)
     if (j.top && (j.top_n < 1 || j.top_n > 1024 || j.top_n > p->n))
         FAIL(SNAPS_EINVAL, "top_n must be in 1..min(1024, n) (got %d)", j.top_n);
     const uint32_t form = j.precision & 0xFFu, index = j.precision & ~0xFFu;
-    if (form != SNAPS_FP32 && form != SNAPS_TC_F16)
+    if (form != SNAPS_FP32 && form != SNAPS_TC_F16 && form != SNAPS_TC_BF16)
         FAIL(SNAPS_EINVAL, "unknown precision %u", j.precision);
     if (index != 0u && index != SNAPS_INDEX_GRID && index != SNAPS_INDEX_NONE)
         FAIL(SNAPS_EINVAL, "unknown index choice in precision 0x%x", j.precision);
-    if (form == SNAPS_TC_F16 && !p->unit_range)
-        FAIL(SNAPS_EINVAL, "SNAPS_TC_F16 needs every feature to span at most 1 "
+    if (form != SNAPS_FP32 && !p->unit_range)
+        FAIL(SNAPS_EINVAL, "the tensor-core forms need every feature to span at most 1 "
                            "(index the population with SNAPS_NORM_MINMAX)");
     return SNAPS_OK;
 }
@@ -369,7 +369,7 @@ Plan make_plan(const JobSpec &j)
     // requested subspaces per 32-subspace chunk: a subspace that shares its
     // chunk rides the tree kernel's shared walk; a lone one (and every one in
     // the tensor-core form) is joined on its own
-    const bool tc_form = (j.precision & 0xFFu) == SNAPS_TC_F16;
+    const bool tc_form = (j.precision & 0xFFu) != SNAPS_FP32;
     std::unordered_map<uint32_t, int> per_chunk;
     for (int m = 0; m < j.n_masks; ++m) ++per_chunk[(uint32_t)j.masks[m] >> kTreeLowBits];
     std::vector<int> rest;
@@ -398,7 +398,7 @@ Plan make_plan(const JobSpec &j)
             rest.push_back(m);
         }
     }
-    if ((j.precision & 0xFFu) == SNAPS_TC_F16) {
+    if (tc_form) {
         // the tensor-core join takes any subspaces, 128 at a time; sorted by
         // dimension, so that the threads of a warp see similar hit rates
         std::vector<int> order = rest;
@@ -715,7 +715,8 @@ snaps_status run_job(snaps_ctx *ctx, const JobSpec &j, cudaStream_t st, Scratch 
     }
     if (!pl.blocks.empty()) {
         TraceScope ts(ctx, SNAPS_PHASE_JOIN_TC, st);
-        SNAPS_TRY(launch_join_tc(shape, L.blocks, (int)pl.blocks.size(), out, ctrl, st));
+        SNAPS_TRY(launch_join_tc(shape, L.blocks, (int)pl.blocks.size(),
+                                 (j.precision & 0xFFu) == SNAPS_TC_BF16, out, ctrl, st));
     }
     if (!pl.grids.empty()) {
         const GridBufs gb = grid_carve(L.grid, n, pl.grid_max_cells);

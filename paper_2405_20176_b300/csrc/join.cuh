@@ -73,7 +73,7 @@ snaps_status launch_join_lanemask(const JoinShape &s, const MaskGroup *groups, i
 
 // Launch the tensor-core filtered join over `n_blocks` blocks (device array).
 // Requires every feature of the population to span at most 1.
-snaps_status launch_join_tc(const JoinShape &s, const TcBlock *blocks, int n_blocks,
+snaps_status launch_join_tc(const JoinShape &s, const TcBlock *blocks, int n_blocks, bool bf16,
                             const JoinOut &o, DeviceControl *ctrl, cudaStream_t st);
 
 // Launch the subspace-batched tree join over `n_chunks` chunks (device array).

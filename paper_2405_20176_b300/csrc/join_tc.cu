@@ -1,21 +1,23 @@
 // Tensor-core filtered self-join: DSSJ (Sec. 3.5) and kNNSJ (Sec. 3.6) for
 // any list of subspaces, with the one dense contraction of the method --
 // per-pair squared feature differences times the 0/1 subspace-mask matrix --
-// on the 5th-generation tensor cores (tcgen05, kind::f16, FP32 accumulators
-// in tensor memory).
+// on the 5th-generation tensor cores (tcgen05, kind::f16 with FP16 or BF16
+// operands, FP32 accumulators in tensor memory).
 //
 // The contraction.  For a query i and 128 candidates j, the B operand holds
-// per candidate the 15 squared differences (x_j - x_i)^2 rounded to FP16 and
-// a constant 1; the A operand holds per subspace S its 15 mask bits and minus
-// its filter threshold.  One MMA (M = 128 subspaces, N = 128 candidates,
-// K = 16) gives in tensor memory
+// per candidate the 15 squared differences (x_j - x_i)^2 rounded to the
+// operand type and a constant 1; the A operand holds per subspace S its 15
+// mask bits and minus its filter threshold.  One MMA (M = 128 subspaces,
+// N = 128 candidates, K = 16) gives in tensor memory
 //     D[S][j] ~= sum_{f in S} (x_jf - x_if)^2 - Tf_S,
 // and D < 0 marks the candidates that may lie within eps of the query or
 // below the current k-th distance.  Tf_S = max(k-th squared distance, eps^2)
-// * (1 + 2^-8) + 2^-20, rounded up to FP16: the FP16 rounding of a squared
-// difference is <= 2^-11 relative (2^-25 absolute below FP16's normal range)
-// and the FP32 accumulation of 16 exact products adds far less, so no true
-// neighbour is lost.  Every candidate that passes is recomputed with the
+// * (1 + m) + 2^-20, rounded up to the operand type, with m = 2^-8 for FP16
+// and 2^-6 for BF16: rounding a squared difference to FP16 is <= 2^-11
+// relative (2^-25 absolute below FP16's normal range), to BF16 <= 2^-8
+// relative, and the FP32 accumulation of 16 exact products adds far less, so
+// no true neighbour is lost.  BF16's wider margin lets more candidates through
+// to the exact recompute.  Every candidate that passes is recomputed with the
 // library's canonical FP32 fold (FMAs from the highest feature down), and only
 // that exact value decides counts, sums and kNN lists: the results are the
 // plain FP32 path's, bit for bit.
@@ -51,6 +53,7 @@
 // memory and leaves.  Populations whose features span more than a unit range
 // are rejected by the host (their squared differences could overflow FP16).
 
+#include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <math_constants.h>
 
@@ -115,13 +118,45 @@ __device__ __forceinline__ uint32_t op_off(int r, int k)
     return (uint32_t)((r >> 3) * kSBO + (k >> 3) * kLBO + (r & 7) * 16 + (k & 7) * 2);
 }
 
-// A row entry 15 for a subspace: minus its conservative FP16 filter threshold.
-__device__ __forceinline__ __half neg_filter(float t)
-{
-    if (!(t >= 0.f)) return __float2half(1.f);  // nothing to find: D >= +1 - 1 * 0 on real rows
-    const float f = fminf(t * (1.f + 0.00390625f) + 9.5367431640625e-07f, 65504.f);
-    return __hneg(__float2half_ru(f));
-}
+// Operand element encodings of the two 16-bit forms.
+template <bool BF16>
+struct Op16 {
+    // 1.0, and the "never passes" squared difference of a skipped row
+    // (65504 in FP16, 65536 in BF16: finite, and >= 2 of them exceed any
+    // threshold of a unit-range population)
+    static constexpr uint32_t kOne = BF16 ? 0x3F80u : 0x3C00u;
+    static constexpr uint32_t kBig = BF16 ? 0x4780u : 0x7BFFu;
+    // relative filter margin: 2^-8 against FP16's 2^-11 rounding of a squared
+    // difference, 2^-6 against BF16's 2^-8
+    static constexpr float kMargin = BF16 ? 0.015625f : 0.00390625f;
+    // instruction descriptor: D = F32, A and B of one type (F16 = 0, BF16 = 1),
+    // both K-major; N = 128, M = 128
+    static constexpr uint32_t kIdesc = (1u << 4) | ((BF16 ? 1u : 0u) << 7) | ((BF16 ? 1u : 0u) << 10) |
+                                       ((uint32_t)(kNC >> 3) << 17) | ((uint32_t)(kM >> 4) << 24);
+    static __device__ __forceinline__ uint32_t pack2(float a, float b)
+    {
+        if constexpr (BF16) {
+            const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+            return *reinterpret_cast<const uint32_t *>(&h);
+        } else {
+            const __half2 h = __floats2half2_rn(a, b);
+            return *reinterpret_cast<const uint32_t *>(&h);
+        }
+    }
+    // A row entry 15 for a subspace: minus its conservative filter threshold,
+    // rounded up in magnitude
+    static __device__ __forceinline__ unsigned short neg_filter(float t)
+    {
+        if (!(t >= 0.f)) return (unsigned short)kOne;  // nothing to find: D >= +1 - 1 * 0 on real rows
+        if constexpr (BF16) {
+            const float f = fminf(t * (1.f + kMargin) + 9.5367431640625e-07f, 1e30f);
+            return __bfloat16_as_ushort(__hneg(__float2bfloat16_ru(f)));
+        } else {
+            const float f = fminf(t * (1.f + kMargin) + 9.5367431640625e-07f, 65504.f);
+            return __half_as_ushort(__hneg(__float2half_ru(f)));
+        }
+    }
+};
 
 __device__ __forceinline__ float eps_floor(float e2) { return e2 >= 0.f ? e2 : -CUDART_INF_F; }
 
@@ -228,27 +263,23 @@ __device__ __forceinline__ void decide(TcSmem<KMAX> &sm, int tid, int k, float d
 }
 
 // Write the A row of subspace r (mask bits, then minus the filter threshold).
+template <bool BF16>
 __device__ __forceinline__ void write_a_row(unsigned char *A, int r, uint32_t mask, unsigned short thr)
 {
+    constexpr uint32_t one = Op16<BF16>::kOne;
     uint32_t w[8];
 #pragma unroll
     for (int p = 0; p < 8; ++p) {
         const int f0 = 2 * p, f1 = 2 * p + 1;
-        const uint32_t lo = ((mask >> f0) & 1u) ? 0x3C00u : 0u;  // FP16 1.0 / 0.0
-        const uint32_t hi = f1 == 15 ? (uint32_t)thr : (((mask >> f1) & 1u) ? 0x3C00u : 0u);
+        const uint32_t lo = ((mask >> f0) & 1u) ? one : 0u;  // 1.0 / 0.0
+        const uint32_t hi = f1 == 15 ? (uint32_t)thr : (((mask >> f1) & 1u) ? one : 0u);
         w[p] = lo | (hi << 16);
     }
     *reinterpret_cast<uint4 *>(A + op_off(r, 0)) = make_uint4(w[0], w[1], w[2], w[3]);
     *reinterpret_cast<uint4 *>(A + op_off(r, 8)) = make_uint4(w[4], w[5], w[6], w[7]);
 }
 
-__device__ __forceinline__ uint32_t pack_half2(float a, float b)
-{
-    const __half2 h = __floats2half2_rn(a, b);
-    return *reinterpret_cast<const uint32_t *>(&h);
-}
-
-template <int KMAX>
+template <int KMAX, bool BF16>
 __global__ void __launch_bounds__(kCtaThreads, 1)
     join_tc_kernel(JoinShape s, const TcBlock *__restrict__ blocks, int n_blocks, JoinOut o,
                    DeviceControl *ctrl)
@@ -323,8 +354,7 @@ __global__ void __launch_bounds__(kCtaThreads, 1)
             };
             for (int st = 0; st < kStages; ++st) issue_next();
             const long long total_sub = (long long)my_items * n_sub;
-            // D = F32, A = B = F16, both K-major; N = 128, M = 128
-            const uint32_t idesc = (1u << 4) | ((uint32_t)(kNC >> 3) << 17) | ((uint32_t)(kM >> 4) << 24);
+            const uint32_t idesc = Op16<BF16>::kIdesc;
             long long g = 0;
             bool ok = true;
             for (; g < total_sub; ++g) {
@@ -444,9 +474,9 @@ __global__ void __launch_bounds__(kCtaThreads, 1)
             // the threshold last written into each A copy
             float t_w0 = act ? fmaxf(km.T, eps_floor(e2)) : -1.f, t_w1 = t_w0;
             {
-                const unsigned short th = __half_as_ushort(neg_filter(t_w0));
-                write_a_row(sm.A[0][half], arow, mask, th);
-                write_a_row(sm.A[1][half], arow, mask, th);
+                const unsigned short th = Op16<BF16>::neg_filter(t_w0);
+                write_a_row<BF16>(sm.A[0][half], arow, mask, th);
+                write_a_row<BF16>(sm.A[1][half], arow, mask, th);
             }
 
             const int t0 = iq / kTile;
@@ -464,17 +494,18 @@ __global__ void __launch_bounds__(kCtaThreads, 1)
                 const bool skip = j >= n || j == iq || (unsigned)(j - w0) < (unsigned)wcount;
                 uint4 wd;
                 if (skip) {
-                    // never passes: every feature 65504, no threshold column
-                    wd = make_uint4(0x7BFF7BFFu, 0x7BFF7BFFu, 0x7BFF7BFFu, bh ? 0x00007BFFu : 0x7BFF7BFFu);
+                    // never passes: every squared difference big, no threshold column
+                    constexpr uint32_t big = Op16<BF16>::kBig, big2 = big | (big << 16);
+                    wd = make_uint4(big2, big2, big2, bh ? big : big2);
                 } else {
                     const float4 c0 = sm.ring[slot][(2 * bh) * kTile + rr];
                     const float4 c1 = sm.ring[slot][(2 * bh + 1) * kTile + rr];
                     const float d0 = c0.x - bx0.x, d1 = c0.y - bx0.y, d2 = c0.z - bx0.z, d3 = c0.w - bx0.w;
                     const float d4 = c1.x - bx1.x, d5 = c1.y - bx1.y, d6 = c1.z - bx1.z, d7 = c1.w - bx1.w;
-                    wd.x = pack_half2(d0 * d0, d1 * d1);
-                    wd.y = pack_half2(d2 * d2, d3 * d3);
-                    wd.z = pack_half2(d4 * d4, d5 * d5);
-                    wd.w = pack_half2(d6 * d6, bh ? 1.f : d7 * d7);
+                    wd.x = Op16<BF16>::pack2(d0 * d0, d1 * d1);
+                    wd.y = Op16<BF16>::pack2(d2 * d2, d3 * d3);
+                    wd.z = Op16<BF16>::pack2(d4 * d4, d5 * d5);
+                    wd.w = Op16<BF16>::pack2(d6 * d6, bh ? 1.f : d7 * d7);
                 }
                 *reinterpret_cast<uint4 *>(&sm.B[u & 1][op_off(br, 8 * bh)]) = wd;
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -534,7 +565,8 @@ __global__ void __launch_bounds__(kCtaThreads, 1)
                     float &tw = b ? t_w1 : t_w0;
                     if (tn != tw) {
                         tw = tn;
-                        *reinterpret_cast<__half *>(&sm.A[b][half][op_off(arow, 15)]) = neg_filter(tn);
+                        *reinterpret_cast<unsigned short *>(&sm.A[b][half][op_off(arow, 15)]) =
+                            Op16<BF16>::neg_filter(tn);
                     }
                 }
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -590,12 +622,12 @@ __global__ void __launch_bounds__(kCtaThreads, 1)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols));
 }
 
-template <int KMAX>
+template <int KMAX, bool BF16>
 snaps_status launch_tc(const JoinShape &s, const TcBlock *blocks, int n_blocks, const JoinOut &o,
                        DeviceControl *ctrl, cudaStream_t st)
 {
     const size_t smem = sizeof(TcSmem<KMAX>) + 1024;  // slack for the 1024-byte alignment
-    auto kern = join_tc_kernel<KMAX>;
+    auto kern = join_tc_kernel<KMAX, BF16>;
     SNAPS_CHECK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int dev = 0, sms = 0;
     SNAPS_CHECK_CUDA(cudaGetDevice(&dev));
@@ -610,12 +642,16 @@ snaps_status launch_tc(const JoinShape &s, const TcBlock *blocks, int n_blocks, 
 
 }  // namespace
 
-snaps_status launch_join_tc(const JoinShape &s, const TcBlock *blocks, int n_blocks,
+snaps_status launch_join_tc(const JoinShape &s, const TcBlock *blocks, int n_blocks, bool bf16,
                             const JoinOut &o, DeviceControl *ctrl, cudaStream_t st)
 {
     if (n_blocks <= 0) return SNAPS_OK;
-    if (s.k <= 16) return launch_tc<16>(s, blocks, n_blocks, o, ctrl, st);
-    return launch_tc<32>(s, blocks, n_blocks, o, ctrl, st);
+    if (bf16) {
+        if (s.k <= 16) return launch_tc<16, true>(s, blocks, n_blocks, o, ctrl, st);
+        return launch_tc<32, true>(s, blocks, n_blocks, o, ctrl, st);
+    }
+    if (s.k <= 16) return launch_tc<16, false>(s, blocks, n_blocks, o, ctrl, st);
+    return launch_tc<32, false>(s, blocks, n_blocks, o, ctrl, st);
 }
 
 }  // namespace snaps

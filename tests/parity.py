@@ -89,8 +89,9 @@ def check_top(gpu_top, ora_scores, ora_top, metric):
     if metric == oracle.EPS_MEAN:
         key = np.where(s[oracle.EPS_COUNT] == 0, -np.inf, key)
     gk, ok = key[gpu_top], key[ora_top]
-    tol = SCORE_RTOL * np.maximum(np.abs(gk), np.abs(ok)) + 1e-12
     finite = np.isfinite(gk) & np.isfinite(ok)
-    assert np.all(np.where(finite, np.abs(gk - ok) <= tol, gk == ok)), \
+    tol = SCORE_RTOL * np.maximum(np.abs(gk), np.abs(ok)) + 1e-12
+    diff = np.abs(np.where(finite, gk, 0.0) - np.where(finite, ok, 0.0))
+    assert np.all(np.where(finite, diff <= tol, gk == ok)), \
         "top-list keys differ beyond the tolerance"
     return int((gpu_top != ora_top).sum())

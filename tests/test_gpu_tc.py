@@ -1,8 +1,8 @@
-"""The tensor-core filtered join (SNAPS_TC_F16) returns exactly the plain FP32
-path's results -- same canonical distances, exact decisions on every
-survivor of the FP16 filter -- across block fills, subspace mixes, k, ragged
-N and extreme radii (every candidate passing stresses the event buffers),
-and matches the FP64 oracle under the same rules."""
+"""The tensor-core filtered joins (SNAPS_TC_F16, SNAPS_TC_BF16) return exactly
+the plain FP32 path's results -- same canonical distances, exact decisions on
+every survivor of the FP16 or BF16 filter -- across block fills, subspace
+mixes, k, ragged N and extreme radii (every candidate passing stresses the
+event buffers), and match the FP64 oracle under the same rules."""
 import numpy as np
 import pytest
 
@@ -29,7 +29,7 @@ def run_both(ctx, x, masks, k, eps=None, top_n=100):
         n = x.shape[0]
         top_n = min(top_n, n)
         out = {}
-        for prec in (snaps.SNAPS_FP32, snaps.SNAPS_TC_F16):
+        for prec in (snaps.SNAPS_FP32, snaps.SNAPS_TC_F16, snaps.SNAPS_TC_BF16):
             sc = np.zeros((masks.size, 4, n), dtype=np.float32)
             nz = np.zeros_like(sc)
             tp = np.zeros((masks.size, 4, top_n), dtype=np.int32)
@@ -42,9 +42,10 @@ def run_both(ctx, x, masks, k, eps=None, top_n=100):
 
 
 def assert_same(out):
-    a, b = out[snaps.SNAPS_FP32], out[snaps.SNAPS_TC_F16]
-    for u, v, name in zip(a, b, ("scores", "norm", "top")):
-        np.testing.assert_array_equal(v, u, err_msg=name)
+    a = out[snaps.SNAPS_FP32]
+    for form in (snaps.SNAPS_TC_F16, snaps.SNAPS_TC_BF16):
+        for u, v, name in zip(a, out[form], ("scores", "norm", "top")):
+            np.testing.assert_array_equal(v, u, err_msg=f"{name}, form {form}")
 
 
 @pytest.mark.parametrize("n,seed", [(2000, 0), (257, 1), (513, 2), (1100, 3)])
@@ -71,7 +72,9 @@ def test_tc_extreme_radii_and_large_k(ctx):
     assert_same(run_both(ctx, x, masks, 10, eps=[0.0, 1e-9, 0.0, 1e-9, 0.0]))
 
 
-def test_tc_matches_oracle(ctx):
+@pytest.mark.parametrize("form", ["f16", "bf16"])
+def test_tc_matches_oracle(ctx, form):
+    prec = snaps.SNAPS_TC_F16 if form == "f16" else snaps.SNAPS_TC_BF16
     x = snaps_inputs.population(1500, 41)
     masks = snaps_inputs.mask_sample(12, 41)
     pop = snaps.snaps_index(ctx, x)
@@ -81,7 +84,7 @@ def test_tc_matches_oracle(ctx):
         dist = torch.empty((m, n, 10), device="cuda")
         sc = np.zeros((m, 4, n), dtype=np.float32)
         tp = np.zeros((m, 4, 100), dtype=np.int32)
-        snaps.snaps_scores(pop, masks, 10, precision=snaps.SNAPS_TC_F16, scores=sc, top=tp, top_n=100)
+        snaps.snaps_scores(pop, masks, 10, precision=prec, scores=sc, top=tp, top_n=100)
         snaps.snaps_knn_selfjoin(pop, masks, 10, idx, dist)
         torch.cuda.synchronize()
     finally:
@@ -105,9 +108,10 @@ def test_tc_rejects_wide_features(ctx):
     x = (snaps_inputs.population(300, 3) * 10).astype(np.float32)
     pop = snaps.snaps_index(ctx, x, flags=0)
     try:
-        with pytest.raises(snaps.SnapsError) as ei:
-            snaps.snaps_scores(pop, [0b11], 5, precision=snaps.SNAPS_TC_F16,
-                               scores=np.zeros((1, 4, 300), np.float32))
-        assert ei.value.status == snaps.SNAPS_EINVAL
+        for prec in (snaps.SNAPS_TC_F16, snaps.SNAPS_TC_BF16, 3):
+            with pytest.raises(snaps.SnapsError) as ei:
+                snaps.snaps_scores(pop, [0b11], 5, precision=prec,
+                                   scores=np.zeros((1, 4, 300), np.float32))
+            assert ei.value.status == snaps.SNAPS_EINVAL
     finally:
         snaps.snaps_release(pop)
