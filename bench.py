@@ -41,6 +41,7 @@ K_DEFAULT = 10
 L2_FLUSH_BYTES = 512 << 20   # > 126 MB L2
 SAMPLE_SEED = 1              # the 64-subspace oracle sample of the batching workload
 COMPARES_PER_SM_CLK = 64     # FP32 compare throughput per SM per clock
+MUFU_PER_SM_CLK = 16         # special-function (square root) throughput per SM per clock
 # DRAM bytes (read + write) per pair-subspace evaluation, from one ncu capture
 # of each kernel (dram__bytes_read.sum + dram__bytes_write.sum): the tree join
 # on one 32-subspace chunk at N = 31,693 (7.83 MB + 3.97 MB), the tensor-core
@@ -572,6 +573,22 @@ def run_rubin(args):
     ms = ev0.elapsed_time(ev1)
     tr = snaps.snaps_trace_read(ctx)
     held, budget = snaps.snaps_mem_info(ctx)
+    # every ordered eps-neighbour pair needs one square root for the mean distance
+    nbr_pairs = float(sc[:, 0].double().sum().item())
+    props = torch.cuda.get_device_properties(0)
+    clocks = clk.summary()
+    mhz = clocks["sm_max_mhz"] or 2032.0
+    grid_ms = tr["grid"][0]
+    mufu_peak = props.multi_processor_count * MUFU_PER_SM_CLK * mhz * 1e6 / 1e12
+    achieved = nbr_pairs / (grid_ms / 1e3) / 1e12 if grid_ms > 0 else None
+    roofline = {"bound": "alu", "kernel": "grid phase (index build, grid_tile_kernel, grid_ring_kernel)",
+                "achieved": achieved, "peak": mufu_peak, "unit": "T sqrt/s",
+                "frac": achieved / mufu_peak if achieved else None, "traffic": None,
+                "peak_basis": f"{props.multi_processor_count} SMs x {MUFU_PER_SM_CLK} MUFU ops/clk x "
+                              f"{mhz:.0f} MHz: one square root per ordered eps-neighbour pair "
+                              f"({nbr_pairs:.3e} in this call), the algorithmic minimum of the mean "
+                              f"eps distance",
+                "eps_neighbour_pairs": nbr_pairs}
     out_bytes = sc.numel() * 4 + top.numel() * 4
     snaps.snaps_release(pop)
     snaps.snaps_destroy(ctx)
@@ -583,7 +600,8 @@ def run_rubin(args):
             "phase_ms": {k: v[0] for k, v in tr.items() if v[1]},
             "index_s": index_s,
             "hbm_bytes": {"library_held": held, "caller_outputs": out_bytes, "total": held + out_bytes},
-            "clocks": clk.summary(), "dtype": "f32", "data": "synthetic",
+            "roofline": roofline,
+            "clocks": clocks, "dtype": "f32", "data": "synthetic",
             "config": {"workload": f"N={n} objects (seed 0), {masks.size} of the 105 two-feature subspaces "
                                    f"(evenly spaced), k={args.k}, eps=0.05*sqrt(2); grid index over both "
                                    f"features, cells {'eps/3 (the library default)' if not args.rubin_cells else f'eps/{args.rubin_cells}'} "

@@ -228,15 +228,13 @@ __device__ __forceinline__ void scan_cells(const GridSpec &g, const V *pts, cons
     scan_range(pts, orig, start[la], start[la + (b - a) + 1], st, do_eps);
 }
 
+// One warp joins the query at sorted position p: the block, then rings.
 template <typename V>
-__global__ void __launch_bounds__(kGridWarps * 32, 2)
-    grid_join_kernel(const V *__restrict__ pts, const int32_t *__restrict__ orig,
-                     const int32_t *__restrict__ start, int n, GridSpec g, int k, JoinOut o)
+__device__ __forceinline__ void warp_query(const V *__restrict__ pts, const int32_t *__restrict__ orig,
+                                           const int32_t *__restrict__ start, int n, const GridSpec &g, int k,
+                                           const JoinOut &o, int p)
 {
-    const int warp = threadIdx.x >> 5;
     const unsigned lane = dev::lane_id();
-    const int p = blockIdx.x * kGridWarps + warp;
-    if (p >= n) return;
     QueryState<V> st;
     st.q = pts[p];
     st.qrow = p;
@@ -336,6 +334,217 @@ __global__ void __launch_bounds__(kGridWarps * 32, 2)
     }
 }
 
+// Queries whose kNN list the cell-tile join could not certify (listed in
+// `ring`, *ring_n of them): a warp per query, grid-stride.
+template <typename V>
+__global__ void __launch_bounds__(kGridWarps * 32, 2)
+    grid_ring_kernel(const V *__restrict__ pts, const int32_t *__restrict__ orig,
+                     const int32_t *__restrict__ start, int n, GridSpec g, int k, JoinOut o,
+                     const int32_t *__restrict__ ring, const int32_t *__restrict__ ring_n)
+{
+    const int warp = threadIdx.x >> 5;
+    const int m = *ring_n;
+    for (int i = blockIdx.x * kGridWarps + warp; i < m; i += gridDim.x * kGridWarps) {
+        const int p = ring[i];
+        if (p >= 0 && p < n) warp_query(pts, orig, start, n, g, k, o, p);
+    }
+}
+
+// ---- cell-tile join ------------------------------------------------------------------------------
+//
+// A CTA owns kTileQ consecutive sorted positions, one query per thread.  It
+// splits them into segments that share the leading cell coordinates (one
+// row of cells along the fastest dimension); the queries of a segment lie in
+// cells cl_lo..cl_hi of that row, so the union of their (2R + 1)^D blocks is
+// the (2R + 1)^(D - 1) neighbouring rows, each restricted to cells
+// cl_lo - R .. cl_hi + R: one contiguous range of sorted positions per row.
+// Those candidates are staged in shared memory kTileC at a time and every
+// thread tests all of them against its query, so a candidate is read from
+// global memory once per segment instead of once per query.  Candidates
+// outside a query's own block are tested too; they only make its kNN list
+// tighter sooner, and every decision is the exact canonical distance.
+//
+// Each thread keeps its eps count, exact quantised sum and an unsorted kNN
+// list (largest entry tracked) privately.  A query whose k-th distance is not
+// below R w afterwards (the reach beyond which the rings begin) may have
+// nearer objects outside the scanned block; it is appended to the ring list
+// and joined afresh by grid_ring_kernel, and this kernel writes nothing for it.
+constexpr int kTileQ = 256;   // queries per CTA
+constexpr int kTileC = 1024;  // candidates staged per round
+
+template <typename V, int KMAX>
+struct TileSmem {
+    static constexpr int NF = sizeof(V) / sizeof(float);  // 2 or 4 stored features
+    float cand[NF][kTileC + 2];  // feature-planar, so that a float2 read holds two candidates
+    float ld[KMAX][kTileQ];      // kNN lists, entry-major: thread t owns column t
+    int lj[KMAX][kTileQ];
+};
+
+__device__ __forceinline__ float comp(const float2 &v, int f) { return f == 0 ? v.x : v.y; }
+__device__ __forceinline__ float comp(const float4 &v, int f)
+{
+    return f == 0 ? v.x : (f == 1 ? v.y : (f == 2 ? v.z : v.w));
+}
+
+__device__ __forceinline__ int fastest_cell(const GridSpec &g, const int (&c)[3]) { return g.D == 2 ? c[1] : c[2]; }
+
+template <typename V, int KMAX>
+__global__ void __launch_bounds__(kTileQ, 2)
+    grid_tile_kernel(const V *__restrict__ pts, const int32_t *__restrict__ orig,
+                     const int32_t *__restrict__ start, int n, GridSpec g, int k, JoinOut o,
+                     int32_t *__restrict__ ring, int32_t *__restrict__ ring_n)
+{
+    extern __shared__ __align__(16) unsigned char tile_smem[];
+    TileSmem<V, KMAX> &sm = *reinterpret_cast<TileSmem<V, KMAX> *>(tile_smem);
+    constexpr int NF = TileSmem<V, KMAX>::NF;
+    const int t = threadIdx.x;
+    const int p0 = blockIdx.x * kTileQ;
+    const int p1 = min(p0 + kTileQ, n);
+    const int D = g.D, R = g.R;
+    const int nl = D == 2 ? g.nc[1] : g.nc[2];  // cells along the fastest dimension
+    const bool do_eps = g.eps2 >= 0.f;
+    const float e2 = g.eps2;
+    const float esc = dev::eps_scale(g.eps2).scale;
+    // objects outside a query's (2R + 1)^D block are at least this far away
+    const float reach = (float)R * g.w * (1.f - 1.f / 1024.f);
+    const float reach2 = reach * reach;
+    float *sc = o.scores + (int64_t)g.slot * 4 * n;
+
+    int pos = p0;
+    while (pos < p1) {  // every thread computes the same segments
+        int c[3];
+        point_cell(g, pts[pos], c);
+        const int row0 = D == 2 ? c[0] * g.nc[1] : (c[0] * g.nc[1] + c[1]) * g.nc[2];
+        const int se = min(p1, (int)start[row0 + nl]);  // > pos: pos lies in this row
+        int ce[3];
+        point_cell(g, pts[se - 1], ce);
+        const int a = max(fastest_cell(g, c) - R, 0);
+        const int b = min(fastest_cell(g, ce) + R, nl - 1);
+
+        const int q = pos + t;
+        const bool act = q < se;
+        const V qv = act ? pts[q] : V{};
+        float2 nq[NF];
+#pragma unroll
+        for (int f = 0; f < NF; ++f) nq[f] = make_float2(-comp(qv, f), -comp(qv, f));
+#pragma unroll 1
+        for (int e = 0; e < KMAX; ++e) {
+            sm.ld[e][t] = CUDART_INF_F;
+            sm.lj[e][t] = 0x7fffffff;
+        }
+        float T = (act && k > 0) ? CUDART_INF_F : -CUDART_INF_F;  // largest list entry
+        int Tj = 0x7fffffff, Tp = 0;
+        unsigned cnt = 0;
+        unsigned long long qs = 0ull;
+
+        const int i0lo = max(c[0] - R, 0), i0hi = min(c[0] + R, g.nc[0] - 1);
+        const int i1lo = D == 3 ? max(c[1] - R, 0) : 0, i1hi = D == 3 ? min(c[1] + R, g.nc[1] - 1) : 0;
+#pragma unroll 1
+        for (int i0 = i0lo; i0 <= i0hi; ++i0) {
+#pragma unroll 1
+            for (int i1 = i1lo; i1 <= i1hi; ++i1) {
+                const int lead = D == 2 ? i0 : i0 * g.nc[1] + i1;
+                const int beg = start[lead * nl + a], end = start[lead * nl + b + 1];
+#pragma unroll 1
+                for (int c0 = beg; c0 < end; c0 += kTileC) {
+                    const int cn = min(kTileC, end - c0);
+                    __syncthreads();  // the previous round's candidates are no longer read
+                    for (int u = t; u < cn; u += kTileQ) {
+                        const V pv = pts[c0 + u];
+#pragma unroll
+                        for (int f = 0; f < NF; ++f) sm.cand[f][u] = comp(pv, f);
+                    }
+                    if (t < NF) sm.cand[t][cn] = 1e18f;  // the partner of an odd last candidate: never
+                                                         // an eps-neighbour, and no kNN entry (cp < cend)
+                    __syncthreads();
+                    if (!act) continue;
+                    const int cend = c0 + cn;
+#pragma unroll 2
+                    for (int u = 0; u < cn; u += 2) {
+                        // the canonical fold of two candidates at once, highest feature first
+                        float2 dd = __fadd2_rn(*reinterpret_cast<const float2 *>(&sm.cand[0][u]), nq[0]);
+                        float2 acc = __fmul2_rn(dd, dd);
+#pragma unroll
+                        for (int f = 1; f < NF; ++f) {
+                            dd = __fadd2_rn(*reinterpret_cast<const float2 *>(&sm.cand[f][u]), nq[f]);
+                            acc = __ffma2_rn(dd, dd, acc);
+                        }
+#pragma unroll
+                        for (int h = 0; h < 2; ++h) {
+                        const float d2 = h ? acc.y : acc.x;
+                        const int cp = c0 + u + h;
+                        // the query itself (d2 = 0) is counted here and taken off at the end
+                        if (d2 <= e2) {
+                            ++cnt;
+                            qs += dev::eps_quant(d2, esc);
+                        }
+                        if (d2 <= T && cp != q && cp < cend) {
+                            const int oj = orig[cp];
+                            if (d2 < T || oj < Tj) {
+                                sm.ld[Tp][t] = d2;
+                                sm.lj[Tp][t] = oj;
+                                float mx = sm.ld[0][t];
+                                int mj = sm.lj[0][t], mp = 0;
+                                for (int e = 1; e < k; ++e) {
+                                    const float v = sm.ld[e][t];
+                                    const int j = sm.lj[e][t];
+                                    const bool gt = v > mx || (v == mx && j > mj);
+                                    mx = gt ? v : mx;
+                                    mj = gt ? j : mj;
+                                    mp = gt ? e : mp;
+                                }
+                                T = mx;
+                                Tj = mj;
+                                Tp = mp;
+                            }
+                        }
+                        }
+                    }
+                }
+            }
+        }
+        if (act && do_eps) --cnt;  // the query, at distance 0, is in its own block
+
+        if (act) {
+            if (k > 0 && !(reach2 > T)) {
+                // nearer objects may lie beyond the block: the ring search decides
+                ring[atomicAdd(ring_n, 1)] = q;
+            } else {
+                const int oi = orig[q];
+                sc[oi] = do_eps ? (float)cnt : 0.f;
+                sc[n + oi] = do_eps ? dev::eps_mean(qs, (int)cnt, esc) : 0.f;
+                if (o.eps_count) o.eps_count[(int64_t)g.slot * n + oi] = do_eps ? (int)cnt : 0;
+                if (k > 0) {
+                    // sort the list by (distance, index), then the mean in that order
+                    for (int e = 1; e < k; ++e) {
+                        const float v = sm.ld[e][t];
+                        const int j = sm.lj[e][t];
+                        int r = e;
+                        while (r > 0 && (sm.ld[r - 1][t] > v || (sm.ld[r - 1][t] == v && sm.lj[r - 1][t] > j))) {
+                            sm.ld[r][t] = sm.ld[r - 1][t];
+                            sm.lj[r][t] = sm.lj[r - 1][t];
+                            --r;
+                        }
+                        sm.ld[r][t] = v;
+                        sm.lj[r][t] = j;
+                    }
+                    float msum = 0.f;
+                    for (int e = 0; e < k; ++e) {
+                        const float dd = sqrtf(sm.ld[e][t]);
+                        const int j = sm.lj[e][t];
+                        msum += dd;
+                        if (j >= 0 && j < n) atomicAdd(&sc[2 * n + j], 1.f);
+                        if (o.knn_idx) o.knn_idx[((int64_t)g.slot * n + oi) * k + e] = j;
+                        if (o.knn_dist) o.knn_dist[((int64_t)g.slot * n + oi) * k + e] = dd;
+                    }
+                    sc[3 * n + oi] = msum / (float)k;
+                }
+            }
+        }
+        pos = se;
+    }
+}
+
 }  // namespace
 
 namespace {
@@ -352,7 +561,7 @@ size_t sort_temp_bytes(int64_t n)
 size_t grid_scratch_bytes(int64_t n, int max_cells)
 {
     return 4 * al256(n * 4) + al256(n * 16) + al256(n * 4) + al256((size_t)(max_cells + 1) * 4) +
-           al256(sort_temp_bytes(n));
+           al256(sort_temp_bytes(n)) + al256(n * 4) + al256(4);
 }
 
 GridBufs grid_carve(void *base, int64_t n, int max_cells)
@@ -374,8 +583,33 @@ GridBufs grid_carve(void *base, int64_t n, int max_cells)
     b.start = (int32_t *)take((size_t)(max_cells + 1) * 4);
     b.tmp_bytes = sort_temp_bytes(n);
     b.tmp = take(b.tmp_bytes);
+    b.ring = (int32_t *)take(n * 4);
+    b.ring_n = (int32_t *)take(4);
     return b;
 }
+
+namespace {
+// The cell-tile join over all queries, then the ring search for the queries
+// it could not certify.
+template <typename V, int KMAX>
+snaps_status launch_tile(const V *pts, const GridBufs &b, int n, const GridSpec &g, int k, const JoinOut &o,
+                         cudaStream_t st)
+{
+    const size_t smem = sizeof(TileSmem<V, KMAX>);
+    auto tk = grid_tile_kernel<V, KMAX>;
+    SNAPS_CHECK_CUDA(cudaFuncSetAttribute(tk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const unsigned tb = (unsigned)((n + kTileQ - 1) / kTileQ);
+    tk<<<tb, kTileQ, smem, st>>>(pts, b.orig, b.start, n, g, k, o, b.ring, b.ring_n);
+    SNAPS_CHECK_CUDA(cudaGetLastError());
+    if (k > 0) {
+        // a warp per listed query; the list length is only known on the device
+        const unsigned rb = (unsigned)std::min<int64_t>(((int64_t)n + kGridWarps - 1) / kGridWarps, 148 * 8);
+        grid_ring_kernel<V><<<rb, kGridWarps * 32, 0, st>>>(pts, b.orig, b.start, n, g, k, o, b.ring, b.ring_n);
+        SNAPS_CHECK_CUDA(cudaGetLastError());
+    }
+    return SNAPS_OK;
+}
+}  // namespace
 
 int grid_key_bits(const GridSpec &g)
 {
@@ -400,14 +634,14 @@ snaps_status run_grid_subspace(const JoinShape &s, const GridSpec &g, const Join
     SNAPS_CHECK_CUDA(cudaGetLastError());
     grid_gather_kernel<<<blocks, threads, 0, st>>>(s.x, b.v_out, n, g, b.pts, b.orig);
     SNAPS_CHECK_CUDA(cudaGetLastError());
-    const unsigned jb = (unsigned)((n + kGridWarps - 1) / kGridWarps);
-    if (g.d <= 2)
-        grid_join_kernel<float2><<<jb, kGridWarps * 32, 0, st>>>(reinterpret_cast<const float2 *>(b.pts), b.orig,
-                                                                  b.start, (int)n, g, s.k, o);
-    else
-        grid_join_kernel<float4><<<jb, kGridWarps * 32, 0, st>>>(b.pts, b.orig, b.start, (int)n, g, s.k, o);
-    SNAPS_CHECK_CUDA(cudaGetLastError());
-    return SNAPS_OK;
+    SNAPS_CHECK_CUDA(cudaMemsetAsync(b.ring_n, 0, sizeof(int32_t), st));
+    if (g.d <= 2) {
+        const float2 *p2 = reinterpret_cast<const float2 *>(b.pts);
+        if (s.k <= 16) return launch_tile<float2, 16>(p2, b, (int)n, g, s.k, o, st);
+        return launch_tile<float2, 32>(p2, b, (int)n, g, s.k, o, st);
+    }
+    if (s.k <= 16) return launch_tile<float4, 16>(b.pts, b, (int)n, g, s.k, o, st);
+    return launch_tile<float4, 32>(b.pts, b, (int)n, g, s.k, o, st);
 }
 
 }  // namespace snaps

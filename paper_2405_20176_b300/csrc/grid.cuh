@@ -41,6 +41,8 @@ struct GridBufs {
     int32_t *start;          // cell starts (ncells + 1)
     void *tmp;               // radix-sort temporary storage
     size_t tmp_bytes;
+    int32_t *ring;           // queries left to the ring search (sorted positions)
+    int32_t *ring_n;         // their number
 };
 
 // Device bytes the index of n objects with up to max_cells cells needs, and
