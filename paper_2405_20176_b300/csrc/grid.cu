@@ -11,20 +11,24 @@
 // sorted position of cell c, so the objects of a run of cells along the
 // fastest dimension are one contiguous range.  The sorted objects are stored
 // as one float4 each (the subspace's features from the highest index down,
-// zero padded) plus their original indices.
+// zero padded; a float2 for subspaces of two features) plus their original
+// indices.
 //
-// Join.  A warp owns one query.  Every eps-neighbour lies in the 3^D block of
-// cells around the query's own (w >= eps, and w carries a 2^-10 margin so
-// that rounding in the cell computation cannot separate two points by more
-// than one cell), so the warp scans those ranges -- lanes striding over the
-// candidates -- counts eps-neighbours with ballot/popc, sums their quantised
-// distances exactly and keeps the kNN list warp-cooperatively.  When the k-th
-// distance still exceeds the cell width afterwards (sparse regions, outliers),
-// rings of cells at Chebyshev distance r = 2, 3, ... are scanned for the kNN
-// list until (r - 1) w exceeds it: no object outside the scanned cells can be
-// nearer (a subspace distance is at least the distance over the index
-// features).  Distances are the library's canonical FP32 fold (FMAs from the
-// highest feature down), so results equal every other path's bit for bit.
+// Join.  Every eps-neighbour of a query lies in the (2R + 1)^D block of
+// cells around its own (R w >= eps, and w carries a 2^-10 margin so that
+// rounding in the cell computation cannot separate two points by more than R
+// cells).  grid_tile_kernel gives a CTA 256 consecutive queries in cell order
+// and, per row segment of them, stages the union of their blocks in shared
+// memory once; every thread tests all of it against its query, counts
+// eps-neighbours, sums their quantised distances exactly and keeps a private
+// kNN list.  When a query's k-th distance is not below R w afterwards
+// (sparse regions, outliers), grid_ring_kernel joins it again, a warp per
+// query, scanning rings of cells at Chebyshev distance r = R + 1, R + 2, ...
+// until (r - 1) w exceeds the k-th distance: no object outside the scanned
+// cells can be nearer (a subspace distance is at least the distance over the
+// index features).  Distances are the library's canonical FP32 fold (FMAs
+// from the highest feature down), so results equal every other path's bit for
+// bit.
 
 #include <cub/cub.cuh>
 #include <math_constants.h>
@@ -375,7 +379,8 @@ constexpr int kTileC = 1024;  // candidates staged per round
 template <typename V, int KMAX>
 struct TileSmem {
     static constexpr int NF = sizeof(V) / sizeof(float);  // 2 or 4 stored features
-    float cand[NF][kTileC + 2];  // feature-planar, so that a float2 read holds two candidates
+    float cand[NF][kTileC + 4];  // feature-planar, so that a float4 read holds four candidates
+    int corig[kTileC];           // their original indices
     float ld[KMAX][kTileQ];      // kNN lists, entry-major: thread t owns column t
     int lj[KMAX][kTileQ];
 };
@@ -386,10 +391,21 @@ __device__ __forceinline__ float comp(const float4 &v, int f)
     return f == 0 ? v.x : (f == 1 ? v.y : (f == 2 ? v.z : v.w));
 }
 
+// dev::eps_quant's value, for the eps-neighbours of a subspace whose scale
+// maps eps to 2^20, without the conversion unit: the product p < 2^22 is
+// rounded as dev::eps_quant rounds it, and adding 1.5 * 2^23 (an even
+// integer, in a binade where floats are the integers) rounds p to the
+// nearest integer, ties to even, exactly as __float2uint_rn does.
+__device__ __forceinline__ unsigned quant_rn(float d2, float scale)
+{
+    const float p = __fmul_rn(dev::eps_sqrt(d2), scale);
+    return __float_as_uint(__fadd_rn(p, 12582912.f)) - 0x4B400000u;
+}
+
 __device__ __forceinline__ int fastest_cell(const GridSpec &g, const int (&c)[3]) { return g.D == 2 ? c[1] : c[2]; }
 
 template <typename V, int KMAX>
-__global__ void __launch_bounds__(kTileQ, 2)
+__global__ void __launch_bounds__(kTileQ, 4)
     grid_tile_kernel(const V *__restrict__ pts, const int32_t *__restrict__ orig,
                      const int32_t *__restrict__ start, int n, GridSpec g, int k, JoinOut o,
                      int32_t *__restrict__ ring, int32_t *__restrict__ ring_n)
@@ -437,14 +453,8 @@ __global__ void __launch_bounds__(kTileQ, 2)
         unsigned cnt = 0;
         unsigned long long qs = 0ull;
 
-        const int i0lo = max(c[0] - R, 0), i0hi = min(c[0] + R, g.nc[0] - 1);
-        const int i1lo = D == 3 ? max(c[1] - R, 0) : 0, i1hi = D == 3 ? min(c[1] + R, g.nc[1] - 1) : 0;
-#pragma unroll 1
-        for (int i0 = i0lo; i0 <= i0hi; ++i0) {
-#pragma unroll 1
-            for (int i1 = i1lo; i1 <= i1hi; ++i1) {
-                const int lead = D == 2 ? i0 : i0 * g.nc[1] + i1;
-                const int beg = start[lead * nl + a], end = start[lead * nl + b + 1];
+        // stage and test the candidates at sorted positions [beg, end)
+        auto scan = [&](int beg, int end) {
 #pragma unroll 1
                 for (int c0 = beg; c0 < end; c0 += kTileC) {
                     const int cn = min(kTileC, end - c0);
@@ -453,54 +463,94 @@ __global__ void __launch_bounds__(kTileQ, 2)
                         const V pv = pts[c0 + u];
 #pragma unroll
                         for (int f = 0; f < NF; ++f) sm.cand[f][u] = comp(pv, f);
+                        sm.corig[u] = orig[c0 + u];
                     }
-                    if (t < NF) sm.cand[t][cn] = 1e18f;  // the partner of an odd last candidate: never
-                                                         // an eps-neighbour, and no kNN entry (cp < cend)
+                    // partners of the last candidates up to a multiple of four: never an
+                    // eps-neighbour, and no kNN entry (cp < cend)
+                    if (t < 4 * NF) sm.cand[t >> 2][cn + (t & 3)] = 1e18f;
                     __syncthreads();
                     if (!act) continue;
                     const int cend = c0 + cn;
+                    unsigned qr = 0u;  // this round's quantised sum: <= kTileC terms of <= 2^20 + 1
 #pragma unroll 2
-                    for (int u = 0; u < cn; u += 2) {
-                        // the canonical fold of two candidates at once, highest feature first
-                        float2 dd = __fadd2_rn(*reinterpret_cast<const float2 *>(&sm.cand[0][u]), nq[0]);
-                        float2 acc = __fmul2_rn(dd, dd);
+                    for (int u = 0; u < cn; u += 4) {
+                        // the canonical fold of four candidates, two per f32x2 instruction,
+                        // highest feature first
+                        float2 acc[2];
 #pragma unroll
-                        for (int f = 1; f < NF; ++f) {
-                            dd = __fadd2_rn(*reinterpret_cast<const float2 *>(&sm.cand[f][u]), nq[f]);
-                            acc = __ffma2_rn(dd, dd, acc);
+                        for (int f = 0; f < NF; ++f) {
+                            const float4 v = *reinterpret_cast<const float4 *>(&sm.cand[f][u]);
+                            const float2 d0 = __fadd2_rn(make_float2(v.x, v.y), nq[f]);
+                            const float2 d1 = __fadd2_rn(make_float2(v.z, v.w), nq[f]);
+                            acc[0] = f == 0 ? __fmul2_rn(d0, d0) : __ffma2_rn(d0, d0, acc[0]);
+                            acc[1] = f == 0 ? __fmul2_rn(d1, d1) : __ffma2_rn(d1, d1, acc[1]);
                         }
+                        // eps: branch-free (the query itself, at d2 = 0, is counted here and
+                        // taken off at the end)
 #pragma unroll
-                        for (int h = 0; h < 2; ++h) {
-                        const float d2 = h ? acc.y : acc.x;
-                        const int cp = c0 + u + h;
-                        // the query itself (d2 = 0) is counted here and taken off at the end
-                        if (d2 <= e2) {
-                            ++cnt;
-                            qs += dev::eps_quant(d2, esc);
+                        for (int h = 0; h < 4; ++h) {
+                            const float d2 = (h & 1) ? acc[h >> 1].y : acc[h >> 1].x;
+                            const bool in = d2 <= e2;
+                            const unsigned qv = quant_rn(fminf(d2, e2), esc);
+                            cnt += in ? 1u : 0u;
+                            qr += in ? qv : 0u;
                         }
-                        if (d2 <= T && cp != q && cp < cend) {
-                            const int oj = orig[cp];
-                            if (d2 < T || oj < Tj) {
-                                sm.ld[Tp][t] = d2;
-                                sm.lj[Tp][t] = oj;
-                                float mx = sm.ld[0][t];
-                                int mj = sm.lj[0][t], mp = 0;
-                                for (int e = 1; e < k; ++e) {
-                                    const float v = sm.ld[e][t];
-                                    const int j = sm.lj[e][t];
-                                    const bool gt = v > mx || (v == mx && j > mj);
-                                    mx = gt ? v : mx;
-                                    mj = gt ? j : mj;
-                                    mp = gt ? e : mp;
+                        // kNN: one test for the four, then each
+                        if (fminf(fminf(acc[0].x, acc[0].y), fminf(acc[1].x, acc[1].y)) <= T) {
+#pragma unroll
+                        for (int h = 0; h < 4; ++h) {
+                            const float d2 = (h & 1) ? acc[h >> 1].y : acc[h >> 1].x;
+                            if (d2 <= T) {
+                                const int cp = c0 + u + h;
+                                if (cp != q && cp < cend) {
+                                    const int oj = sm.corig[u + h];
+                                    if (d2 < T || oj < Tj) {
+                                        sm.ld[Tp][t] = d2;
+                                        sm.lj[Tp][t] = oj;
+                                        float mx = sm.ld[0][t];
+                                        int mj = sm.lj[0][t], mp = 0;
+                                        for (int e = 1; e < k; ++e) {
+                                            const float v = sm.ld[e][t];
+                                            const int j = sm.lj[e][t];
+                                            const bool gt = v > mx || (v == mx && j > mj);
+                                            mx = gt ? v : mx;
+                                            mj = gt ? j : mj;
+                                            mp = gt ? e : mp;
+                                        }
+                                        T = mx;
+                                        Tj = mj;
+                                        Tp = mp;
+                                    }
                                 }
-                                T = mx;
-                                Tj = mj;
-                                Tp = mp;
                             }
                         }
                         }
                     }
+                    qs += qr;
                 }
+        };
+        // the segment's own cells first and then the rows outwards, so that the
+        // kNN thresholds are tight early and few candidates reach the insertion
+        const int cl_lo = fastest_cell(g, c), cl_hi = fastest_cell(g, ce);
+        {
+            const int base = (D == 2 ? c[0] : c[0] * g.nc[1] + c[1]) * nl;
+            const int m0 = start[base + cl_lo], m1 = start[base + cl_hi + 1];
+            scan(m0, m1);
+            scan(start[base + a], m0);
+            scan(m1, start[base + b + 1]);
+        }
+        const int r1max = D == 3 ? 2 * R : 0;
+#pragma unroll 1
+        for (int r0 = 0; r0 <= 2 * R; ++r0) {
+            const int i0 = c[0] + ((r0 & 1) ? -((r0 + 1) >> 1) : (r0 >> 1));  // c0, c0 - 1, c0 + 1, ...
+            if (i0 < 0 || i0 >= g.nc[0]) continue;
+#pragma unroll 1
+            for (int r1 = 0; r1 <= r1max; ++r1) {
+                const int i1 = c[1] + ((r1 & 1) ? -((r1 + 1) >> 1) : (r1 >> 1));
+                if (D == 3 && (i1 < 0 || i1 >= g.nc[1])) continue;
+                if (r0 == 0 && r1 == 0) continue;  // the own row, done above
+                const int lead = D == 2 ? i0 : i0 * g.nc[1] + i1;
+                scan(start[lead * nl + a], start[lead * nl + b + 1]);
             }
         }
         if (act && do_eps) --cnt;  // the query, at distance 0, is in its own block
