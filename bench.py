@@ -182,6 +182,18 @@ class ClockSampler:
 
 # ---- our arm -------------------------------------------------------------------------------
 
+def max_over_ranks(x: float, dist, device) -> float:
+    """The largest of every rank's x: a job's time is its slowest rank's.  With
+    N replicas each rank does the same work, so the job's throughput is N times
+    one rank's units over that time."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def run_ours(args, rank, world, dist):
     import torch
 
@@ -242,11 +254,7 @@ def run_ours(args, rank, world, dist):
         snaps.snaps_trace(ctx, False)
         for p in pops:
             snaps.snaps_release(p)
-        total_ms = sum(a.elapsed_time(b) for a, b in ev)
-        if dist is not None:
-            t = torch.tensor([total_ms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            total_ms = float(t.item())
+        total_ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in ev), dist, dev)
         return total_ms, trace, clk.summary()
 
     total_ms, trace, clocks = timed_leg(head_prec, args.steps, args.warmup)
@@ -336,11 +344,7 @@ def run_ours(args, rank, world, dist):
         for _ in range(args.steps):
             e2e_step()
         barrier()
-        e2e_s = time.perf_counter() - t0
-        if dist is not None:
-            t = torch.tensor([e2e_s], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_s = float(t.item())
+        e2e_s = max_over_ranks(time.perf_counter() - t0, dist, dev)
         e2e = {"value": units / e2e_s, "unit": "objects*subspaces/s",
                "h2d_bytes_per_step": int(x.nbytes), "d2h_bytes_per_step": int(m * 4 * 100 * 4)}
 
