@@ -259,7 +259,8 @@ snaps_status validate(const JobSpec &j)
 }
 
 // Split the requested subspaces between the tree kernel (chunks with >= 2
-// requested subspaces) and the lane-per-subspace kernel (everything else).
+// requested subspaces) and the subspace-at-a-time kernel (everything else,
+// listed in groups of 32).
 struct Plan {
     std::vector<TreeChunk> chunks;
     std::vector<MaskGroup> groups;
@@ -711,7 +712,7 @@ snaps_status run_job(snaps_ctx *ctx, const JobSpec &j, cudaStream_t st, Scratch 
     }
     if (!pl.groups.empty()) {
         TraceScope ts(ctx, SNAPS_PHASE_JOIN_LANE, st);
-        SNAPS_TRY(launch_join_lanemask(shape, L.groups, (int)pl.groups.size(), out, ctrl, st));
+        SNAPS_TRY(launch_join_single(shape, L.groups, (int)pl.groups.size(), out, st));
     }
     if (!pl.blocks.empty()) {
         TraceScope ts(ctx, SNAPS_PHASE_JOIN_TC, st);

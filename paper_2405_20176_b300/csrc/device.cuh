@@ -103,6 +103,17 @@ __device__ __forceinline__ unsigned eps_quant(float d2, float scale) {
     return __float2uint_rn(eps_sqrt(d2) * scale);
 }
 
+// eps_quant's value, for the eps-neighbours of a subspace (scale maps eps to
+// 2^20), without the conversion unit: the product p < 2^22 is rounded as
+// eps_quant rounds it, and adding 1.5 * 2^23 (an even integer, in a binade
+// where floats are the integers) rounds p to the nearest integer, ties to
+// even, exactly as __float2uint_rn does.  The _rn intrinsics are never fused
+// into one FMA, which would round once instead of twice.
+__device__ __forceinline__ unsigned eps_quant_fma_pipe(float d2, float scale) {
+    const float p = __fmul_rn(eps_sqrt(d2), scale);
+    return __float_as_uint(__fadd_rn(p, 12582912.f)) - 0x4B400000u;
+}
+
 // Mean distance from the exact quantised sum.
 __device__ __forceinline__ float eps_mean(unsigned long long qsum, int cnt, float scale) {
     if (cnt <= 0 || scale == 0.f) return 0.f;

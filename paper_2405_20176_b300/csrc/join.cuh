@@ -71,6 +71,11 @@ struct JoinShape {
 snaps_status launch_join_lanemask(const JoinShape &s, const MaskGroup *groups, int n_groups,
                                   const JoinOut &o, DeviceControl *ctrl, cudaStream_t st);
 
+// Launch the subspace-at-a-time join over every used entry of `n_groups`
+// groups (device array): one launch row per entry, a CTA per 256 queries.
+snaps_status launch_join_single(const JoinShape &s, const MaskGroup *groups, int n_groups,
+                                const JoinOut &o, cudaStream_t st);
+
 // Launch the tensor-core filtered join over `n_blocks` blocks (device array).
 // Requires every feature of the population to span at most 1.
 snaps_status launch_join_tc(const JoinShape &s, const TcBlock *blocks, int n_blocks, bool bf16,
