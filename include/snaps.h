@@ -379,7 +379,8 @@ snaps_status snaps_calibrate_alu(int device, double *evals_per_s);
 
 #define SNAPS_PHASE_INDEX 0      /* normalisation kernels of snaps_index */
 #define SNAPS_PHASE_JOIN_TREE 1  /* subspace-batched (tree) join kernel */
-#define SNAPS_PHASE_JOIN_LANE 2  /* lane-per-subspace join kernel */
+#define SNAPS_PHASE_JOIN_LANE 2  /* joins of subspaces alone in their 32-subspace chunk
+                                  * (the subspace-at-a-time kernel) */
 #define SNAPS_PHASE_NORM 3       /* normalised-metric kernel */
 #define SNAPS_PHASE_TOP 4        /* top-n ranking kernel */
 #define SNAPS_PHASE_JOIN_TC 5    /* tensor-core filtered join kernel */
