@@ -93,6 +93,9 @@ const char *snaps_version(void);
  * valid until that thread's next snaps_* call. */
 const char *snaps_last_error(void);
 
+/* ---- contexts and populations: library plumbing (the paper has no
+ * counterpart; it runs one process per subspace, Sec. 3.8) ---- */
+
 /* Create a context on CUDA device `device`.  `hbm_budget_bytes` caps the
  * device memory the context may hold (populations + scratch + in-flight
  * requests); 0 means 90 % of the device's free memory at creation.
@@ -100,10 +103,12 @@ const char *snaps_last_error(void);
 snaps_status snaps_create(int device, size_t hbm_budget_bytes, snaps_ctx **out);
 
 /* Finish all queued requests, free everything the context owns.  Populations
- * not yet released are released.  NULL is a no-op. */
+ * not yet released are released.  NULL is a no-op.  Errors: none (returns
+ * SNAPS_OK). */
 snaps_status snaps_destroy(snaps_ctx *ctx);
 
-/* Device memory currently held and the budget, in bytes. */
+/* Device memory currently held and the budget, in bytes (either output may
+ * be NULL).  Errors: EINVAL (ctx NULL). */
 snaps_status snaps_mem_info(const snaps_ctx *ctx, size_t *held, size_t *budget);
 
 /* Index a population: the data set D of Sec. 3.1.
@@ -125,14 +130,18 @@ snaps_status snaps_mem_info(const snaps_ctx *ctx, size_t *held, size_t *budget);
 snaps_status snaps_index(snaps_ctx *ctx, const float *feat, int64_t n, int f,
                          uint32_t flags, void *stream, snaps_pop **out);
 
-/* Release a population.  EBUSY while requests that use it are in flight. */
+/* Release a population and its device memory.  NULL is a no-op.
+ * Errors: EBUSY while requests that use it are in flight. */
 snaps_status snaps_release(snaps_pop *pop);
 
-/* Size of a population. */
+/* Size of a population: objects n and features f (host outputs).
+ * Errors: EINVAL (pop or an output NULL). */
 snaps_status snaps_pop_shape(const snaps_pop *pop, int64_t *n, int *f);
 
 /* Copy the population's stored (normalised) features out as n x f float32
- * row-major into `out` (host or device). */
+ * row-major into `out` (host or device; caller-owned), in the caller's row
+ * order.  Ordered on `stream`; a host `out` is written before the call
+ * returns.  Errors: EINVAL (pop or out NULL), ECUDA. */
 snaps_status snaps_pop_features(const snaps_pop *pop, float *out, void *stream);
 
 /* kNN self-join (kNNSJ, Sec. 3.6) of every subspace in `masks`.
@@ -284,12 +293,16 @@ snaps_status snaps_autotune(snaps_pop *pop, int k, snaps_tune_entry *out, void *
  * ignored).  Errors: EINVAL. */
 snaps_status snaps_autotune_set(snaps_ctx *ctx, int64_t n, int k, const snaps_tune_entry *e);
 
-/* Forget every recorded choice (the built-in rule applies again). */
+/* Forget every recorded choice (the built-in rule applies again).
+ * Errors: EINVAL (ctx NULL). */
 snaps_status snaps_autotune_clear(snaps_ctx *ctx);
 
 /* ---- serving: continuous batching of scoring requests ---- */
 
-/* One scoring request: snaps_scores on a resident population.  masks and
+/* Continuous batching is this library's serving layer; the paper schedules
+ * whole subspaces across GPUs instead (Sec. 3.8.2).
+ *
+ * One scoring request: snaps_scores on a resident population.  masks and
  * eps are copied at submit; the outputs (device or host, caller-owned) must
  * stay valid until the request completes. */
 typedef struct snaps_request {
@@ -330,7 +343,9 @@ snaps_status snaps_poll(snaps_ctx *ctx, uint64_t ticket, int64_t timeout_us,
  * status); EBUSY if it is already running or done. */
 snaps_status snaps_cancel(snaps_ctx *ctx, uint64_t ticket);
 
-/* Number of requests the scheduler may run at once (default 4, 1..64). */
+/* Number of requests the scheduler may run at once (default 4, 1..64).
+ * Errors: EINVAL (ctx NULL or slots out of range), EBUSY (lowering it after
+ * serving has started). */
 snaps_status snaps_set_slots(snaps_ctx *ctx, int slots);
 
 /* ---- scoring without device allocation ---- */
@@ -375,7 +390,8 @@ snaps_status snaps_scores_static(int device, const float *feat, int64_t n, int f
  * Errors: EINVAL (NULL output), ECUDA. */
 snaps_status snaps_calibrate_alu(int device, double *evals_per_s);
 
-/* ---- tracing: device time per phase ---- */
+/* ---- tracing: device time per phase (measurement plumbing; the paper has
+ * no counterpart) ---- */
 
 #define SNAPS_PHASE_INDEX 0      /* normalisation kernels of snaps_index */
 #define SNAPS_PHASE_JOIN_TREE 1  /* subspace-batched (tree) join kernel */
@@ -391,13 +407,15 @@ snaps_status snaps_calibrate_alu(int device, double *evals_per_s);
 
 /* enable != 0: clear the counters and start recording, around every kernel
  * launch of every later call on this context, a pair of CUDA events on the
- * stream the kernel is launched on.  enable == 0 stops recording. */
+ * stream the kernel is launched on.  enable == 0 stops recording.
+ * Errors: EINVAL (ctx NULL). */
 snaps_status snaps_trace(snaps_ctx *ctx, int enable);
 
 /* Wait for the recorded events, then report per phase the summed device time
  * in milliseconds (ms[SNAPS_N_PHASES]) and the number of kernel launches
  * (launches[SNAPS_N_PHASES]) since tracing was enabled or last read; either
- * array may be NULL.  The counters restart from zero. */
+ * array may be NULL.  The counters restart from zero.
+ * Errors: EINVAL (ctx NULL), ECUDA (an event failed). */
 snaps_status snaps_trace_read(snaps_ctx *ctx, double *ms, int64_t *launches);
 
 #ifdef __cplusplus
