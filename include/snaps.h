@@ -14,7 +14,11 @@
  *    failure snaps_last_error() gives a message for the calling thread.
  *  - Pointers are plain host or device pointers; the library tells them
  *    apart with cudaPointerGetAttributes.  Unless a call says otherwise,
- *    input arrays may be host or device memory, and so may outputs.  A call
+ *    input arrays may be host or device memory, and so may outputs.  Device
+ *    memory must belong to the call's device (or be managed memory); a
+ *    buffer on another GPU is rejected with EINVAL.
+ *  - A call makes its context's device current while it runs and restores
+ *    the calling thread's previous current device before it returns.  A call
  *    that writes any host output returns only after that output is written
  *    (it synchronises the stream); a call with device outputs only is
  *    asynchronous on `stream`.
@@ -174,9 +178,11 @@ snaps_status snaps_eps_selfjoin(snaps_pop *pop, const uint16_t *masks, int n_mas
  * scores: n_masks x 4 x n float32 raw metrics (rows SNAPS_SCORE_*), or NULL.
  *   Counts and in-degrees are exact integers stored as float.
  * norm:   n_masks x 4 x n float32, each metric mapped onto [0, 1] with
- *   1 = most outlying, from its population min and max taken in FP64 (a
- *   constant metric maps to 0; objects without eps-neighbours get 1 for the
- *   eps mean distance and the rest are scaled among themselves), or NULL.
+ *   1 = most outlying, from its population min and max (a constant metric
+ *   maps to 0; objects without eps-neighbours get 1 for the eps mean
+ *   distance and the rest are scaled among themselves), or NULL.  The span
+ *   max - min and its reciprocal are taken in FP64; each value is within
+ *   half an FP32 ulp (plus 2^-20 ulp) of the FP64 quotient.
  * top:    n_masks x 4 x top_n int32, the first top_n objects of each ranking
  *   (Sec. 3.4, rank 0 = most outlying): counts and in-degrees ascending,
  *   mean distances descending, objects without eps-neighbours first for the
@@ -360,10 +366,13 @@ snaps_status snaps_set_slots(snaps_ctx *ctx, int slots);
  * It allocates nothing.  Its working memory -- the normalised population,
  * statistics, the kernels' control block and the subspace plan, about 2.7 MB
  * -- is one static device array inside the library that every GPU which loads
- * the library keeps until the process exits.  The first call on a device looks
- * up that array's device address; make that first call before any stream
- * capture.
- * device: CUDA device to run on (made current by the call).
+ * the library keeps until the process exits.  Every call looks up that
+ * array's device address (cudaGetSymbolAddress, with `device` current).  The
+ * first call on a device may make the CUDA driver load the library's device
+ * code and, with it, create the array; make that first call before any
+ * stream capture.
+ * device: CUDA device to run on.  The call makes it current and restores the
+ *   calling thread's previous current device before it returns.
  * feat: n x f float32 row-major in device memory, normalised as flags say
  *   (SNAPS_NORM_MINMAX / SNAPS_NAN_TO_MEAN), 2 <= n <= SNAPS_STATIC_MAX_N.
  * masks, n_masks (<= SNAPS_STATIC_MAX_MASKS), k, eps: as for snaps_scores.
@@ -374,8 +383,8 @@ snaps_status snaps_set_slots(snaps_ctx *ctx, int slots);
  * at zero), so calls whose GPU work overlaps -- on different streams or
  * threads -- race; issue them one after another.  Results equal those of
  * snaps_index + snaps_scores.
- * Errors: EINVAL (sizes beyond the limits, host pointers, bad masks / k / eps,
- * non-finite features), ETIMEOUT, ECUDA. */
+ * Errors: EINVAL (sizes beyond the limits, host pointers or memory of another
+ * GPU, bad masks / k / eps, non-finite features), ETIMEOUT, ECUDA. */
 snaps_status snaps_scores_static(int device, const float *feat, int64_t n, int f,
                                  uint32_t flags, const uint16_t *masks, int n_masks, int k,
                                  const float *eps, float *scores, int32_t *top, int top_n,
@@ -397,8 +406,10 @@ snaps_status snaps_calibrate_alu(int device, double *evals_per_s);
 #define SNAPS_PHASE_JOIN_TREE 1  /* subspace-batched (tree) join kernel */
 #define SNAPS_PHASE_JOIN_LANE 2  /* joins of subspaces alone in their 32-subspace chunk
                                   * (the subspace-at-a-time kernel) */
-#define SNAPS_PHASE_NORM 3       /* normalised-metric kernel */
-#define SNAPS_PHASE_TOP 4        /* top-n ranking kernel */
+#define SNAPS_PHASE_NORM 3       /* finishing kernel of a call that asks for normalised
+                                  * metrics (it also ranks, when top-n lists are asked for) */
+#define SNAPS_PHASE_TOP 4        /* finishing kernel of a call that asks for top-n rankings
+                                  * alone */
 #define SNAPS_PHASE_JOIN_TC 5    /* tensor-core filtered join kernel */
 #define SNAPS_PHASE_ORDER 6      /* per-chunk row orders for the subspace-batched join */
 #define SNAPS_PHASE_GRID 7       /* grid index builds and grid-indexed joins */

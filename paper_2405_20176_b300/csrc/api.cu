@@ -24,6 +24,7 @@
 #include "prep.cuh"
 #include "grid.cuh"
 #include "select.cuh"
+#include "pointers.h"
 
 // ---- error plumbing -----------------------------------------------------------------
 
@@ -49,6 +50,14 @@ using namespace snaps;
         snaps::set_error(__VA_ARGS__);  \
         return code;                    \
     } while (0)
+
+// Make `dev` current for the rest of the entry point; the caller's current
+// device is restored when the entry point returns.
+#define ON_DEVICE(dev)                                                                    \
+    DeviceScope device_scope_(dev);                                                      \
+    if (device_scope_.error() != cudaSuccess)                                            \
+    FAIL(SNAPS_ECUDA, "cudaSetDevice(%d) failed: %s", (int)(dev),                        \
+         cudaGetErrorString(device_scope_.error()))
 
 // ---- objects -------------------------------------------------------------------------
 
@@ -191,6 +200,15 @@ bool is_device_ptr(const void *p)
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+// EINVAL for a caller buffer in another GPU's memory: the kernels on the
+// context's device would fault on it.
+snaps_status check_not_foreign(const void *p, int device, const char *name)
+{
+    if (p && ptr_kind(p, device) == PtrKind::Foreign)
+        FAIL(SNAPS_EINVAL, "%s is device memory of another GPU (the context runs on device %d)", name, device);
+    return SNAPS_OK;
+}
+
 inline int popc16(uint32_t m) { return __builtin_popcount(m); }
 
 // Carve aligned sub-buffers out of one scratch block.
@@ -234,6 +252,16 @@ snaps_status validate(const JobSpec &j)
     if (!j.masks) FAIL(SNAPS_EINVAL, "masks is NULL");
     if (is_device_ptr(j.masks)) FAIL(SNAPS_EINVAL, "masks must be a host array");
     if (j.eps && is_device_ptr(j.eps)) FAIL(SNAPS_EINVAL, "eps must be a host array");
+    {
+        const int dev = p->ctx->device;
+        SNAPS_TRY(check_not_foreign(j.scores, dev, "scores"));
+        SNAPS_TRY(check_not_foreign(j.norm, dev, "norm"));
+        SNAPS_TRY(check_not_foreign(j.top, dev, "top"));
+        SNAPS_TRY(check_not_foreign(j.knn_idx, dev, "idx"));
+        SNAPS_TRY(check_not_foreign(j.knn_dist, dev, "dist"));
+        SNAPS_TRY(check_not_foreign(j.eps_count, dev, "count"));
+        SNAPS_TRY(check_not_foreign(j.eps_mean, dev, "mean_dist"));
+    }
     for (int m = 0; m < j.n_masks; ++m) {
         const uint32_t v = j.masks[m];
         if (popc16(v) < 2 || (v >> p->f) != 0)
@@ -730,13 +758,10 @@ snaps_status run_job(snaps_ctx *ctx, const JobSpec &j, cudaStream_t st, Scratch 
             SNAPS_TRY(run_grid_subspace(shape, g, out, gb, st));
         }
     }
-    if (j.norm) {
-        TraceScope ts(ctx, SNAPS_PHASE_NORM, st);
-        SNAPS_TRY(launch_norm(L.scores, n, j.n_masks, L.norm, st));
-    }
-    if (j.top) {
-        TraceScope ts(ctx, SNAPS_PHASE_TOP, st);
-        SNAPS_TRY(launch_top(L.scores, n, j.n_masks, j.top_n, L.top, st));
+    if (j.norm || j.top) {
+        // one finishing kernel for the normalised metrics and the rankings
+        TraceScope ts(ctx, j.norm ? SNAPS_PHASE_NORM : SNAPS_PHASE_TOP, st);
+        SNAPS_TRY(launch_finish(L.scores, n, j.n_masks, L.norm, j.top ? j.top_n : 0, L.top, st));
     }
 
     bool host_out = false;
@@ -769,12 +794,6 @@ snaps_status run_job(snaps_ctx *ctx, const JobSpec &j, cudaStream_t st, Scratch 
         if (err & kErrBadRow) FAIL(SNAPS_ECUDA, "a join kernel met rows without a valid original index (error word 0x%x)", err);
         if (err) FAIL(SNAPS_ETIMEOUT, "a device-side wait gave up (error word 0x%x)", err);
     }
-    return SNAPS_OK;
-}
-
-snaps_status device_guard(const snaps_ctx *ctx)
-{
-    SNAPS_CHECK_CUDA(cudaSetDevice(ctx->device));
     return SNAPS_OK;
 }
 
@@ -874,7 +893,7 @@ snaps_status snaps_create(int device, size_t hbm_budget_bytes, snaps_ctx **out)
     int count = 0;
     SNAPS_CHECK_CUDA(cudaGetDeviceCount(&count));
     if (device < 0 || device >= count) FAIL(SNAPS_EINVAL, "device %d out of range (%d devices)", device, count);
-    SNAPS_CHECK_CUDA(cudaSetDevice(device));
+    ON_DEVICE(device);
     size_t free_b = 0, total_b = 0;
     SNAPS_CHECK_CUDA(cudaMemGetInfo(&free_b, &total_b));
     snaps_ctx *ctx = new snaps_ctx();
@@ -895,7 +914,7 @@ snaps_status snaps_destroy(snaps_ctx *ctx)
 {
     clear_error();
     if (!ctx) return SNAPS_OK;
-    cudaSetDevice(ctx->device);
+    DeviceScope device_scope(ctx->device);
     {
         std::lock_guard<std::mutex> lk(ctx->q_mu);
         ctx->stopping = true;
@@ -942,7 +961,7 @@ snaps_status snaps_index(snaps_ctx *ctx, const float *feat, int64_t n, int f, ui
     if (n < 2 || n > (int64_t(1) << 24)) FAIL(SNAPS_EINVAL, "n must be in 2..2^24 (got %lld)", (long long)n);
     if (f < 1 || f > SNAPS_MAX_FEATURES) FAIL(SNAPS_EINVAL, "f must be in 1..15 (got %d)", f);
     if (flags & ~(SNAPS_NORM_MINMAX | SNAPS_NAN_TO_MEAN)) FAIL(SNAPS_EINVAL, "unknown flags 0x%x", flags);
-    SNAPS_TRY(device_guard(ctx));
+    ON_DEVICE(ctx->device);
     cudaStream_t st = (cudaStream_t)stream;
     snaps_pop *p = new snaps_pop();
     p->ctx = ctx;
@@ -959,6 +978,7 @@ snaps_status snaps_index(snaps_ctx *ctx, const float *feat, int64_t n, int f, ui
     p->x = (float4 *)xp;
     // staging: input copy (when on the host) + column statistics + flag
     const size_t in_bytes = (size_t)n * f * sizeof(float);
+    SNAPS_TRY(check_not_foreign(feat, ctx->device, "feat"));
     const bool dev_in = is_device_ptr(feat);
     const size_t aux = 256 + sizeof(ColStats) * 16 + 256;
     void *stage = nullptr;
@@ -1072,7 +1092,7 @@ snaps_status snaps_release(snaps_pop *pop)
     if (!pop) return SNAPS_OK;
     if (pop->inflight.load() > 0) FAIL(SNAPS_EBUSY, "population has %d requests in flight", pop->inflight.load());
     snaps_ctx *ctx = pop->ctx;
-    cudaSetDevice(ctx->device);
+    DeviceScope device_scope(ctx->device);
     cudaDeviceSynchronize();
     ctx_free(ctx, pop->x, pop->bytes);
     ctx->n_pops.fetch_sub(1);
@@ -1094,9 +1114,10 @@ snaps_status snaps_pop_features(const snaps_pop *pop, float *out, void *stream)
     clear_error();
     if (!pop || !out) FAIL(SNAPS_EINVAL, "pop and out must be non-NULL");
     snaps_ctx *ctx = pop->ctx;
-    SNAPS_TRY(device_guard(ctx));
+    ON_DEVICE(ctx->device);
     cudaStream_t st = (cudaStream_t)stream;
     const size_t bytes = (size_t)pop->n * pop->f * sizeof(float);
+    SNAPS_TRY(check_not_foreign(out, ctx->device, "out"));
     if (is_device_ptr(out)) return launch_unpack(pop->x, pop->n, pop->f, out, st);
     void *tmp = nullptr;
     SNAPS_TRY(ctx_alloc(ctx, bytes, &tmp));
@@ -1119,7 +1140,7 @@ snaps_status snaps_knn_selfjoin(snaps_pop *pop, const uint16_t *masks, int n_mas
     if (!pop) FAIL(SNAPS_EINVAL, "pop is NULL");
     if (!idx) FAIL(SNAPS_EINVAL, "idx is NULL");
     if (k < 1) FAIL(SNAPS_EINVAL, "k must be >= 1 (got %d)", k);
-    SNAPS_TRY(device_guard(pop->ctx));
+    ON_DEVICE(pop->ctx->device);
     JobSpec j;
     j.pop = pop;
     j.masks = masks;
@@ -1137,7 +1158,7 @@ snaps_status snaps_eps_selfjoin(snaps_pop *pop, const uint16_t *masks, int n_mas
 {
     clear_error();
     if (!pop) FAIL(SNAPS_EINVAL, "pop is NULL");
-    SNAPS_TRY(device_guard(pop->ctx));
+    ON_DEVICE(pop->ctx->device);
     JobSpec j;
     j.pop = pop;
     j.masks = masks;
@@ -1201,7 +1222,7 @@ snaps_status snaps_select(snaps_pop *pop, const uint16_t *masks, int n_masks, co
 {
     clear_error();
     if (!pop) FAIL(SNAPS_EINVAL, "pop is NULL");
-    SNAPS_TRY(device_guard(pop->ctx));
+    ON_DEVICE(pop->ctx->device);
     snaps_ctx *ctx = pop->ctx;
     const int64_t n = pop->n;
     if (n_masks < 1 || !masks || is_device_ptr(masks)) FAIL(SNAPS_EINVAL, "masks: a host array of >= 1 masks");
@@ -1209,6 +1230,10 @@ snaps_status snaps_select(snaps_pop *pop, const uint16_t *masks, int n_masks, co
         if (popc16(masks[m]) < 2 || (masks[m] >> pop->f) != 0)
             FAIL(SNAPS_EINVAL, "mask %d (0x%x) must have 2..%d bits, all below feature %d", m, masks[m], pop->f,
                  pop->f);
+    SNAPS_TRY(check_not_foreign(u_eps, ctx->device, "u_eps"));
+    SNAPS_TRY(check_not_foreign(eps_select, ctx->device, "eps_select"));
+    SNAPS_TRY(check_not_foreign(u_k, ctx->device, "u_k"));
+    SNAPS_TRY(check_not_foreign(k_select, ctx->device, "k_select"));
     const bool want_eps = u_eps || eps_select, want_k = u_k || k_select;
     if (!want_eps && !want_k) FAIL(SNAPS_EINVAL, "no output requested");
     if (want_eps) {
@@ -1318,7 +1343,7 @@ snaps_status snaps_autotune(snaps_pop *pop, int k, snaps_tune_entry *out, void *
 {
     clear_error();
     if (!pop) FAIL(SNAPS_EINVAL, "pop is NULL");
-    SNAPS_TRY(device_guard(pop->ctx));
+    ON_DEVICE(pop->ctx->device);
     snaps_ctx *ctx = pop->ctx;
     const int64_t n = pop->n;
     const int f = pop->f;
@@ -1453,7 +1478,7 @@ snaps_status snaps_eps_selectivity(snaps_pop *pop, const uint16_t *masks, int n_
 {
     clear_error();
     if (!pop) FAIL(SNAPS_EINVAL, "pop is NULL");
-    SNAPS_TRY(device_guard(pop->ctx));
+    ON_DEVICE(pop->ctx->device);
     snaps_ctx *ctx = pop->ctx;
     const int64_t n = pop->n;
     if (n < 2) FAIL(SNAPS_EINVAL, "need at least 2 objects");
@@ -1473,6 +1498,8 @@ snaps_status snaps_eps_selectivity(snaps_pop *pop, const uint16_t *masks, int n_
     if (n_bins < 1 || n_bins > SNAPS_SELECTIVITY_MAX_BINS)
         FAIL(SNAPS_EINVAL, "n_bins must be in 1..%d", SNAPS_SELECTIVITY_MAX_BINS);
     if (!eps) FAIL(SNAPS_EINVAL, "eps is NULL");
+    SNAPS_TRY(check_not_foreign(eps, ctx->device, "eps"));
+    SNAPS_TRY(check_not_foreign(eps_mean, ctx->device, "eps_mean"));
     SelectivityTargets tg{};
     tg.n = n_targets;
     tg.m = (int)std::min<int64_t>(n_sample, n);
@@ -1513,7 +1540,7 @@ snaps_status snaps_scores(snaps_pop *pop, const uint16_t *masks, int n_masks, in
     clear_error();
     if (!pop) FAIL(SNAPS_EINVAL, "pop is NULL");
     if (k < 1) FAIL(SNAPS_EINVAL, "k must be >= 1 (got %d)", k);
-    SNAPS_TRY(device_guard(pop->ctx));
+    ON_DEVICE(pop->ctx->device);
     JobSpec j;
     j.pop = pop;
     j.masks = masks;
@@ -1548,7 +1575,7 @@ snaps_status snaps_submit(snaps_ctx *ctx, const snaps_request *req, uint64_t *ti
     if (!ctx || !req || !ticket) FAIL(SNAPS_EINVAL, "ctx, req and ticket must be non-NULL");
     if (!req->pop || req->pop->ctx != ctx) FAIL(SNAPS_EINVAL, "request population does not belong to this context");
     if (req->k < 1) FAIL(SNAPS_EINVAL, "k must be >= 1 (got %d)", req->k);
-    SNAPS_TRY(device_guard(ctx));
+    ON_DEVICE(ctx->device);
     Request *r = new Request();
     r->req = *req;
     if (req->n_masks < 1 || !req->masks) {
@@ -1643,7 +1670,7 @@ snaps_status snaps_trace(snaps_ctx *ctx, int enable)
 {
     clear_error();
     if (!ctx) FAIL(SNAPS_EINVAL, "ctx is NULL");
-    SNAPS_TRY(device_guard(ctx));
+    ON_DEVICE(ctx->device);
     std::lock_guard<std::mutex> g(ctx->tr_mu);
     if (enable) {
         for (auto &m : ctx->marks) {
@@ -1660,7 +1687,7 @@ snaps_status snaps_trace_read(snaps_ctx *ctx, double *ms, int64_t *launches)
 {
     clear_error();
     if (!ctx) FAIL(SNAPS_EINVAL, "ctx is NULL");
-    SNAPS_TRY(device_guard(ctx));
+    ON_DEVICE(ctx->device);
     std::vector<snaps_ctx::Mark> marks;
     {
         std::lock_guard<std::mutex> g(ctx->tr_mu);

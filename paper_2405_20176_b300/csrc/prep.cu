@@ -1,6 +1,6 @@
-// Population preparation (Sec. 3.3 normalisation, Sec. 2.1 missing values)
-// and the per-subspace finishing steps: normalised metrics from FP64
-// population statistics and the top-n outlier rankings (Sec. 3.4, Table 2).
+// Population preparation: normalisation (Sec. 3.3), missing values (Sec. 2.1),
+// the sort-by-cell row order and the per-chunk row copies of the
+// subspace-batched join.
 
 #include <math_constants.h>
 
@@ -302,198 +302,6 @@ __global__ void gather_rows_kernel(const float4 *__restrict__ src, const int32_t
     }
 }
 
-// ---- normalised metrics --------------------------------------------------------
-
-constexpr int kRowThreads = 512;
-
-__device__ __forceinline__ void block_minmax(double &lo, double &hi)
-{
-    __shared__ double s_lo[32], s_hi[32];
-    for (int o = 16; o > 0; o >>= 1) {
-        lo = fmin(lo, __shfl_xor_sync(dev::kFull, lo, o));
-        hi = fmax(hi, __shfl_xor_sync(dev::kFull, hi, o));
-    }
-    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-    __syncthreads();
-    if (l == 0) {
-        s_lo[w] = lo;
-        s_hi[w] = hi;
-    }
-    __syncthreads();
-    lo = s_lo[0];
-    hi = s_hi[0];
-    for (int i = 1; i < (int)(blockDim.x >> 5); ++i) {
-        lo = fmin(lo, s_lo[i]);
-        hi = fmax(hi, s_hi[i]);
-    }
-}
-
-// One block per (subspace, metric) row.  Counts and in-degrees: 1 at the
-// population minimum; mean distances: 1 at the maximum; objects without
-// eps-neighbours get 1 for the eps mean distance and the others are scaled
-// over the objects that have neighbours.  Statistics and the scaling are FP64.
-__global__ void __launch_bounds__(kRowThreads)
-    norm_kernel(const float *__restrict__ scores, int64_t n, float *__restrict__ norm)
-{
-    const int64_t row = blockIdx.x;  // slot * 4 + metric
-    const int m = (int)(row % 4);
-    const float *s = scores + row * n;
-    const float *cnt = scores + (row - m) * n;  // metric 0 of the same subspace
-    double lo = CUDART_INF, hi = -CUDART_INF;
-    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
-        if (m == SNAPS_SCORE_EPS_MEAN && cnt[i] == 0.f) continue;
-        const double v = (double)s[i];
-        lo = fmin(lo, v);
-        hi = fmax(hi, v);
-    }
-    block_minmax(lo, hi);
-    const double span = hi - lo;
-    const bool up = (m == SNAPS_SCORE_EPS_MEAN || m == SNAPS_SCORE_KNN_MEAN);
-    float *z = norm + row * n;
-    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
-        if (m == SNAPS_SCORE_EPS_MEAN && cnt[i] == 0.f) {
-            z[i] = 1.f;
-            continue;
-        }
-        const double v = (double)s[i];
-        double y = 0.0;
-        if (span > 0.0) y = up ? (v - lo) / span : (hi - v) / span;
-        z[i] = (float)y;
-    }
-}
-
-// ---- top-n rankings -------------------------------------------------------------
-
-// Order key of object i for a metric: smaller = more outlying.  Metric values
-// are non-negative floats, whose bit patterns order like the values.
-__device__ __forceinline__ uint32_t order_key(const float *s, const float *cnt, int m, int64_t i)
-{
-    const uint32_t b = __float_as_uint(s[i]);
-    switch (m) {
-    case SNAPS_SCORE_EPS_COUNT:
-    case SNAPS_SCORE_KNN_INDEG:
-        return b;  // ascending
-    case SNAPS_SCORE_EPS_MEAN:
-        return cnt[i] == 0.f ? 0u : 0xffffffffu - b;  // no neighbours first, then descending
-    default:
-        return 0xffffffffu - b;  // descending
-    }
-}
-
-constexpr int kTopThreads = 1024;
-constexpr int kTopMax = 1024;
-
-// One block per (subspace, metric) row: radix-select the top_n-th smallest
-// key (8 bits per pass, warp-aggregated histogram updates), gather every
-// object with a smaller key plus the lowest-index objects equal to it, and
-// sort the gathered (key, index) pairs.
-__global__ void __launch_bounds__(kTopThreads)
-    top_kernel(const float *__restrict__ scores, int64_t n, int top_n, int32_t *__restrict__ top)
-{
-    __shared__ unsigned hist[256];
-    __shared__ unsigned long long sel[kTopMax];
-    __shared__ uint32_t s_prefix, s_need;
-    __shared__ unsigned s_count;
-    __shared__ unsigned s_warp[32];
-    const int64_t row = blockIdx.x;
-    const int m = (int)(row % 4);
-    const float *s = scores + row * n;
-    const float *cnt = scores + (row - m) * n;
-    const unsigned lane = threadIdx.x & 31u;
-    const int warp = threadIdx.x >> 5;
-
-    uint32_t prefix = 0, pmask = 0;
-    unsigned need = (unsigned)top_n;
-    for (int shift = 24; shift >= 0; shift -= 8) {
-        for (int b = threadIdx.x; b < 256; b += blockDim.x) hist[b] = 0;
-        __syncthreads();
-        const int64_t n_round = (n + 31) / 32 * 32;
-        for (int64_t i = threadIdx.x; i < n_round; i += blockDim.x) {
-            bool in = false;
-            unsigned bin = 0;
-            if (i < n) {
-                const uint32_t key = order_key(s, cnt, m, i);
-                in = (key & pmask) == prefix;
-                bin = (key >> shift) & 255u;
-            }
-            const unsigned grp = __match_any_sync(dev::kFull, in ? bin : 256u + lane);
-            if (in && (__ffs(grp) - 1) == (int)lane) atomicAdd(&hist[bin], __popc(grp));
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            unsigned acc = 0;
-            int b = 0;
-            for (; b < 256; ++b) {
-                if (acc + hist[b] >= need) break;
-                acc += hist[b];
-            }
-            s_prefix = prefix | ((uint32_t)b << shift);
-            s_need = need - acc;
-        }
-        __syncthreads();
-        prefix = s_prefix;
-        need = s_need;
-        pmask |= 255u << shift;
-        __syncthreads();
-    }
-    // prefix = the top_n-th smallest key; `need` objects with that key are taken
-    if (threadIdx.x == 0) s_count = 0;
-    __syncthreads();
-    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
-        const uint32_t key = order_key(s, cnt, m, i);
-        if (key < prefix) {
-            const unsigned p = atomicAdd(&s_count, 1u);
-            sel[p] = ((unsigned long long)key << 32) | (uint32_t)i;
-        }
-    }
-    __syncthreads();
-    // equal keys in index order: block-wide ordered compaction
-    unsigned base = s_count;
-    unsigned left = need;
-    for (int64_t c0 = 0; c0 < n && left > 0; c0 += blockDim.x) {
-        const int64_t i = c0 + threadIdx.x;
-        const bool eq = i < n && order_key(s, cnt, m, i) == prefix;
-        const unsigned bal = __ballot_sync(dev::kFull, eq);
-        if (lane == 0) s_warp[warp] = __popc(bal);
-        __syncthreads();
-        unsigned before = 0, total = 0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
-            if (w < warp) before += s_warp[w];
-            total += s_warp[w];
-        }
-        before += __popc(bal & ((1u << lane) - 1u));
-        if (eq && before < left)
-            sel[base + before] = ((unsigned long long)prefix << 32) | (uint32_t)i;
-        __syncthreads();
-        const unsigned took = total < left ? total : left;
-        base += took;
-        left -= took;
-    }
-    // bitonic sort of the gathered pairs (padded to a power of two)
-    int size = 1;
-    while (size < top_n) size <<= 1;
-    for (int i = threadIdx.x + top_n; i < size; i += blockDim.x) sel[i] = ~0ull;
-    __syncthreads();
-    for (int kk = 2; kk <= size; kk <<= 1) {
-        for (int jj = kk >> 1; jj > 0; jj >>= 1) {
-            for (int i = threadIdx.x; i < size; i += blockDim.x) {
-                const int p = i ^ jj;
-                if (p > i) {
-                    const unsigned long long a = sel[i], b = sel[p];
-                    const bool asc = (i & kk) == 0;
-                    if ((a > b) == asc) {
-                        sel[i] = b;
-                        sel[p] = a;
-                    }
-                }
-            }
-            __syncthreads();
-        }
-    }
-    for (int i = threadIdx.x; i < top_n; i += blockDim.x)
-        top[row * top_n + i] = (int32_t)(uint32_t)(sel[i] & 0xffffffffull);
-}
-
 }  // namespace
 
 snaps_status launch_normalise(const float *in_dev, int64_t n, int64_t n_pad, int f,
@@ -562,27 +370,6 @@ snaps_status launch_unpack(const float4 *x, int64_t n, int f, float *out, cudaSt
 {
     const int64_t blocks = std::min<int64_t>((n + 255) / 256, 148 * 16);
     unpack_rows_kernel<<<(unsigned)blocks, 256, 0, st>>>(x, n, f, out);
-    SNAPS_CHECK_CUDA(cudaGetLastError());
-    return SNAPS_OK;
-}
-
-snaps_status launch_norm(const float *scores, int64_t n, int n_slots, float *norm, cudaStream_t st)
-{
-    if (n_slots <= 0) return SNAPS_OK;
-    norm_kernel<<<(unsigned)(n_slots * 4), kRowThreads, 0, st>>>(scores, n, norm);
-    SNAPS_CHECK_CUDA(cudaGetLastError());
-    return SNAPS_OK;
-}
-
-snaps_status launch_top(const float *scores, int64_t n, int n_slots, int top_n, int32_t *top,
-                        cudaStream_t st)
-{
-    if (n_slots <= 0 || top_n <= 0) return SNAPS_OK;
-    if (top_n > kTopMax || top_n > n) {
-        set_error("top_n %d out of range (max %d, n %lld)", top_n, kTopMax, (long long)n);
-        return SNAPS_EINVAL;
-    }
-    top_kernel<<<(unsigned)(n_slots * 4), kTopThreads, 0, st>>>(scores, n, top_n, top);
     SNAPS_CHECK_CUDA(cudaGetLastError());
     return SNAPS_OK;
 }

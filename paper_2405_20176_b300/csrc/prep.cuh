@@ -59,10 +59,12 @@ snaps_status launch_chunk_boxes(const float4 *copies, int64_t n_pad, int n_chunk
 // in the objects' original order.
 snaps_status launch_unpack(const float4 *x, int64_t n, int f, float *out, cudaStream_t st);
 
-// norm[slot][m][i] from scores[slot][m][i] (n_slots x 4 x n each).
+// The finishing kernel (finish.cu), one launch for both outputs:
+// norm[slot][m][i] from scores[slot][m][i] (n_slots x 4 x n each; NULL skips
+// it) and top[slot][m][0..top_n) (NULL or top_n == 0 skips it).
+snaps_status launch_finish(const float *scores, int64_t n, int n_slots, float *norm, int top_n, int32_t *top,
+                           cudaStream_t st);
 snaps_status launch_norm(const float *scores, int64_t n, int n_slots, float *norm, cudaStream_t st);
-
-// top[slot][m][0..top_n) from scores (n_slots x 4 x n).
 snaps_status launch_top(const float *scores, int64_t n, int n_slots, int top_n, int32_t *top,
                         cudaStream_t st);
 

@@ -25,6 +25,7 @@
 #include "common.cuh"
 #include "join.cuh"
 #include "prep.cuh"
+#include "pointers.h"
 
 namespace snaps {
 namespace {
@@ -49,10 +50,8 @@ constexpr size_t kStaticScratchBytes = kOffGroups + align256(sizeof(MaskGroup) *
 // address comes from cudaGetSymbolAddress.
 static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
 
-// Per-device address of the array, looked up once per device.
 constexpr int kMaxDevices = 64;
 std::mutex g_static_mu;
-void *g_static_addr[kMaxDevices] = {};
 
 // Host staging of the subspace plan: fixed arrays, no heap.
 TreeChunk g_plan_chunks[kStaticMaxChunks];
@@ -66,15 +65,9 @@ float default_or_given_eps2(const uint16_t *masks, const float *eps, int m)
     return eps ? eps[m] * eps[m] : default_eps2(__builtin_popcount(masks[m]));
 }
 
-bool device_memory(const void *p)
-{
-    cudaPointerAttributes a;
-    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
-        cudaGetLastError();
-        return false;
-    }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
-}
+// Device (or managed) memory that the kernels on `device` may use; memory of
+// another GPU does not qualify.
+bool device_memory(const void *p, int device) { return ptr_kind(p, device) == PtrKind::Device; }
 
 }  // namespace
 }  // namespace snaps
@@ -114,22 +107,27 @@ extern "C" snaps_status snaps_scores_static(int device, const float *feat, int64
         if (eps && !(eps[m] >= 0.f && eps[m] < 3.0e18f))
             STATIC_FAIL(SNAPS_EINVAL, "eps[%d] must be a finite value >= 0", m);
     }
-    SNAPS_CHECK_CUDA(cudaSetDevice(device));
-    if (!device_memory(feat) || !device_memory(scores) || (top && !device_memory(top)))
-        STATIC_FAIL(SNAPS_EINVAL, "feat, scores and top must be device memory for the allocation-free call");
+    // the caller's current device is restored on every return path
+    DeviceScope device_scope(device);
+    if (device_scope.error() != cudaSuccess)
+        STATIC_FAIL(SNAPS_ECUDA, "cudaSetDevice(%d) failed: %s", device, cudaGetErrorString(device_scope.error()));
+    if (!device_memory(feat, device) || !device_memory(scores, device) || (top && !device_memory(top, device)))
+        STATIC_FAIL(SNAPS_EINVAL, "feat, scores and top must be memory of device %d for the allocation-free call",
+                    device);
 
     std::lock_guard<std::mutex> guard(g_static_mu);
-    // First call on this device: look up the array's device address (with
-    // this device current).
-    if (!g_static_addr[device]) {
-        void *p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
-        if (e != cudaSuccess || !p)
+    // The array's device address, with this device current.  Looked up on
+    // every call: after a context reset the module is loaded again and the
+    // address can change.  The first call on a device may make the driver
+    // load the library's device code, and with it create the array.
+    void *addr = nullptr;
+    {
+        const cudaError_t e = cudaGetSymbolAddress(&addr, g_static_scratch);
+        if (e != cudaSuccess || !addr)
             STATIC_FAIL(SNAPS_ECUDA, "cudaGetSymbolAddress of the static scratch failed: %s",
                         cudaGetErrorString(e));
-        g_static_addr[device] = p;
     }
-    char *base = (char *)g_static_addr[device];
+    char *base = (char *)addr;
     float4 *pop = (float4 *)(base + kOffPop);
     float4 *pair = (float4 *)(base + kOffPair);
     ColStats *stats = (ColStats *)(base + kOffStats);

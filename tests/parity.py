@@ -95,3 +95,48 @@ def check_top(gpu_top, ora_scores, ora_top, metric):
     assert np.all(np.where(finite, diff <= tol, gk == ok)), \
         "top-list keys differ beyond the tolerance"
     return int((gpu_top != ora_top).sum())
+
+
+NORM_ATOL = 1e-7  # FP32 output of a value in [0, 1]: half an ulp is <= 3e-8
+
+
+def check_norm(gpu_norm, gpu_scores, ora_scores, ora_norm=None):
+    """Normalised metrics (4, n).
+
+    (a) The normalisation step on its own: the library's output must be the
+        oracle's FP64 normalisation of the library's own raw metrics, to
+        NORM_ATOL.
+    (b) End to end against the oracle's FP64 metrics.  Integer metrics whose
+        rows agree exactly must agree to NORM_ATOL; mean distances within
+        SCORE_RTOL relative move z = (v - lo) / (hi - lo) by at most
+        SCORE_RTOL (|v| + 2 |lo| + |hi|) / (hi - lo), which is the tolerance
+        (the eps mean distance only where the counts agree, since the counts
+        decide which objects take part in its statistics).
+    Returns the largest end-to-end error per metric (None where not compared)."""
+    g64 = np.asarray(gpu_scores, dtype=np.float64)
+    ref = oracle.normalised_scores(g64)
+    np.testing.assert_allclose(gpu_norm, ref, rtol=0, atol=NORM_ATOL,
+                               err_msg="normalisation of the library's own metrics")
+    if ora_norm is None:
+        ora_norm = oracle.normalised_scores(ora_scores)
+    errs = [None] * 4
+    for m in (oracle.EPS_COUNT, oracle.KNN_INDEG):
+        if np.array_equal(g64[m], ora_scores[m]):
+            np.testing.assert_allclose(gpu_norm[m], ora_norm[m], rtol=0, atol=NORM_ATOL)
+            errs[m] = float(np.abs(gpu_norm[m] - ora_norm[m]).max())
+    for m in (oracle.EPS_MEAN, oracle.KNN_MEAN):
+        if m == oracle.EPS_MEAN and not np.array_equal(g64[oracle.EPS_COUNT], ora_scores[oracle.EPS_COUNT]):
+            continue
+        v = ora_scores[m]
+        use = ora_scores[oracle.EPS_COUNT] > 0 if m == oracle.EPS_MEAN else np.ones(v.size, bool)
+        if not use.any():
+            continue
+        lo, hi = v[use].min(), v[use].max()
+        if not hi > lo:
+            np.testing.assert_array_equal(gpu_norm[m][use], 0.0)
+            continue
+        tol = SCORE_RTOL * (np.abs(v) + 2 * abs(lo) + abs(hi)) / (hi - lo) + NORM_ATOL
+        d = np.abs(gpu_norm[m] - ora_norm[m])
+        assert np.all(d <= tol), f"metric {m}: normalised value off by {d.max():.3g}"
+        errs[m] = float(d.max())
+    return errs

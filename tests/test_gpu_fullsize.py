@@ -15,7 +15,7 @@ import pytest
 import oracle
 import paper_2405_20176_b300 as snaps
 import snaps_inputs
-from parity import SCORE_RTOL, check_eps, check_top, eps_bounds
+from parity import SCORE_RTOL, check_eps, check_norm, check_top, eps_bounds
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -30,10 +30,11 @@ def run():
     masks = snaps_inputs.all_masks()
     pop = snaps.snaps_index(ctx, torch.from_numpy(x).cuda())
     sc = torch.empty((masks.size, 4, N), dtype=torch.float32, device="cuda")
+    nz = torch.empty((masks.size, 4, N), dtype=torch.float32, device="cuda")
     top = torch.empty((masks.size, 4, 100), dtype=torch.int32, device="cuda")
-    snaps.snaps_scores(pop, masks, K, scores=sc, top=top, top_n=100)
+    snaps.snaps_scores(pop, masks, K, scores=sc, norm=nz, top=top, top_n=100)
     torch.cuda.synchronize()
-    yield dict(ctx=ctx, pop=pop, x=x, masks=masks, sc=sc, top=top)
+    yield dict(ctx=ctx, pop=pop, x=x, masks=masks, sc=sc, nz=nz, top=top)
     snaps.snaps_release(pop)
     snaps.snaps_destroy(ctx)
 
@@ -61,7 +62,7 @@ def test_sample_against_oracle(run):
     in_band = 0
     # error against the FP64 oracle per metric, over the 16 subspaces checked in full
     err = {"eps_count_mismatch": 0, "knn_indeg_mismatch": 0, "eps_mean_max_rel": 0.0,
-           "knn_mean_max_rel": 0.0}
+           "knn_mean_max_rel": 0.0, "norm_max_abs": [0.0, 0.0, 0.0, 0.0], "norm_compared": [0, 0, 0, 0]}
     for s, mask in enumerate(sample):
         mask = int(mask)
         g = run["sc"][slot[mask]].cpu().numpy()
@@ -78,6 +79,11 @@ def test_sample_against_oracle(run):
             err["eps_mean_max_rel"] = max(err["eps_mean_max_rel"], float(np.max(np.abs(g[1][sure] - ref) / ref)))
             ref = r.scores[oracle.KNN_MEAN]
             err["knn_mean_max_rel"] = max(err["knn_mean_max_rel"], float(np.max(np.abs(g[3] - ref) / ref)))
+            zs = check_norm(run["nz"][slot[mask]].cpu().numpy(), g, r.scores, r.normalised)
+            for mm, e in enumerate(zs):
+                if e is not None:
+                    err["norm_max_abs"][mm] = max(err["norm_max_abs"][mm], e)
+                    err["norm_compared"][mm] += 1
             gt = run["top"][slot[mask]].cpu().numpy()
             if np.array_equal(g[2], r.scores[oracle.KNN_INDEG]):
                 check_top(gt[oracle.KNN_INDEG], r.scores, r.top[oracle.KNN_INDEG], oracle.KNN_INDEG)
@@ -100,6 +106,20 @@ def test_sample_against_oracle(run):
     assert in_band <= 0.01 * (16 * N + 48 * queries.size)
     print(f"\nerror against the FP64 oracle over 16 x {N} objects: {err}; objects with a "
           f"candidate in the band: {in_band}")
+
+
+def test_normalised_every_subspace(run):
+    """At any size: every normalised value lies in [0, 1]; each metric's most
+    outlying object (the head of its top list) maps to 1, and so does every
+    object without eps-neighbours for the eps mean distance, unless the metric
+    is constant."""
+    nz, top, sc = run["nz"], run["top"], run["sc"]
+    assert torch.all((nz >= 0) & (nz <= 1))
+    head = torch.gather(nz, 2, top[:, :, :1].long()).squeeze(2)
+    flat = (sc.amax(dim=2) == sc.amin(dim=2))
+    assert torch.all((head == 1) | flat)
+    none = sc[:, 0] == 0
+    assert torch.all(nz[:, 1][none] == 1)
 
 
 def test_tensor_core_form_same_bits(run):

@@ -9,7 +9,7 @@ import pytest
 import oracle
 import paper_2405_20176_b300 as snaps
 import snaps_inputs
-from parity import BAND, check_eps, check_knn, check_top
+from parity import BAND, check_eps, check_knn, check_norm, check_top
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -76,10 +76,8 @@ def compare(g, xn, masks, k, eps=None, top_n=100):
             np.testing.assert_array_equal(sc[2], r.scores[oracle.KNN_INDEG])
         assert sc[2].sum() == n * k
         np.testing.assert_allclose(sc[3], r.scores[oracle.KNN_MEAN], rtol=1e-5, atol=1e-12)
-        # normalised metrics
-        if np.array_equal(sc[0], r.scores[0]):
-            np.testing.assert_allclose(g["norm"][s][0], r.normalised[0], rtol=0, atol=1e-7)
-        np.testing.assert_allclose(g["norm"][s][3], r.normalised[3], rtol=0, atol=2e-5)
+        # normalised metrics, all four: the step itself and end to end
+        check_norm(g["norm"][s], sc, r.scores, r.normalised)
         # top lists
         for m in range(4):
             if m in (oracle.EPS_COUNT,) and not np.array_equal(sc[0], r.scores[0]):
@@ -137,6 +135,12 @@ def test_table2_worked_example(ctx, golden_dir):
                               "knn_in_degree_rank", "knn_mean_distance_rank"]):
         expect = np.lexsort((np.arange(10), np.array(t2[name])))
         np.testing.assert_array_equal(g["top"][0][m], expect)
+    # normalised metrics worked out by hand from the printed Table 2 values
+    with open(os.path.join(golden_dir, "normalised.json")) as fh:
+        z = json.load(fh)["table2"]
+    for m, name, tol in [(0, "eps_count", 1e-7), (1, "eps_mean", 1e-3), (2, "knn_indeg", 1e-7),
+                         (3, "knn_mean", 1e-3)]:
+        np.testing.assert_allclose(g["norm"][0][m], z[name], rtol=0, atol=tol, err_msg=name)
 
 
 def test_config1_full_space(ctx):
@@ -190,6 +194,29 @@ def test_custom_eps_and_extremes(ctx):
     assert np.all(g["count"][0] == 399) and np.all(g["count"][4] == 399)
     assert np.all(g["count"][2] == 0) and np.all(g["scores"][2][1] == 0)
     compare(g, oracle.normalise(x), masks, 10, eps=[2.0, 2.0, 1e-9, 0.0, 4.0])
+
+
+@pytest.mark.parametrize("case", ["no_neighbours", "crowded_bin"])
+def test_top_lists_crowded_rows(ctx, case):
+    """Rows whose top-100 boundary falls in a crowded part of the ranking: every
+    object tied (no eps-neighbours anywhere: the lowest indices win), and
+    99 far outliers above a cluster of 8,901 objects whose kNN mean distances
+    all fall in one code bin of the finishing kernel."""
+    rng = np.random.default_rng(77)
+    if case == "no_neighbours":
+        x = rng.uniform(0.0, 1.0, size=(9000, 2)).astype(np.float32)
+        eps = [0.0]
+    else:
+        cluster = rng.uniform(0.0, 0.01, size=(8901, 2))
+        line = 1.0 + 0.5 * np.arange(99)[:, None] * np.ones((1, 2))
+        x = np.concatenate([cluster, line])[rng.permutation(9000)].astype(np.float32)
+        eps = [0.002]
+    g = gpu_all(ctx, x, [0b11], 10, eps=eps, flags=0)
+    compare(g, x, [0b11], 10, eps=eps)
+    if case == "no_neighbours":
+        assert np.all(g["scores"][0][0] == 0)
+        for m in (oracle.EPS_COUNT, oracle.EPS_MEAN):
+            np.testing.assert_array_equal(g["top"][0][m], np.arange(100))
 
 
 def test_lattice_ties_and_duplicates_exact(ctx):

@@ -9,7 +9,7 @@ import pytest
 import oracle
 import paper_2405_20176_b300 as snaps
 import snaps_inputs
-from parity import check_eps, check_knn, check_top
+from parity import check_eps, check_knn, check_norm, check_top
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -83,8 +83,9 @@ def test_tc_matches_oracle(ctx, form):
         idx = torch.empty((m, n, 10), dtype=torch.int32, device="cuda")
         dist = torch.empty((m, n, 10), device="cuda")
         sc = np.zeros((m, 4, n), dtype=np.float32)
+        nz = np.zeros((m, 4, n), dtype=np.float32)
         tp = np.zeros((m, 4, 100), dtype=np.int32)
-        snaps.snaps_scores(pop, masks, 10, precision=prec, scores=sc, top=tp, top_n=100)
+        snaps.snaps_scores(pop, masks, 10, precision=prec, scores=sc, norm=nz, top=tp, top_n=100)
         snaps.snaps_knn_selfjoin(pop, masks, 10, idx, dist)
         torch.cuda.synchronize()
     finally:
@@ -102,6 +103,7 @@ def test_tc_matches_oracle(ctx, form):
         np.testing.assert_allclose(sc[s][3], r.scores[oracle.KNN_MEAN], rtol=1e-5)
         for mm in (oracle.EPS_MEAN, oracle.KNN_MEAN):
             check_top(tp[s][mm], r.scores, r.top[mm], mm)
+        check_norm(nz[s], sc[s], r.scores, r.normalised)
 
 
 def test_tc_rejects_wide_features(ctx):
