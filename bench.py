@@ -15,9 +15,11 @@ same metric through the C ABI with host buffers: the features are copied in
 from pinned host memory and the top-100 rankings copied back every step.
 
 `--impl reference` times the FP64 CPU oracle on the host cores instead, on a
-bounded sample of the same workload.  Under torchrun each rank runs its own
-replica (subspaces are independent; no collective on the data path) and the
-reported time is the max over ranks.
+bounded sample of the same workload.  Under torchrun the subspaces are
+shared out across the ranks (whole 32-subspace chunks, longest first to the
+least-loaded rank, Sec. 3.8.2; no collective on the data path), so the job's
+total work is fixed (strong scaling); the reported time is the max over
+ranks, and rank 0 gathers every rank's top-100 lists after the timed legs.
 """
 from __future__ import annotations
 
@@ -103,6 +105,9 @@ def parse():
                          "warm-up call) instead of the two-feature subspaces")
     ap.add_argument("--rubin-cells", type=int, default=0, metavar="R",
                     help="grid cells 1/R of eps wide for the Rubin leg (0: the library's choice)")
+    ap.add_argument("--serving-leg", type=int, default=60, metavar="R",
+                    help="after the batching legs (one GPU), a Poisson stream of R requests through "
+                         "both join forms, reported as the line's `serving` object (0: skip)")
     ap.add_argument("--serving-max-n", type=int, default=100000)
     ap.add_argument("--serving-max-masks", type=int, default=64)
     ap.add_argument("--serving-slots", type=int, default=4)
@@ -187,9 +192,8 @@ class ClockSampler:
 # ---- our arm -------------------------------------------------------------------------------
 
 def max_over_ranks(x: float, dist, device) -> float:
-    """The largest of every rank's x: a job's time is its slowest rank's.  With
-    N replicas each rank does the same work, so the job's throughput is N times
-    one rank's units over that time."""
+    """The largest of every rank's x: a job's time is its slowest rank's, and
+    the job's throughput is all ranks' units over that time."""
     if dist is None:
         return float(x)
     import torch
@@ -206,9 +210,16 @@ def run_ours(args, rank, world, dist):
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
+    from paper_2405_20176_b300 import shard
+
     x = snaps_inputs.population(args.n, 0)
-    masks = workload_masks(args.masks)
+    all_masks = workload_masks(args.masks)
+    # this rank's share of the subspaces (all of them on one GPU)
+    parts, _ = shard.partition(all_masks, args.n, world)
+    positions = parts[rank]
+    masks = all_masks[positions]
     m, n, k = masks.size, args.n, args.k
+    m_total = all_masks.size
     index_flag = {"auto": 0, "grid": snaps.SNAPS_INDEX_GRID, "none": snaps.SNAPS_INDEX_NONE}[args.index]
     head_prec = {"tc_f16": snaps.SNAPS_TC_F16, "tc_bf16": snaps.SNAPS_TC_BF16}.get(
         args.precision, snaps.SNAPS_FP32) | index_flag
@@ -262,7 +273,7 @@ def run_ours(args, rank, world, dist):
         return total_ms, trace, clk.summary()
 
     total_ms, trace, clocks = timed_leg(head_prec, args.steps, args.warmup)
-    units = float(n) * m * args.steps * world
+    units = float(n) * m_total * args.steps
     value = units / (total_ms / 1e3)
     evals_per_step = float(n) * (n - 1) * m
     props = torch.cuda.get_device_properties(local)
@@ -316,11 +327,11 @@ def run_ours(args, rank, world, dist):
     for form in {"both": [snaps.SNAPS_TC_F16], "all": [snaps.SNAPS_TC_F16, snaps.SNAPS_TC_BF16]}.get(
             args.precision, []):
         tc_ms, tc_trace, tc_clocks = timed_leg(form | index_flag, args.tc_steps, 1)
-        tc_units = float(n) * m * args.tc_steps * world
+        tc_units = float(n) * m_total * args.tc_steps
         tc_legs[form_name[form]] = {"value": tc_units / (tc_ms / 1e3), "unit": "objects*subspaces/s",
                   "ms_per_step": tc_ms / args.tc_steps, "steps": args.tc_steps, "warmup": 1,
                   "vs_plain": (tc_units / (tc_ms / 1e3)) / value,
-                  "distance_evals_per_s": evals_per_step * args.tc_steps * world / (tc_ms / 1e3),
+                  "distance_evals_per_s": float(n) * (n - 1) * m_total * args.tc_steps / (tc_ms / 1e3),
                   "roofline": tensor_roofline(tc_trace, args.tc_steps),
                   "phase_ms_per_step": {kn: v[0] / args.tc_steps for kn, v in tc_trace.items()},
                   "gpu_launches": int(sum(v[1] for v in tc_trace.values())),
@@ -352,6 +363,10 @@ def run_ours(args, rank, world, dist):
         e2e = {"value": units / e2e_s, "unit": "objects*subspaces/s",
                "h2d_bytes_per_step": int(x.nbytes), "d2h_bytes_per_step": int(m * 4 * 100 * 4)}
 
+    # every rank's top-100 lists on rank 0, in request order (after the timed legs)
+    gathered = shard.gather({"top": top.cpu().numpy()}, positions, m_total, rank, world, dist)
+    if rank == 0 and gathered["top"].shape[0] != m_total:
+        raise RuntimeError("the gathered top lists do not cover every subspace")
     snaps.snaps_destroy(ctx)
     result = {
         "metric": "objects*subspaces/s",
@@ -362,16 +377,17 @@ def run_ours(args, rank, world, dist):
         "warmup": args.warmup,
         "ms_per_step": total_ms / args.steps,
         "higher_is_better": True,
-        "scaling": "weak",
+        "scaling": "strong",
         "vs_baseline": None,
         "dtype": "f32",
         "data": "synthetic",
-        "config": {"workload": workload_name(args, m), "objects": n, "subspaces": int(m), "k": k,
+        "config": {"workload": workload_name(args, m_total), "objects": n, "subspaces": int(m_total), "k": k,
                    "precision": form_name[head_prec & 0xFF],
                    "index": args.index,
                    "l2": "flushed before every step (512 MB write)",
-                   "parallelism": f"replicas x{world}"},
-        "distance_evals_per_s": evals_per_step * args.steps * world / (total_ms / 1e3),
+                   "parallelism": (f"subspaces sharded x{world}: whole 32-subspace chunks, longest first "
+                                   f"to the least-loaded rank (rank 0: {m} of {m_total})")},
+        "distance_evals_per_s": float(n) * (n - 1) * m_total * args.steps / (total_ms / 1e3),
         "roofline": roofline,
         "phase_ms_per_step": {kname: v[0] / args.steps for kname, v in trace.items()},
         "clocks": clocks,
@@ -384,7 +400,7 @@ def run_ours(args, rank, world, dist):
 
 # ---- serving: a Poisson stream of mixed requests ----------------------------------------------
 
-def serving_requests(args, rng):
+def serving_requests(args, rng, count):
     """Populations N ~ LogUniform(1e3, max_n) (seeded per population), requests
     with 1..max_masks subspaces (d uniform in 2..15, then a uniform subset),
     k in {5, 10, 20}, eps = 0.05 sqrt(d)."""
@@ -394,7 +410,7 @@ def serving_requests(args, rng):
         n = int(np.exp(rng.uniform(np.log(1e3), np.log(args.serving_max_n))))
         pops.append((n, int(rng.integers(0, 1 << 30))))
     reqs = []
-    for _ in range(args.serving):
+    for _ in range(count):
         pi = int(rng.integers(0, n_pops))
         nm = int(rng.integers(1, args.serving_max_masks + 1))
         masks = []
@@ -406,7 +422,7 @@ def serving_requests(args, rng):
     return pops, reqs
 
 
-def run_serving(args):
+def run_serving(args, count=None, with_tc=None):
     """The same Poisson stream of requests through the plain form and, under
     --precision both, through the tensor-core form: identical arrivals (the rate
     is set from the plain form's service time alone), p50/p99 latency for each."""
@@ -414,9 +430,11 @@ def run_serving(args):
 
     import paper_2405_20176_b300 as snaps
 
+    count = args.serving if count is None else count
+    with_tc = (args.precision == "both") if with_tc is None else with_tc
     torch.cuda.set_device(0)
     rng = np.random.default_rng(20240530)
-    pops, reqs = serving_requests(args, rng)
+    pops, reqs = serving_requests(args, rng, count)
     ctx = snaps.snaps_create(0)
     snaps.snaps_set_slots(ctx, args.serving_slots)
     handles = [snaps.snaps_index(ctx, snaps_inputs.population(n, seed)) for n, seed in pops]
@@ -461,7 +479,7 @@ def run_serving(args):
                 "clocks": clk.summary()}
 
     main = stream(head)
-    tc = stream(snaps.SNAPS_TC_F16) if args.precision == "both" else None
+    tc = stream(snaps.SNAPS_TC_F16) if with_tc else None
     for h in handles:
         snaps.snaps_release(h)
     snaps.snaps_destroy(ctx)
@@ -739,6 +757,15 @@ def main():
         dist = tdist
     res = run_ours(args, rank, world, dist)
     if rank == 0:
+        if world == 1 and args.serving_leg > 0:
+            sv = run_serving(args, count=args.serving_leg, with_tc=True)
+            keep = ("value", "unit", "p50_latency_ms", "p99_latency_ms", "p50_queue_ms", "p99_queue_ms",
+                    "requests", "failed", "makespan_s", "arrival_rate_per_s", "mean_service_alone_s",
+                    "config", "clocks")
+            res["serving"] = {key: sv[key] for key in keep}
+            res["serving"]["tc_f16"] = {key: sv["tc_f16"][key] for key in
+                                        ("value", "p50_latency_ms", "p99_latency_ms", "p50_queue_ms",
+                                         "p99_queue_ms", "failed", "makespan_s", "vs_plain", "clocks")}
         if world == 1 and not args.no_cpu_baseline:
             res["cpu_baseline"] = cpu_baseline(args)
         print(json.dumps(res))
