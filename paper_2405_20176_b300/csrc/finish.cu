@@ -21,7 +21,8 @@
 //      lowest indices are taken by an ordered compaction; otherwise a radix
 //      select over the whole row's keys decides (a fallback for rows whose
 //      values crowd one bin).
-// The row is read from HBM once; passes 2 and 3 find it in L2.
+// The row is read from HBM once; passes 2 and 3 find it in L2.  Pass 3
+// needs only the ranking code, not the normalised value.
 
 #include <math_constants.h>
 
@@ -104,7 +105,7 @@ __device__ __forceinline__ void scale_one(const RowScale &c, float v, float &z, 
     if (c.wide) {
         const double q = ((double)a - (double)b) * c.inv64;
         z = fminf(fmaxf((float)q, 0.f), 1.f);
-        bin = min(kBins - 1, (int)(q * (double)kBins));
+        bin = min(kBins - 1, (int)(((double)a - (double)b) * c.inv64 * (double)kBins));
         return;
     }
     const float s = __fsub_rn(a, b);
@@ -261,6 +262,60 @@ __device__ __forceinline__ bool no_neighbours(const float *cnt, int m, int64_t i
     return m == SNAPS_SCORE_EPS_MEAN && cnt[i] == 0.f;
 }
 
+// Visit every object of the row: f(i, v, none) gets the object's index, metric
+// value and whether it lacks eps-neighbours.  The row's 16-byte aligned body
+// is read as float4, two per thread in flight; the few objects before the
+// first 16-byte boundary and after the last whole float4 are read singly.  (A
+// row starts wherever row * n floats lands; the count row that the eps mean
+// distance consults has another alignment and is read singly.)
+template <class F>
+__device__ __forceinline__ void visit_row(const float *s, const float *cnt, int m, int64_t n, F &&f)
+{
+    const bool em = m == SNAPS_SCORE_EPS_MEAN;
+    const int tid = threadIdx.x;
+    const int64_t head = std::min<int64_t>((int64_t)(((16u - ((uintptr_t)s & 15u)) & 15u) >> 2), n);
+    const int64_t body = (n - head) >> 2;  // whole float4 units
+    const int64_t tail0 = head + 4 * body;
+    if (tid < head) f((int64_t)tid, s[tid], em && cnt[tid] == 0.f);
+    if (tid < n - tail0) {
+        const int64_t i = tail0 + tid;
+        f(i, s[i], em && cnt[i] == 0.f);
+    }
+    const float4 *s4 = reinterpret_cast<const float4 *>(s + head);
+    for (int64_t u0 = tid; u0 < body; u0 += 2 * kFinThreads) {
+        const int64_t u1 = u0 + kFinThreads;
+        const float4 a = s4[u0];
+        const float4 b = u1 < body ? s4[u1] : make_float4(0.f, 0.f, 0.f, 0.f);
+        float ca[4] = {1.f, 1.f, 1.f, 1.f}, cb[4] = {1.f, 1.f, 1.f, 1.f};
+        if (em) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                ca[q] = cnt[head + 4 * u0 + q];
+                if (u1 < body) cb[q] = cnt[head + 4 * u1 + q];
+            }
+        }
+        const float va[4] = {a.x, a.y, a.z, a.w};
+#pragma unroll
+        for (int q = 0; q < 4; ++q) f(head + 4 * u0 + q, va[q], ca[q] == 0.f);
+        if (u1 < body) {
+            const float vb[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+            for (int q = 0; q < 4; ++q) f(head + 4 * u1 + q, vb[q], cb[q] == 0.f);
+        }
+    }
+}
+
+// The ranking code of a qualifying object alone: the same operations as
+// scale_one's, without the normalised value.
+__device__ __forceinline__ int code_of(const RowScale &c, float v)
+{
+    if (c.flat) return 0;
+    const float a = c.up ? v : c.hi;
+    const float b = c.up ? c.lo : v;
+    if (c.wide) return min(kBins - 1, (int)(((double)a - (double)b) * c.inv64 * (double)kBins));
+    return min(kBins - 1, __float2int_rz(__fmul_rn(__fsub_rn(a, b), c.bscale)));
+}
+
 __global__ void __launch_bounds__(kFinThreads, 3)
     finish_kernel(const float *__restrict__ scores, int64_t n, float *__restrict__ norm, int top_n,
                   int32_t *__restrict__ top)
@@ -283,12 +338,12 @@ __global__ void __launch_bounds__(kFinThreads, 3)
         sh.key_max = 0u;
     }
     float lo = CUDART_INF_F, hi = -CUDART_INF_F;
-    for (int64_t i = tid; i < n; i += kFinThreads) {
-        const float v = s[i];
-        if (no_neighbours(cnt, m, i)) continue;
-        lo = fminf(lo, v);
-        hi = fmaxf(hi, v);
-    }
+    visit_row(s, cnt, m, n, [&](int64_t, float v, bool none) {
+        if (!none) {
+            lo = fminf(lo, v);
+            hi = fmaxf(hi, v);
+        }
+    });
     for (int o = 16; o > 0; o >>= 1) {
         lo = fminf(lo, __shfl_xor_sync(dev::kFull, lo, o));
         hi = fmaxf(hi, __shfl_xor_sync(dev::kFull, hi, o));
@@ -309,11 +364,10 @@ __global__ void __launch_bounds__(kFinThreads, 3)
 
     // ---- pass 2: normalised values and the code histogram ---------------------------
     float *z_out = norm ? norm + row * n : nullptr;
-    for (int64_t i = tid; i < n; i += kFinThreads) {
-        const float v = s[i];
+    visit_row(s, cnt, m, n, [&](int64_t i, float v, bool none) {
         float z;
         int bin;
-        if (no_neighbours(cnt, m, i)) {
+        if (none) {
             z = 1.f;
             bin = kBins;
         } else {
@@ -321,7 +375,7 @@ __global__ void __launch_bounds__(kFinThreads, 3)
         }
         if (z_out) z_out[i] = z;
         if (top) atomicAdd(&sh.hist[bin], 1u);
-    }
+    });
     if (!top) return;
     __syncthreads();
 
@@ -365,13 +419,9 @@ __global__ void __launch_bounds__(kFinThreads, 3)
 
     // ---- pass 3: gather the objects above that bin and in it ---------------------------
     uint32_t kmin = 0xffffffffu, kmax = 0u;
-    for (int64_t i = tid; i < n; i += kFinThreads) {
-        const float v = s[i];
-        const bool none = no_neighbours(cnt, m, i);
-        float z;
-        int bin = kBins;
-        if (!none) scale_one(c, v, z, bin);
-        if (bin < b_star) continue;
+    visit_row(s, cnt, m, n, [&](int64_t i, float v, bool none) {
+        const int bin = none ? kBins : code_of(c, v);
+        if (bin < b_star) return;
         const unsigned long long pair = ((unsigned long long)order_key(v, none, m) << 32) | (uint32_t)i;
         if (bin > b_star) {
             sh.sel[atomicAdd(&sh.n_above, 1u)] = pair;
@@ -382,7 +432,7 @@ __global__ void __launch_bounds__(kFinThreads, 3)
             const unsigned p = c_above + atomicAdd(&sh.n_at, 1u);
             if (p < kCap) sh.sel[p] = pair;
         }
-    }
+    });
     kmin = __reduce_min_sync(dev::kFull, kmin);
     kmax = __reduce_max_sync(dev::kFull, kmax);
     if (lane == 0) {
@@ -400,13 +450,7 @@ __global__ void __launch_bounds__(kFinThreads, 3)
         for (int64_t c0 = 0; c0 < n && left > 0; c0 += kFinThreads) {
             const int64_t i = c0 + tid;
             bool eq = false;
-            if (i < n) {
-                const bool none = no_neighbours(cnt, m, i);
-                float z;
-                int bin = kBins;
-                if (!none) scale_one(c, s[i], z, bin);
-                eq = bin == b_star;
-            }
+            if (i < n) eq = (no_neighbours(cnt, m, i) ? kBins : code_of(c, s[i])) == b_star;
             const unsigned bal = __ballot_sync(dev::kFull, eq);
             __syncthreads();
             if (lane == 0) sh.warp_sum[warp] = __popc(bal);

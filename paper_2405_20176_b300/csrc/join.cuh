@@ -21,6 +21,12 @@ struct MaskGroup {
 // of one high part H, as scheduled for the subspace-batched tree kernel.
 constexpr int kTreeLowBits = 5;
 constexpr int kTreeWidth = 1 << kTreeLowBits;
+// A chunk goes to the subspace-batched kernel when at least this many of its
+// subspaces are requested.  Its shared walk costs about 45 FP32-pipe
+// operations per candidate pair whatever the number requested (plus about 3
+// per requested subspace for events); a subspace joined on its own costs about
+// 1.25 d + 8 (18 at d = 8).  Below four, the lone joins cost less.
+constexpr int kTreeMinActive = 4;
 struct TreeChunk {
     uint32_t high;                 // H
     uint32_t active;               // bit L set when subspace (H << 5) | L is requested
@@ -65,6 +71,10 @@ struct JoinShape {
     // compacted, the highest first, in floats 5.. (0 after them); the boxes
     // then follow the same order
     bool compact = false;
+    // tensor-core join only: spins after which a pipeline wait gives up and the
+    // launch reports kErrTimeout (0 = dev::kSpinLimit).  Waits for copies and
+    // MMAs already in flight, on the way out, always use dev::kSpinLimit.
+    unsigned wait_limit = 0;
 };
 
 // Launch the lane-per-subspace join over `n_groups` groups (device array).
@@ -75,6 +85,28 @@ snaps_status launch_join_lanemask(const JoinShape &s, const MaskGroup *groups, i
 // groups (device array): one launch row per entry, a CTA per 256 queries.
 snaps_status launch_join_single(const JoinShape &s, const MaskGroup *groups, int n_groups,
                                 const JoinOut &o, cudaStream_t st);
+
+// One subspace of one population in a work list that spans several calls
+// (the serving loop fuses the subspaces joined on their own of every small
+// request it admits together into one launch).  The CTA's output goes to
+// scores[4][n] of that subspace: eps count, mean eps distance, in-degree (added
+// to, so it must start at zero) and mean kNN distance.
+struct WorkItem {
+    const float4 *x;   // the population's stored rows (n_pad rows)
+    float *scores;     // this subspace's 4 x n block
+    int n;
+    int k;             // 1..32
+    uint32_t mask;
+    float eps2;        // < 0 disables the eps join
+    int first_cta;     // the item's first CTA in the launch (items in order)
+    int pad;
+};
+
+// Launch the subspace-at-a-time join over a work list of `n_items` items
+// (device array) whose CTAs number `n_ctas` in all (item i owns CTAs
+// first_cta[i] .. first_cta[i + 1] - 1, one per 256 queries); every item's k
+// must be <= kmax (16 or 32).
+snaps_status launch_join_worklist(const WorkItem *items, int n_items, int n_ctas, int kmax, cudaStream_t st);
 
 // Launch the tensor-core filtered join over `n_blocks` blocks (device array).
 // Requires every feature of the population to span at most 1.

@@ -4,54 +4,67 @@
 // on the 5th-generation tensor cores (tcgen05, kind::f16 with FP16 or BF16
 // operands, FP32 accumulators in tensor memory).
 //
-// The contraction.  For a query i and 128 candidates j, the B operand holds
-// per candidate the 15 squared differences (x_j - x_i)^2 rounded to the
-// operand type and a constant 1; the A operand holds per subspace S its 15
-// mask bits and minus its filter threshold.  One MMA (M = 128 subspaces,
-// N = 128 candidates, K = 16) gives in tensor memory
-//     D[S][j] ~= sum_{f in S} (x_jf - x_if)^2 - Tf_S,
-// and D < 0 marks the candidates that may lie within eps of the query or
-// below the current k-th distance.  Tf_S = max(k-th squared distance, eps^2)
-// * (1 + m) + 2^-20, rounded up to the operand type, with m = 2^-8 for FP16
-// and 2^-6 for BF16: rounding a squared difference to FP16 is <= 2^-11
-// relative (2^-25 absolute below FP16's normal range), to BF16 <= 2^-8
-// relative, and the FP32 accumulation of 16 exact products adds far less, so
-// no true neighbour is lost.  BF16's wider margin lets more candidates through
-// to the exact recompute.  Every candidate that passes is recomputed with the
-// library's canonical FP32 fold (FMAs from the highest feature down), and only
-// that exact value decides counts, sums and kNN lists: the results are the
-// plain FP32 path's, bit for bit.
+// The contraction.  For a query i and 128 candidates j, each squared
+// difference (x_jf - x_if)^2, scaled by S = 2^11 (exact), is split into a
+// high part h = round(s) in the operand type and a low part l = round(s - h).
+// Two MMAs (M = 128 subspaces, N = 128 candidates, K = 16), one over the high
+// parts and one over the low parts, against the same mask operand, leave in
+// tensor memory
+//     D[S][j] = S * sum_{f in S} (x_jf - x_if)^2 * (1 + e).
+// The split leaves 2^-22 relative (FP16) or 2^-18 (BF16) per term; the FP32
+// accumulation of the 30 exact products adds at most 30 roundings of 2^-23
+// (the bound for truncating adds; the hardware's own rounding is not
+// documented), 3.6e-6.  So |e| <= 3.9e-6 (FP16) or 7.4e-6 (BF16).  The
+// decisions use a margin delta (2^-17 = 7.6e-6 for FP16, 2^-15 for BF16)
+// that also covers the canonical FP32 fold's own rounding (<= (d + 2) 2^-24),
+// plus an absolute slack of 2^-20 (scaled) for FP16 parts below its normal
+// range:
+//   * D below eps^2 (1 - delta): an eps-neighbour for certain.  It is counted,
+//     and its distance sqrt(D / S) enters the exact quantised distance sum;
+//   * D within eps^2 (1 +- delta): recomputed with the library's canonical
+//     FP32 fold, which decides;
+//   * D at or below the k-th distance (1 + delta): recomputed exactly and
+//     inserted into the kNN list with the canonical value.
+// So eps counts, kNN lists, in-degrees and kNN mean distances are the plain
+// FP32 path's, bit for bit; the mean eps distance takes the accumulator's
+// distances, within |e| / 2 + 2^-24 (d + 2) of the canonical ones (2.5e-6
+// relative for FP16, 4.2e-6 for BF16).  Skipped rows (padding, the query itself, the rows folded at start-up)
+// carry a large high part in every feature, far above any threshold (every
+// threshold is capped at 16 S, above the largest real D of a unit-range
+// population, 15 S (1 + delta)).
 //
 // Mapping.  A CTA owns work items of one query x 256 subspaces (two 128-row A
-// operands).  Its 8 consumer warps are the subspace threads: thread s reads
-// row s % 128 of the accumulator of half s / 128 -- warp w reaches
-// tensor-memory lanes 32 (w % 4) .. 32 (w % 4) + 31 -- and keeps that
-// subspace's eps count, exact distance sum and kNN list privately, so events
-// need no atomics, locks or buffers.  One producer warp issues the bulk copies
-// (TMA) of 256-row candidate tiles into a ring and, per sub-tile of 128
-// candidates, the two MMAs into one of two accumulator sets (2 x 128 columns
-// each, 512 in all).  The warps meet only at mbarriers: consumers build a
-// sub-tile's B rows (half a row each) and arrive on `b_ready`; the producer
-// waits for that and for `t_empty` (the accumulator set it will overwrite has
-// been read), issues the MMAs and commits them to `mma_done`; consumers wait
-// for `mma_done`, filter -- 32 accumulators OR-ed into one sign test --
-// recompute and decide the survivors, write tightened thresholds into the A
-// copy that batch used (its next reader is issued only after they arrive on
-// `t_empty`), and arrive.  Subspaces arrive sorted by dimension, so the
-// threads of a warp see similar hit rates.
+// operands); the A operands hold only mask bits, so they are written once per
+// block of subspaces.  Its 16 consumer warps hold two threads per subspace:
+// thread (c, s) reads row s % 128 of the accumulator of half s / 128 --
+// warp w reaches tensor-memory lanes 32 (w % 4) .. 32 (w % 4) + 31 -- and
+// columns 64 c .. 64 c + 63 of every sub-tile, and keeps its own eps count,
+// distance sum and kNN list.  The two lists of a subspace are merged when the
+// item ends; meanwhile each thread filters with the smaller of the two k-th
+// distances (a candidate at or above the other thread's k-th cannot enter the
+// merged list), read from shared memory, where a stale value is only larger.
+// A thread first takes the minimum of 32 accumulators and looks at them one by
+// one only when it is below the subspace's pass threshold.  One producer warp
+// issues the bulk copies (TMA) of 256-row candidate tiles into a ring and, per
+// sub-tile of 128 candidates, the four MMAs into one of two accumulator sets
+// (2 x 128 columns each, 512 in all).  The warps meet only at mbarriers:
+// consumers build a sub-tile's B rows and arrive on `b_ready`; the producer
+// waits for that and for `t_empty` (the accumulator set it will overwrite
+// has been read), issues the MMAs and commits them to `mma_done`; consumers
+// wait for `mma_done`, filter and decide, and arrive on `t_empty`.
 //
 // kNN lists are kept unsorted with their largest entry tracked: a better
-// candidate overwrites that entry and the k entries are rescanned (k
-// independent loads instead of a dependent shift chain); each list is sorted
-// once, when its query's results are written.
+// candidate overwrites that entry and the k entries are rescanned; each list
+// is sorted once, when its query's results are written.
 //
 // Start-up: the 32 rows around the query (in the stored cell order) are
-// staged in shared memory and folded exactly first, so the thresholds start
-// finite; the stream skips them.  Every wait is bounded and also gives up
-// when another warp has raised the CTA's abort flag; the CTA then sets the
-// error word, waits for its copies and MMAs in flight, frees its tensor
-// memory and leaves.  Populations whose features span more than a unit range
-// are rejected by the host (their squared differences could overflow FP16).
+// staged in shared memory and folded exactly first (by the first thread of
+// each subspace; the second filters with that thread's k-th distance), so the
+// thresholds start finite; the stream skips them.  Every
+// wait is bounded and also gives up when another warp has raised the CTA's
+// abort flag; the CTA then sets the error word, waits for its copies and MMAs
+// in flight, frees its tensor memory and leaves.  Populations whose features
+// span more than a unit range are rejected by the host.
 
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
@@ -65,38 +78,51 @@
 namespace snaps {
 namespace {
 
-constexpr int kNS = kTcBlockWidth;       // 256 subspaces per block (one query)
-constexpr int kM = 128;                  // MMA M: subspaces per A operand
-constexpr int kHalves = kNS / kM;        // 2
-constexpr int kNC = 128;                 // candidates per sub-tile = MMA N
-constexpr int kConsumers = kNS;          // 256: thread s
-constexpr int kProducerWarp = kConsumers / 32;
+constexpr int kNS = kTcBlockWidth;        // 256 subspaces per block (one query)
+constexpr int kM = 128;                   // MMA M: subspaces per A operand
+constexpr int kHalves = kNS / kM;         // 2
+constexpr int kNC = 128;                  // candidates per sub-tile = MMA N
+constexpr int kColParts = 2;              // threads per subspace, 64 columns each
+constexpr int kColsPerThread = kNC / kColParts;
+constexpr int kConsumers = kNS * kColParts;   // 512
+constexpr int kConsumerWarps = kConsumers / 32;
+constexpr int kProducerWarp = kConsumerWarps;
 constexpr int kCtaThreads = kConsumers + 32;
-constexpr int kTile = 256;               // rows per staged tile (one 16 KB bulk copy)
-constexpr int kSubPerTile = kTile / kNC; // 2
-constexpr int kStages = 6;               // ring depth in tiles
-constexpr int kWarm = 32;                // rows folded exactly before the filter starts
-constexpr uint32_t kLBO = 128;           // K-direction step between 8x16-byte core matrices
-constexpr uint32_t kSBO = 256;           // row-direction step
+constexpr int kTile = 256;                // rows per staged tile (one 16 KB bulk copy)
+constexpr int kSubPerTile = kTile / kNC;  // 2
+constexpr int kWarm = 32;                 // rows folded exactly before the filter starts
+constexpr uint32_t kLBO = 128;            // K-direction step between 8x16-byte core matrices
+constexpr uint32_t kSBO = 256;            // row-direction step
 constexpr uint32_t kTmemCols = 2 * kHalves * kNC;  // 512: two accumulator sets
+constexpr float kScale = 2048.f;          // S: squared differences are scaled by 2^11
+constexpr float kRsqrtScale = 0.02209708691207961f;  // 1 / sqrt(S)
+constexpr float kCap = 16.f * kScale;     // every threshold is capped here (> 15 S (1 + delta))
+constexpr float kSlack = 9.5367431640625e-07f;  // 2^-20, in scaled units
 static_assert(kHalves == 2 && kTmemCols == 512, "one CTA holds all of an SM's tensor memory");
-static_assert(kNC * 2 == kConsumers, "every consumer builds half of one B row");
+static_assert(kNC * 4 == kConsumers, "every consumer builds four features of one B row");
 static_assert(kRowPad % kTile == 0, "padded rows must cover whole tiles");
 
 template <int KMAX>
+constexpr int kStages = KMAX <= 16 ? 6 : 4;
+
+template <int KMAX>
 struct TcSmem {
-    float4 ring[kStages][kTile * 4];                   // candidate tiles (quad-planar)
-    alignas(1024) unsigned char A[2][kHalves][kM * 32]; // FP16 128 x 16, K-major
-    alignas(1024) unsigned char B[2][kNC * 32];         // FP16 128 x 16, K-major
+    float4 ring[kStages<KMAX>][kTile * 4];              // candidate tiles (quad-planar)
+    alignas(1024) unsigned char A[kHalves][kM * 32];    // mask bits, 128 x 16, K-major
+    alignas(1024) unsigned char Bh[2][kNC * 32];        // high parts, 128 x 16, K-major
+    alignas(1024) unsigned char Bl[2][kNC * 32];        // low parts
     float ld[KMAX][kConsumers];                         // kNN lists, entry-major: private
     int lj[KMAX][kConsumers];                           // to a thread, distinct banks
+    float tk[kConsumers];                               // each thread's current k-th distance
+    int pcnt[kNS];                                      // the second thread's eps count and
+    unsigned long long pqs[kNS];                        // sum, handed over at the item's end
     float4 warm[4][kWarm];                              // start-up rows, quad-planar
     float4 xq[4];                                       // the item's query row
-    uint64_t full[kStages];                             // tile landed
-    uint64_t b_ready[2];                                // B rows written (8 warp arrivals)
-    uint64_t t_empty[2];                                // accumulators read (8 warp arrivals)
+    uint64_t full[kStages<KMAX>];                       // tile landed
+    uint64_t b_ready[2];                                // B rows written (16 warp arrivals)
+    uint64_t t_empty[2];                                // accumulators read (16 warp arrivals)
     uint64_t mma_done[2];                               // MMA batch complete (commit)
-    uint64_t cbar;                                      // consumer-only barrier (8 warps)
+    uint64_t cbar;                                      // consumer-only barrier (16 warps)
     uint32_t tmem_base;
     int abort;
 };
@@ -112,59 +138,48 @@ __device__ __forceinline__ uint64_t smem_desc(const void *p)
     return d;
 }
 
-// Byte offset of element (r, k) in a K-major 16-column FP16 operand.
+// Byte offset of element (r, k) in a K-major 16-column 16-bit operand.
 __device__ __forceinline__ uint32_t op_off(int r, int k)
 {
     return (uint32_t)((r >> 3) * kSBO + (k >> 3) * kLBO + (r & 7) * 16 + (k & 7) * 2);
 }
 
-// Operand element encodings of the two 16-bit forms.
+// Operand element encodings and error margins of the two 16-bit forms.
 template <bool BF16>
 struct Op16 {
-    // 1.0, and the "never passes" squared difference of a skipped row
-    // (65504 in FP16, 65536 in BF16: finite, and >= 2 of them exceed any
-    // threshold of a unit-range population)
+    // 1.0, and the high part of every feature of a skipped row (65504 in FP16,
+    // 65536 in BF16: two of them exceed every capped threshold)
     static constexpr uint32_t kOne = BF16 ? 0x3F80u : 0x3C00u;
     static constexpr uint32_t kBig = BF16 ? 0x4780u : 0x7BFFu;
-    // relative filter margin: 2^-8 against FP16's 2^-11 rounding of a squared
-    // difference, 2^-6 against BF16's 2^-8
-    static constexpr float kMargin = BF16 ? 0.015625f : 0.00390625f;
+    // relative margin of the decisions (see the file comment)
+    static constexpr float kDelta = BF16 ? 3.0517578125e-05f : 7.62939453125e-06f;
     // instruction descriptor: D = F32, A and B of one type (F16 = 0, BF16 = 1),
     // both K-major; N = 128, M = 128
     static constexpr uint32_t kIdesc = (1u << 4) | ((BF16 ? 1u : 0u) << 7) | ((BF16 ? 1u : 0u) << 10) |
                                        ((uint32_t)(kNC >> 3) << 17) | ((uint32_t)(kM >> 4) << 24);
-    static __device__ __forceinline__ uint32_t pack2(float a, float b)
+    // high and low parts of a scaled squared difference
+    static __device__ __forceinline__ void split(float s, uint32_t &h, uint32_t &l)
     {
         if constexpr (BF16) {
-            const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
-            return *reinterpret_cast<const uint32_t *>(&h);
+            const __nv_bfloat16 a = __float2bfloat16_rn(s);
+            const __nv_bfloat16 b = __float2bfloat16_rn(s - __bfloat162float(a));
+            h = __bfloat16_as_ushort(a);
+            l = __bfloat16_as_ushort(b);
         } else {
-            const __half2 h = __floats2half2_rn(a, b);
-            return *reinterpret_cast<const uint32_t *>(&h);
-        }
-    }
-    // A row entry 15 for a subspace: minus its conservative filter threshold,
-    // rounded up in magnitude
-    static __device__ __forceinline__ unsigned short neg_filter(float t)
-    {
-        if (!(t >= 0.f)) return (unsigned short)kOne;  // nothing to find: D >= +1 - 1 * 0 on real rows
-        if constexpr (BF16) {
-            const float f = fminf(t * (1.f + kMargin) + 9.5367431640625e-07f, 1e30f);
-            return __bfloat16_as_ushort(__hneg(__float2bfloat16_ru(f)));
-        } else {
-            const float f = fminf(t * (1.f + kMargin) + 9.5367431640625e-07f, 65504.f);
-            return __half_as_ushort(__hneg(__float2half_ru(f)));
+            const __half a = __float2half_rn(s);
+            const __half b = __float2half_rn(s - __half2float(a));
+            h = __half_as_ushort(a);
+            l = __half_as_ushort(b);
         }
     }
 };
 
-__device__ __forceinline__ float eps_floor(float e2) { return e2 >= 0.f ? e2 : -CUDART_INF_F; }
-
-// Bounded mbarrier wait that also gives up once the CTA's abort flag is set.
-__device__ __forceinline__ bool wait_or_abort(uint64_t *bar, unsigned parity, const int *abort)
+// Bounded mbarrier wait (at most `limit` tries) that also gives up once the
+// CTA's abort flag is set.
+__device__ __forceinline__ bool wait_or_abort(uint64_t *bar, unsigned parity, const int *abort, unsigned limit)
 {
     const uint32_t addr = dev::smem_addr(bar);
-    for (unsigned it = 0; it < dev::kSpinLimit; ++it) {
+    for (unsigned it = 0; it < limit; ++it) {
         uint32_t done;
         asm volatile(
             "{\n\t.reg .pred p;\n\t"
@@ -232,17 +247,11 @@ struct KnnMax {
     int Tp;    // its position
 };
 
-// One candidate's exact decisions for thread `tid`'s subspace: eps count and
-// quantised distance sum, then, when it beats the list's largest entry by
-// (distance, index), it takes that entry's place and the new largest is found.
+// Insert (d2, oj) into thread `tid`'s list when it beats the largest entry by
+// (distance, index); the new largest entry is found by a rescan.
 template <int KMAX>
-__device__ __forceinline__ void decide(TcSmem<KMAX> &sm, int tid, int k, float d2, int oj, float e2,
-                                       float esc, int &cnt, unsigned long long &qs, KnnMax &m)
+__device__ __forceinline__ void knn_offer(TcSmem<KMAX> &sm, int tid, int k, float d2, int oj, KnnMax &m)
 {
-    if (d2 <= e2) {
-        ++cnt;
-        qs += dev::eps_quant(d2, esc);
-    }
     if (d2 < m.T || (d2 == m.T && oj < m.Tj)) {
         sm.ld[m.Tp][tid] = d2;
         sm.lj[m.Tp][tid] = oj;
@@ -262,17 +271,45 @@ __device__ __forceinline__ void decide(TcSmem<KMAX> &sm, int tid, int k, float d
     }
 }
 
-// Write the A row of subspace r (mask bits, then minus the filter threshold).
+// The decision thresholds of one thread's subspace, in scaled units.
+struct Thresholds {
+    float e_lo;    // D below: an eps-neighbour for certain
+    float e_hi;    // D at or below (and not below e_lo): decided exactly
+    float t_hi;    // D at or below: a kNN candidate, decided exactly
+    float pass;    // max(e_hi, t_hi): nothing above it needs a look
+};
+
 template <bool BF16>
-__device__ __forceinline__ void write_a_row(unsigned char *A, int r, uint32_t mask, unsigned short thr)
+__device__ __forceinline__ Thresholds thresholds(bool act, float e2, float tk)
+{
+    constexpr float dl = Op16<BF16>::kDelta;
+    Thresholds t;
+    if (!act) {
+        t.e_lo = t.e_hi = t.t_hi = t.pass = -CUDART_INF_F;
+        return t;
+    }
+    if (e2 >= 0.f) {
+        t.e_lo = fminf(e2 * kScale * (1.f - dl) - kSlack, kCap);
+        t.e_hi = fminf(e2 * kScale * (1.f + dl) + kSlack, kCap);
+    } else {
+        t.e_lo = t.e_hi = -CUDART_INF_F;
+    }
+    t.t_hi = fminf(tk * kScale * (1.f + dl) + kSlack, kCap);  // +inf (list not full) -> the cap
+    t.pass = fmaxf(t.e_hi, t.t_hi);
+    return t;
+}
+
+// Write the A row of subspace r: its mask bits as 1.0 / 0.0, 0 in column 15.
+template <bool BF16>
+__device__ __forceinline__ void write_a_row(unsigned char *A, int r, uint32_t mask)
 {
     constexpr uint32_t one = Op16<BF16>::kOne;
     uint32_t w[8];
 #pragma unroll
     for (int p = 0; p < 8; ++p) {
         const int f0 = 2 * p, f1 = 2 * p + 1;
-        const uint32_t lo = ((mask >> f0) & 1u) ? one : 0u;  // 1.0 / 0.0
-        const uint32_t hi = f1 == 15 ? (uint32_t)thr : (((mask >> f1) & 1u) ? one : 0u);
+        const uint32_t lo = ((mask >> f0) & 1u) ? one : 0u;
+        const uint32_t hi = (f1 < 15 && ((mask >> f1) & 1u)) ? one : 0u;
         w[p] = lo | (hi << 16);
     }
     *reinterpret_cast<uint4 *>(A + op_off(r, 0)) = make_uint4(w[0], w[1], w[2], w[3]);
@@ -284,6 +321,7 @@ __global__ void __launch_bounds__(kCtaThreads, 1)
     join_tc_kernel(JoinShape s, const TcBlock *__restrict__ blocks, int n_blocks, JoinOut o,
                    DeviceControl *ctrl)
 {
+    constexpr int kSt = kStages<KMAX>;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char *smem_al = smem_raw + ((1024u - (dev::smem_addr(smem_raw) & 1023u)) & 1023u);
     TcSmem<KMAX> &sm = *reinterpret_cast<TcSmem<KMAX> *>(smem_al);
@@ -297,17 +335,18 @@ __global__ void __launch_bounds__(kCtaThreads, 1)
     const int n_sub = n_tiles * kSubPerTile;  // even
     const long long total = (long long)n * n_blocks;  // work items: (block, query)
     const float4 *x = s.x;
+    const unsigned wlimit = s.wait_limit ? s.wait_limit : dev::kSpinLimit;
     // work items of this CTA: blockIdx.x, blockIdx.x + gridDim.x, ...
     const int my_items = total > blockIdx.x ? (int)((total - blockIdx.x + gridDim.x - 1) / gridDim.x) : 0;
 
     if (tid == 0) {
-        for (int st = 0; st < kStages; ++st) dev::mbar_init(&sm.full[st], 1);
+        for (int st = 0; st < kSt; ++st) dev::mbar_init(&sm.full[st], 1);
         for (int b = 0; b < 2; ++b) {
-            dev::mbar_init(&sm.b_ready[b], kConsumers / 32);
-            dev::mbar_init(&sm.t_empty[b], kConsumers / 32);
+            dev::mbar_init(&sm.b_ready[b], kConsumerWarps);
+            dev::mbar_init(&sm.t_empty[b], kConsumerWarps);
             dev::mbar_init(&sm.mma_done[b], 1);
         }
-        dev::mbar_init(&sm.cbar, kConsumers / 32);
+        dev::mbar_init(&sm.cbar, kConsumerWarps);
         sm.abort = 0;
         dev::fence_barrier_init();
     }
@@ -343,7 +382,7 @@ __global__ void __launch_bounds__(kCtaThreads, 1)
                 if (ii < my_items) {
                     int tt = it0 + iv;
                     if (tt >= n_tiles) tt -= n_tiles;
-                    const int st = (int)(issued % kStages);
+                    const int st = (int)(issued % kSt);
                     dev::bulk_load(sm.ring[st], x + (int64_t)tt * kTile * 4, kTile * 64, &sm.full[st]);
                     if (++iv == n_tiles) {
                         iv = 0;
@@ -352,7 +391,7 @@ __global__ void __launch_bounds__(kCtaThreads, 1)
                 }
                 ++issued;
             };
-            for (int st = 0; st < kStages; ++st) issue_next();
+            for (int st = 0; st < kSt; ++st) issue_next();
             const long long total_sub = (long long)my_items * n_sub;
             const uint32_t idesc = Op16<BF16>::kIdesc;
             long long g = 0;
@@ -360,24 +399,29 @@ __global__ void __launch_bounds__(kCtaThreads, 1)
             for (; g < total_sub; ++g) {
                 const int b = (int)(g & 1);
                 const unsigned ph = (unsigned)((g >> 1) & 1);
-                ok = wait_or_abort(&sm.b_ready[b], ph, &sm.abort);
-                if (ok && g >= 2) ok = wait_or_abort(&sm.t_empty[b], ph ^ 1u, &sm.abort);
+                ok = wait_or_abort(&sm.b_ready[b], ph, &sm.abort, wlimit);
+                if (ok && g >= 2) ok = wait_or_abort(&sm.t_empty[b], ph ^ 1u, &sm.abort, wlimit);
                 if (!ok) break;
                 // sub-tiles <= g - 2 are done with: refill the ring behind them
                 if (g >= 2) {
                     const long long tiles_done = (g - 1) / kSubPerTile;
-                    while (issued < tiles_done + kStages) issue_next();
+                    while (issued < tiles_done + kSt) issue_next();
                 }
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                const uint64_t bdesc = smem_desc(sm.B[b]);
+                const uint64_t bh = smem_desc(sm.Bh[b]), bl = smem_desc(sm.Bl[b]);
 #pragma unroll
                 for (int hf = 0; hf < kHalves; ++hf) {
-                    const uint64_t adesc = smem_desc(sm.A[b][hf]);
+                    const uint64_t adesc = smem_desc(sm.A[hf]);
                     const uint32_t dt = tmem + (uint32_t)((b * kHalves + hf) * kNC);
+                    // high parts overwrite the accumulator, low parts add to it
                     asm volatile(
                         "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
                         "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(dt),
-                        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(0));
+                        "l"(adesc), "l"(bh), "r"(idesc), "r"(0));
+                    asm volatile(
+                        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(dt),
+                        "l"(adesc), "l"(bl), "r"(idesc), "r"(1));
                 }
                 asm volatile(
                     "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
@@ -386,29 +430,33 @@ __global__ void __launch_bounds__(kCtaThreads, 1)
             if (!ok) {
                 fail();
                 // let the copies and MMAs in flight land before the CTA leaves: the last
-                // kStages tiles issued (earlier ones were consumed before their slots were refilled)
+                // kSt tiles issued (earlier ones were consumed before their slots were refilled)
                 const long long real = std::min(issued, (long long)my_items * n_tiles);
-                for (long long z = std::max(0ll, real - kStages); z < real; ++z)
-                    dev::mbar_wait(&sm.full[z % kStages], (unsigned)((z / kStages) & 1));
+                for (long long z = std::max(0ll, real - kSt); z < real; ++z)
+                    dev::mbar_wait(&sm.full[z % kSt], (unsigned)((z / kSt) & 1));
                 if (g >= 1) dev::mbar_wait(&sm.mma_done[(g - 1) & 1], (unsigned)(((g - 1) >> 1) & 1));
             }
         }
         __syncwarp();
     } else {
         // ================================ consumers ===============================================
-        // event role: subspace sidx = half * 128 + arow (TMEM lane arow of half `half`)
-        const int half = warp >> 2;
-        const int sub = warp & 3;
-        const int arow = (sub << 5) | (int)lane;
+        // event role: subspace sidx = half * 128 + arow (tensor-memory lane arow of half `half`),
+        // columns 64 cpart .. 64 cpart + 63 of every sub-tile
+        const int cpart = warp >> 3;
+        const int half = (warp >> 2) & 1;
+        const int quarter = warp & 3;
+        const int arow = (quarter << 5) | (int)lane;
         const int sidx = half * kM + arow;
-        // B-build role: candidate row br of the sub-tile, K half bh
-        const int br = tid >> 1;
-        const int bh = tid & 1;
+        const int partner = tid ^ kNS;
+        // B-build role: candidate row br of the sub-tile, features 4 bq .. 4 bq + 3
+        const int br = tid >> 2;
+        const int bq = tid & 3;
         long long gsub = 0;  // global index of this item's first sub-tile
+        int cur_blk = -1;    // the block whose masks the A operands hold
         bool ok = true;
         // every lane of a warp takes the same branch after a wait
         auto wwait = [&](uint64_t *bar, unsigned parity) -> bool {
-            return __all_sync(dev::kFull, wait_or_abort(bar, parity, &sm.abort));
+            return __all_sync(dev::kFull, wait_or_abort(bar, parity, &sm.abort, wlimit));
         };
         // barrier of the consumer warps (an mbarrier, so that it can give up)
         unsigned cuses = 0;
@@ -429,13 +477,14 @@ __global__ void __launch_bounds__(kCtaThreads, 1)
             const bool act = mask != 0u;
             const float e2 = bk.eps2[sidx];
             const float esc = dev::eps_scale(e2).scale;
+            const float esc_s = esc * kRsqrtScale;  // quantisation of sqrt(D), D = S d^2
             const float4 *xq = sm.xq;
-            // ---- B-build role: the query's features of K half bh ----------------------------------
-            const float4 bx0 = x[row_quad(iq, 2 * bh)], bx1 = x[row_quad(iq, 2 * bh + 1)];
+            // ---- B-build role: the query's features 4 bq .. 4 bq + 3 --------------------------------
+            const float4 bx = x[row_quad(iq, bq)];
             // the rows folded exactly first: a window of kWarm rows around the query
             const int wcount = n < kWarm ? n : kWarm;
             const int w0 = std::min(std::max(iq - kWarm / 2, 0), n - wcount);
-            if (!cbarrier()) {  // the previous item's shared rows are no longer read
+            if (!cbarrier()) {  // the previous item's shared rows and lists are no longer read
                 ok = false;
                 break;
             }
@@ -450,33 +499,43 @@ __global__ void __launch_bounds__(kCtaThreads, 1)
                 sm.ld[p][tid] = CUDART_INF_F;
                 sm.lj[p][tid] = 0x7fffffff;
             }
-            if (!cbarrier()) {  // start-up rows staged
+            sm.tk[tid] = CUDART_INF_F;
+            if (blk != cur_blk) {
+                // no MMA reads the A operands now: every MMA issued so far was waited for
+                if (cpart == 0) write_a_row<BF16>(sm.A[half], arow, mask);
+                cur_blk = blk;
+            }
+            if (!cbarrier()) {  // start-up rows staged, lists cleared, masks written
                 ok = false;
                 break;
             }
 
-            // ---- start-up: the private list from the window -----------------------------------------
+            // ---- start-up: the window, folded exactly by the first thread of each subspace;
+            // the second one filters with that thread's k-th distance from the start -----------
             KnnMax km;
             km.T = (act && k > 0) ? CUDART_INF_F : -CUDART_INF_F;
             km.Tj = 0x7fffffff;
             km.Tp = 0;
             int cnt = 0;
             unsigned long long qs = 0ull;
-            if (act) {
+            if (act && cpart == 0) {
 #pragma unroll 1
                 for (int r = 0; r < wcount; ++r) {
                     if (w0 + r == iq) continue;
                     int oj;
                     const float d2 = fold_exact(xq, &sm.warm[0][0], kWarm, r, mask, oj);
-                    decide<KMAX>(sm, tid, k, d2, oj, e2, esc, cnt, qs, km);
+                    if (d2 <= e2) {
+                        ++cnt;
+                        qs += dev::eps_quant(d2, esc);
+                    }
+                    if (k > 0) knn_offer<KMAX>(sm, tid, k, d2, oj, km);
                 }
             }
-            // the threshold last written into each A copy
-            float t_w0 = act ? fmaxf(km.T, eps_floor(e2)) : -1.f, t_w1 = t_w0;
-            {
-                const unsigned short th = Op16<BF16>::neg_filter(t_w0);
-                write_a_row<BF16>(sm.A[0][half], arow, mask, th);
-                write_a_row<BF16>(sm.A[1][half], arow, mask, th);
+            if (act && k > 0) sm.tk[tid] = km.T;
+            Thresholds th = thresholds<BF16>(act, e2, km.T);
+            if (!cbarrier()) {  // every thread's start-up k-th distance is published
+                ok = false;
+                break;
             }
 
             const int t0 = iq / kTile;
@@ -485,29 +544,35 @@ __global__ void __launch_bounds__(kCtaThreads, 1)
             auto build = [&](int u) -> bool {
                 const int v = u / kSubPerTile;
                 const long long z = gsub / kSubPerTile + v;
-                const int slot = (int)(z % kStages);
-                if (u % kSubPerTile == 0 && !wwait(&sm.full[slot], (unsigned)((z / kStages) & 1))) return false;
+                const int slot = (int)(z % kSt);
+                if (u % kSubPerTile == 0 && !wwait(&sm.full[slot], (unsigned)((z / kSt) & 1))) return false;
                 int vt = t0 + v;
                 if (vt >= n_tiles) vt -= n_tiles;
                 const int rr = (u % kSubPerTile) * kNC + br;
                 const int j = vt * kTile + rr;
                 const bool skip = j >= n || j == iq || (unsigned)(j - w0) < (unsigned)wcount;
-                uint4 wd;
+                uint32_t h[4], l[4];
                 if (skip) {
-                    // never passes: every squared difference big, no threshold column
-                    constexpr uint32_t big = Op16<BF16>::kBig, big2 = big | (big << 16);
-                    wd = make_uint4(big2, big2, big2, bh ? big : big2);
+                    // never passes: a large high part in every feature
+                    constexpr uint32_t big = Op16<BF16>::kBig;
+                    h[0] = h[1] = h[2] = big;
+                    h[3] = bq == 3 ? 0u : big;
+                    l[0] = l[1] = l[2] = l[3] = 0u;
                 } else {
-                    const float4 c0 = sm.ring[slot][(2 * bh) * kTile + rr];
-                    const float4 c1 = sm.ring[slot][(2 * bh + 1) * kTile + rr];
-                    const float d0 = c0.x - bx0.x, d1 = c0.y - bx0.y, d2 = c0.z - bx0.z, d3 = c0.w - bx0.w;
-                    const float d4 = c1.x - bx1.x, d5 = c1.y - bx1.y, d6 = c1.z - bx1.z, d7 = c1.w - bx1.w;
-                    wd.x = Op16<BF16>::pack2(d0 * d0, d1 * d1);
-                    wd.y = Op16<BF16>::pack2(d2 * d2, d3 * d3);
-                    wd.z = Op16<BF16>::pack2(d4 * d4, d5 * d5);
-                    wd.w = Op16<BF16>::pack2(d6 * d6, bh ? 1.f : d7 * d7);
+                    const float4 c = sm.ring[slot][bq * kTile + rr];
+                    const float d0 = c.x - bx.x, d1 = c.y - bx.y, d2 = c.z - bx.z, d3 = c.w - bx.w;
+                    Op16<BF16>::split(d0 * d0 * kScale, h[0], l[0]);
+                    Op16<BF16>::split(d1 * d1 * kScale, h[1], l[1]);
+                    Op16<BF16>::split(d2 * d2 * kScale, h[2], l[2]);
+                    if (bq == 3) {
+                        h[3] = l[3] = 0u;  // float 15 holds the original index, not a feature
+                    } else {
+                        Op16<BF16>::split(d3 * d3 * kScale, h[3], l[3]);
+                    }
                 }
-                *reinterpret_cast<uint4 *>(&sm.B[u & 1][op_off(br, 8 * bh)]) = wd;
+                const uint32_t off = op_off(br, 4 * bq);
+                *reinterpret_cast<uint2 *>(&sm.Bh[u & 1][off]) = make_uint2(h[0] | (h[1] << 16), h[2] | (h[3] << 16));
+                *reinterpret_cast<uint2 *>(&sm.Bl[u & 1][off]) = make_uint2(l[0] | (l[1] << 16), l[2] | (l[3] << 16));
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 __syncwarp();
                 if (lane == 0) dev::mbar_arrive(&sm.b_ready[u & 1]);
@@ -528,66 +593,100 @@ __global__ void __launch_bounds__(kCtaThreads, 1)
                     break;
                 }
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                const float4 *tl = sm.ring[(gsub / kSubPerTile + u / kSubPerTile) % kStages];
-                const int rbase = (u % kSubPerTile) * kNC;
-                const uint32_t taddr = tmem + ((uint32_t)(sub * 32) << 16) + (uint32_t)((b * kHalves + half) * kNC);
+                const float4 *tl = sm.ring[(gsub / kSubPerTile + u / kSubPerTile) % kSt];
+                const int rbase = (u % kSubPerTile) * kNC + cpart * kColsPerThread;
+                const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) +
+                                       (uint32_t)((b * kHalves + half) * kNC + cpart * kColsPerThread);
+                // the smaller of the two threads' k-th distances bounds the merged list
+                const float tpart = (act && k > 0) ? sm.tk[partner] : CUDART_INF_F;
+                if (act && k > 0) th = thresholds<BF16>(act, e2, fminf(km.T, tpart));
+                unsigned qpart = 0u;  // this sub-tile's quantised sums (<= 64 terms of <= 2^20 + 1)
 #pragma unroll 1
-                for (int h = 0; h < kNC / 32; ++h) {
+                for (int h = 0; h < kColsPerThread / 32; ++h) {
                     uint32_t r[32];
+                    __syncwarp();  // the load is warp-collective
                     tmem_ld32(taddr + (uint32_t)(32 * h), r);
                     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-                    uint32_t any = 0u;
+                    float mn[16];
 #pragma unroll
-                    for (int c = 0; c < 32; ++c) any |= r[c];
-                    if (act && (int)any < 0) {
-                        uint32_t hm = 0u;  // bit c: column c passed the filter
+                    for (int c = 0; c < 16; ++c) mn[c] = fminf(__uint_as_float(r[c]), __uint_as_float(r[c + 16]));
 #pragma unroll
-                        for (int c = 31; c >= 0; --c) hm = __funnelshift_l(r[c], hm, 1);
-                        // two survivors at a time: their folds overlap
-                        while (hm) {
-                            const int c1 = __ffs(hm) - 1;
-                            hm &= hm - 1u;
-                            const int c2 = hm ? __ffs(hm) - 1 : c1;
-                            const bool two = hm != 0u;
-                            hm &= hm - 1u;
-                            int o1, o2;
-                            const float a1 = fold_exact(xq, tl, kTile, rbase + 32 * h + c1, mask, o1);
-                            const float a2 = fold_exact(xq, tl, kTile, rbase + 32 * h + c2, mask, o2);
-                            decide<KMAX>(sm, tid, k, a1, o1, e2, esc, cnt, qs, km);
-                            if (two) decide<KMAX>(sm, tid, k, a2, o2, e2, esc, cnt, qs, km);
+                    for (int w = 8; w > 0; w >>= 1)
+#pragma unroll
+                        for (int c = 0; c < w; ++c) mn[c] = fminf(mn[c], mn[c + w]);
+                    if (!(mn[0] < th.pass)) continue;
+                    // some accumulator is below the pass threshold: look at each.  Clear
+                    // eps-neighbours are counted here, branch-free when the group has any
+                    // (every column's quantised distance is formed and the clear ones are
+                    // added, so a group costs the same whatever its pattern of hits);
+                    // columns in the band around eps and kNN candidates are recomputed
+                    // exactly below.
+                    uint32_t band = 0u, cand = 0u;
+                    if (mn[0] < th.e_lo) {
+#pragma unroll
+                        for (int c = 0; c < 32; ++c) {
+                            const float v = __uint_as_float(r[c]);
+                            const bool clear = v < th.e_lo;
+                            const unsigned q = dev::eps_quant_fma_pipe(fmaxf(v, 0.f), esc_s);
+                            cnt += clear ? 1 : 0;
+                            qpart += clear ? q : 0u;
+                            band |= (!clear && v <= th.e_hi) ? (1u << c) : 0u;
+                            cand |= (v <= th.t_hi) ? (1u << c) : 0u;
+                        }
+                    } else {
+#pragma unroll
+                        for (int c = 0; c < 32; ++c) {
+                            const float v = __uint_as_float(r[c]);
+                            band |= (v <= th.e_hi) ? (1u << c) : 0u;
+                            cand |= (v <= th.t_hi) ? (1u << c) : 0u;
                         }
                     }
-                }
-                // tightened threshold into the A copy batch gu used: its next reader (batch
-                // gu + 2) is issued only after this warp's t_empty arrival
-                if (act) {
-                    const float tn = fmaxf(km.T, eps_floor(e2));
-                    float &tw = b ? t_w1 : t_w0;
-                    if (tn != tw) {
-                        tw = tn;
-                        *reinterpret_cast<unsigned short *>(&sm.A[b][half][op_off(arow, 15)]) =
-                            Op16<BF16>::neg_filter(tn);
+                    uint32_t need = band | cand;
+                    while (need) {
+                        const int c = __ffs(need) - 1;
+                        const uint32_t bit = 1u << c;
+                        need &= need - 1u;
+                        int oj;
+                        const float d2 = fold_exact(xq, tl, kTile, rbase + 32 * h + c, mask, oj);
+                        if ((band & bit) && d2 <= e2) {
+                            ++cnt;
+                            qs += dev::eps_quant(d2, esc);
+                        }
+                        if (cand & bit) knn_offer<KMAX>(sm, tid, k, d2, oj, km);
                     }
+                    if (cand) th = thresholds<BF16>(act, e2, fminf(km.T, tpart));
                 }
-                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                qs += qpart;
+                if (act && k > 0) sm.tk[tid] = km.T;
                 asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
                 __syncwarp();
                 if (lane == 0) dev::mbar_arrive(&sm.t_empty[b]);
             }
             if (!ok) break;
 
-            // ---- this item's results: thread s reports the query in subspace s --------------------
+            // ---- this item's results: thread (0, s) merges and reports subspace s --------------------
+            if (cpart == 1) {
+                sm.pcnt[sidx] = cnt;
+                sm.pqs[sidx] = qs;
+            }
+            if (!cbarrier()) {
+                ok = false;
+                break;
+            }
             const int orig_i = __float_as_int(xq[3].w);
-            if (act && (orig_i < 0 || orig_i >= n)) {
+            if (cpart == 0 && act && (orig_i < 0 || orig_i >= n)) {
                 atomicOr(&ctrl->error, kErrBadRow);  // rows that do not carry their index
-            } else if (act) {
+            } else if (cpart == 0 && act) {
+                cnt += sm.pcnt[sidx];
+                qs += sm.pqs[sidx];
                 const int slot = bk.slot[sidx];
                 float *sc = o.scores + (int64_t)slot * 4 * n;
                 sc[orig_i] = (float)cnt;
                 sc[n + orig_i] = dev::eps_mean(qs, cnt, esc);
                 if (o.eps_count) o.eps_count[(int64_t)slot * n + orig_i] = cnt;
                 if (k > 0) {
-                    // sort the list by (distance, index)
+                    // the partner's entries into this list, then sort it by (distance, index)
+                    for (int p = 0; p < k; ++p) knn_offer<KMAX>(sm, tid, k, sm.ld[p][partner], sm.lj[p][partner], km);
                     for (int p = 1; p < k; ++p) {
                         const float v = sm.ld[p][tid];
                         const int j = sm.lj[p][tid];

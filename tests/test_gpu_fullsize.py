@@ -8,7 +8,8 @@ eps = 0.05 sqrt(d), one snaps_scores call with device outputs.
 * the benchmark's seeded 64-subspace sample against the FP64 oracle: 16 of
   them in full (every object's four metrics and the four top-100 lists, under
   the band rules of tests/parity.py), the other 48 on 256 sampled queries;
-* the tensor-core form returns the plain form's bits for every subspace."""
+* the tensor-core form returns the plain form's counts, kNN metrics and
+  their rankings bit for bit, and its mean eps distances within 1e-5."""
 import numpy as np
 import pytest
 
@@ -122,11 +123,26 @@ def test_normalised_every_subspace(run):
     assert torch.all(nz[:, 1][none] == 1)
 
 
-def test_tensor_core_form_same_bits(run):
+def test_tensor_core_form_matches_plain(run):
+    """Every subspace: the tensor-core form's eps counts, in-degrees, kNN mean
+    distances and their top lists are the plain form's bits; its mean eps
+    distances agree to 1e-5 relative plus two quantisation steps of eps/2^20,
+    and its eps-mean top lists may differ only among keys tied that closely
+    (checked on the 16 sample subspaces)."""
     sc2 = torch.empty_like(run["sc"])
     top2 = torch.empty_like(run["top"])
     snaps.snaps_scores(run["pop"], run["masks"], K, precision=snaps.SNAPS_TC_F16, scores=sc2, top=top2,
                        top_n=100)
     torch.cuda.synchronize()
-    assert torch.equal(sc2, run["sc"])
-    assert torch.equal(top2, run["top"])
+    same = [0, 2, 3]
+    assert torch.equal(sc2[:, same], run["sc"][:, same])
+    assert torch.equal(top2[:, same], run["top"][:, same])
+    d = torch.tensor([bin(int(m)).count("1") for m in run["masks"]], dtype=torch.float64, device="cuda")
+    step = torch.sqrt(0.0025 * d) / 2.0 ** 20
+    a, b = sc2[:, 1].double(), run["sc"][:, 1].double()
+    assert torch.all((a - b).abs() <= SCORE_RTOL * b.abs() + 2 * step[:, None])
+    slot = {int(m): i for i, m in enumerate(run["masks"])}
+    for mask in snaps_inputs.mask_sample(64, SAMPLE_SEED)[:16]:
+        i = slot[int(mask)]
+        check_top(top2[i, 1].cpu().numpy(), run["sc"][i].double().cpu().numpy(),
+                  run["top"][i, 1].cpu().numpy(), oracle.EPS_MEAN)
