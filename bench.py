@@ -108,6 +108,10 @@ def parse():
     ap.add_argument("--serving-leg", type=int, default=60, metavar="R",
                     help="after the batching legs (one GPU), a Poisson stream of R requests through "
                          "both join forms, reported as the line's `serving` object (0: skip)")
+    ap.add_argument("--by-dimension", action="store_true",
+                    help="instead of the batching workload, time one call over 256 seeded subspaces of each "
+                         "dimension (all of them where fewer exist) through the tensor-core form and the "
+                         "plain form, N = --n objects")
     ap.add_argument("--serving-max-n", type=int, default=100000)
     ap.add_argument("--serving-max-masks", type=int, default=64)
     ap.add_argument("--serving-slots", type=int, default=4)
@@ -266,6 +270,7 @@ def run_ours(args, rank, world, dist):
                 ev[s][1].record(stream)
             barrier()
         trace = snaps.snaps_trace_read(ctx)
+        trace["_steps"] = snaps.snaps_trace_steps(ctx)
         snaps.snaps_trace(ctx, False)
         for p in pops:
             snaps.snaps_release(p)
@@ -278,7 +283,7 @@ def run_ours(args, rank, world, dist):
     evals_per_step = float(n) * (n - 1) * m
     props = torch.cuda.get_device_properties(local)
     max_mhz = clocks["sm_max_mhz"] or 2032.0
-    launches = int(sum(v[1] for v in trace.values()))
+    launches = int(sum(v[1] for kn, v in trace.items() if not kn.startswith("_")))
 
     def alu_roofline(trace, steps):
         """ALU roofline of the plain path's dominant join kernel: one FP32 compare per
@@ -291,8 +296,15 @@ def run_ours(args, rank, world, dist):
         achieved = evals_per_step * steps / (dom_ms / 1e3) / 1e12 if dom_ms > 0 else None
         measured_alu = snaps.snaps_calibrate_alu(local) / 1e12
         traffic = TREE_DRAM_BYTES_PER_EVAL * evals_per_step if dominant == "join_tree" else None
+        loaded, total_steps = trace["_steps"]
+        executed = loaded / total_steps if (dominant == "join_tree" and total_steps) else None
         return {"bound": "alu", "kernel": dominant, "achieved": achieved, "peak": peak,
                 "unit": "Tevals/s", "frac": (achieved / peak) if achieved else None, "traffic": traffic,
+                "executed_fraction": executed,
+                "frac_executed": (achieved * executed / peak) if (achieved and executed) else None,
+                "executed_basis": "64-row steps of the candidate streams loaded and evaluated over all steps "
+                                  "(the rest skipped by their box bound, which proves every pair fails), "
+                                  "counted by the kernel during the timed steps",
                 "traffic_basis": "DRAM bytes per launch: an ncu capture of one 32-subspace chunk (11.8 MB for "
                                  "3.2e10 evaluations) scaled by the launch's evaluations",
                 "peak_basis": f"{props.multi_processor_count} SMs x {COMPARES_PER_SM_CLK} FP32 "
@@ -333,8 +345,9 @@ def run_ours(args, rank, world, dist):
                   "vs_plain": (tc_units / (tc_ms / 1e3)) / value,
                   "distance_evals_per_s": float(n) * (n - 1) * m_total * args.tc_steps / (tc_ms / 1e3),
                   "roofline": tensor_roofline(tc_trace, args.tc_steps),
-                  "phase_ms_per_step": {kn: v[0] / args.tc_steps for kn, v in tc_trace.items()},
-                  "gpu_launches": int(sum(v[1] for v in tc_trace.values())),
+                  "phase_ms_per_step": {kn: v[0] / args.tc_steps for kn, v in tc_trace.items()
+                                        if not kn.startswith("_")},
+                  "gpu_launches": int(sum(v[1] for kn, v in tc_trace.items() if not kn.startswith("_"))),
                   "clocks": tc_clocks,
                   "exactness": f"bit-identical to the plain FP32 join ({form_name[form][3:].upper()} "
                                f"filter, every survivor recomputed in FP32)"}
@@ -389,7 +402,7 @@ def run_ours(args, rank, world, dist):
                                    f"to the least-loaded rank (rank 0: {m} of {m_total})")},
         "distance_evals_per_s": float(n) * (n - 1) * m_total * args.steps / (total_ms / 1e3),
         "roofline": roofline,
-        "phase_ms_per_step": {kname: v[0] / args.steps for kname, v in trace.items()},
+        "phase_ms_per_step": {kname: v[0] / args.steps for kname, v in trace.items() if not kname.startswith("_")},
         "clocks": clocks,
         "e2e": e2e,
         "gpu_launches": launches,
@@ -559,6 +572,50 @@ def run_select(args):
             "config": {"workload": f"N={args.n} objects, {masks.size} sampled subspaces; eps range from "
                                    f"selectivity 0.001 N .. 0.15 N (1024 sampled objects, 4096 bins); eps "
                                    f"grid {n_eps} values; k grid {k_grid}; top-n {top_n}"}}
+
+
+def run_by_dimension(args):
+    """Device time of one call over 256 seeded subspaces of one dimension d,
+    for every d, through the tensor-core form (FP16 operands) and the plain
+    form (no index): where each form spends its time, by dimension."""
+    import torch
+
+    import paper_2405_20176_b300 as snaps
+
+    torch.cuda.set_device(0)
+    n = args.n
+    x = snaps_inputs.population(n, 0)
+    ctx = snaps.snaps_create(0)
+    pop = snaps.snaps_index(ctx, torch.from_numpy(x).cuda())
+    allm = snaps_inputs.all_masks()
+    pc = np.array([bin(int(v)).count("1") for v in allm])
+    rng = np.random.default_rng(SAMPLE_SEED)
+    rows = []
+    for d in range(2, 16):
+        pool = allm[pc == d]
+        ms = np.sort(rng.choice(pool, size=min(256, pool.size), replace=False)).astype(np.uint16)
+        sc = torch.empty((ms.size, 4, n), device="cuda")
+        row = {"d": d, "subspaces": int(ms.size)}
+        for name, prec in (("tc_f16", snaps.SNAPS_TC_F16), ("fp32", snaps.SNAPS_FP32 | snaps.SNAPS_INDEX_NONE)):
+            snaps.snaps_scores(pop, ms, args.k, precision=prec, scores=sc)   # warm-up
+            torch.cuda.synchronize()
+            snaps.snaps_trace(ctx, True)
+            snaps.snaps_scores(pop, ms, args.k, precision=prec, scores=sc)
+            torch.cuda.synchronize()
+            tr = snaps.snaps_trace_read(ctx)
+            snaps.snaps_trace(ctx, False)
+            row[name + "_join_ms"] = tr["join_tc"][0] + tr["join_tree"][0] + tr["join_lane"][0]
+        row["eps_neighbours_per_object"] = float(sc[:, 0].double().mean().item())
+        rows.append(row)
+        print(f"[bench] d={d}: {row}", file=sys.stderr, flush=True)
+    snaps.snaps_release(pop)
+    snaps.snaps_destroy(ctx)
+    return {"metric": "join ms per call of 256 subspaces of one dimension", "n": n, "k": args.k,
+            "rows": rows,
+            "config": {"workload": f"N={n} objects (seed 0); per dimension d = 2..15, 256 subspaces drawn "
+                                   f"with seed {SAMPLE_SEED} (all of them where fewer exist); k={args.k}, "
+                                   f"eps=0.05*sqrt(d); the tensor-core form with FP16 operands and the plain "
+                                   f"form without the grid index; one warm-up call, one timed call each"}}
 
 
 def run_rubin(args):
@@ -747,6 +804,9 @@ def main():
         return 0
     if args.rubin:
         print(json.dumps(run_rubin(args)))
+        return 0
+    if args.by_dimension:
+        print(json.dumps(run_by_dimension(args)))
         return 0
     dist = None
     if world > 1:

@@ -33,9 +33,12 @@
  *  - Distances are Euclidean over the subspace's features, computed in FP32
  *    in one fixed order: the squared differences are accumulated with fused
  *    multiply-adds from the highest feature index down to the lowest.  Every
- *    path (plain, subspace-batched, tensor-core filtered) yields these same
- *    bits.  A point is never its own neighbour.  The eps test is inclusive,
- *    d^2 <= eps^2.  kNN order is by (distance, index).
+ *    neighbour decision uses these bits, so every path (plain,
+ *    subspace-batched, grid-indexed, tensor-core filtered) returns the same
+ *    eps counts, kNN lists, in-degrees and kNN mean distances; the
+ *    tensor-core forms take the mean eps distance from their accumulator
+ *    (see snaps_scores).  A point is never its own neighbour.  The eps test is
+ *    inclusive, d^2 <= eps^2.  kNN order is by (distance, index).
  *  - Default radius (eps == NULL): eps = 0.05 * sqrt(d) for a d-feature
  *    subspace, i.e. eps^2 = 0.0025 * d rounded once to FP32.
  */
@@ -76,8 +79,9 @@ typedef enum snaps_status {
 /* precision argument of snaps_scores / snaps_request: one of the three join
  * forms, optionally OR-ed with one index choice for low-dimensional subspaces */
 #define SNAPS_FP32 0u            /* plain FP32 join */
-#define SNAPS_TC_F16 1u          /* tensor-core FP16 filter, exact FP32 recompute of survivors */
-#define SNAPS_TC_BF16 2u         /* the same with BF16 operands: a 4x wider filter margin, more survivors */
+#define SNAPS_TC_F16 1u          /* tensor-core contraction, high/low FP16 parts, exact FP32 recompute near
+                                  * eps and the k-th distance */
+#define SNAPS_TC_BF16 2u         /* the same with BF16 parts: a 4x wider margin, more recomputes */
 #define SNAPS_INDEX_GRID 0x100u  /* subspaces of <= 4 features always take the grid index */
 #define SNAPS_INDEX_NONE 0x200u  /* no grid index: every subspace is joined by brute force */
 /* Without either index flag, subspaces of <= 4 features take the grid index
@@ -170,8 +174,15 @@ snaps_status snaps_eps_selfjoin(snaps_pop *pop, const uint16_t *masks, int n_mas
 /* Both joins and the four outlier metrics per object and subspace (Table 2).
  * k, eps: as above.  precision: SNAPS_FP32 (plain FP32 joins), SNAPS_TC_F16
  *   or SNAPS_TC_BF16 (the squared-difference x subspace-mask contraction on
- *   the tensor cores as a conservative FP16 or BF16 filter, survivors
- *   recomputed exactly in FP32: the same results).  The tensor-core forms need
+ *   the tensor cores, each scaled squared difference split into a high and a
+ *   low FP16 or BF16 part, FP32 accumulation: d^2 to within 3.9e-6 (FP16) or
+ *   7.4e-6 (BF16) relative.  A candidate within a margin of 2^-17 (FP16) or
+ *   2^-15 (BF16) of eps^2 or of the k-th distance is recomputed exactly in
+ *   FP32, which decides; one clearly inside eps is counted and its distance
+ *   taken from the accumulator.  So counts, kNN lists, in-degrees and kNN
+ *   means are the plain form's bits, and the mean eps distance agrees with
+ *   the plain form's to 2.5e-6 (FP16) or 4.2e-6 (BF16) relative plus
+ *   eps / 2^20).  The tensor-core forms need
  *   every feature to span at most 1, which SNAPS_NORM_MINMAX guarantees
  *   (EINVAL otherwise).  Each may be OR-ed with SNAPS_INDEX_GRID or
  *   SNAPS_INDEX_NONE (see their definitions).
@@ -349,6 +360,17 @@ snaps_status snaps_poll(snaps_ctx *ctx, uint64_t ticket, int64_t timeout_us,
  * status); EBUSY if it is already running or done. */
 snaps_status snaps_cancel(snaps_ctx *ctx, uint64_t ticket);
 
+/* Continuous batching: a slot that admits a request whose every subspace is
+ * joined on its own (plain form; no 32-subspace chunk with four or more of
+ * its subspaces requested; no grid index) and whose work is at most 4e10
+ * candidate-pair evaluations (n (n - 1) x subspaces) also admits the requests
+ * of that kind queued right behind it, up to 32 and within the HBM budget.
+ * Their subspaces are then joined by one launch, each request keeping its own
+ * outputs; results are the same as alone.  Counters since the context was
+ * created: launches that served two or more requests, and the requests they
+ * served (either output may be NULL).  Errors: EINVAL (ctx NULL). */
+snaps_status snaps_serving_stats(snaps_ctx *ctx, int64_t *fused_launches, int64_t *fused_requests);
+
 /* Number of requests the scheduler may run at once (default 4, 1..64).
  * Errors: EINVAL (ctx NULL or slots out of range), EBUSY (lowering it after
  * serving has started). */
@@ -399,6 +421,19 @@ snaps_status snaps_scores_static(int device, const float *feat, int64_t n, int f
  * Errors: EINVAL (NULL output), ECUDA. */
 snaps_status snaps_calibrate_alu(int device, double *evals_per_s);
 
+/* ---- failure detection (library plumbing; the paper has no counterpart) ---- */
+
+/* Every wait of the tensor-core join's pipeline (a tile copy landing, B rows
+ * written, an MMA batch done, accumulators read) is bounded: after `spins`
+ * tries it gives up, the launch's warps leave in order (each waits for its
+ * own copies and MMAs in flight, with the default bound, and tensor memory is
+ * freed), and the call returns SNAPS_ETIMEOUT; the context stays usable.
+ * spins = 0 restores the default, 2^26 tries, far longer than any healthy
+ * copy or MMA takes.  A small value makes the waits give up on purpose, which
+ * is how the failure path is tested.  Applies to later calls on `ctx`.
+ * Errors: EINVAL (ctx NULL). */
+snaps_status snaps_set_wait_limit(snaps_ctx *ctx, unsigned spins);
+
 /* ---- tracing: device time per phase (measurement plumbing; the paper has
  * no counterpart) ---- */
 
@@ -428,6 +463,13 @@ snaps_status snaps_trace(snaps_ctx *ctx, int enable);
  * array may be NULL.  The counters restart from zero.
  * Errors: EINVAL (ctx NULL), ECUDA (an event failed). */
 snaps_status snaps_trace_read(snaps_ctx *ctx, double *ms, int64_t *launches);
+
+/* The subspace-batched join's candidate streams since tracing was last
+ * enabled (the context's synchronous calls only): 64-row steps
+ * loaded and evaluated, and all steps, the skipped ones -- whose box bound
+ * proves every pair fails -- included.  Either output may be NULL.  Waits for
+ * the device.  Errors: EINVAL (ctx NULL), ECUDA. */
+snaps_status snaps_trace_steps(snaps_ctx *ctx, int64_t *steps_loaded, int64_t *steps_total);
 
 #ifdef __cplusplus
 }

@@ -104,6 +104,9 @@ def lib():
             "snaps_cancel": ([p, ctypes.c_uint64], i32),
             "snaps_set_slots": ([p, i32], i32),
             "snaps_trace": ([p, i32], i32),
+            "snaps_set_wait_limit": ([p, u32], i32),
+            "snaps_serving_stats": ([p, p, p], i32),
+            "snaps_trace_steps": ([p, p, p], i32),
             "snaps_calibrate_alu": ([i32, p], i32),
             "snaps_scores_static": ([i32, p, i64, i32, u32, p, i32, i32, p, p, p, i32, p], i32),
             "snaps_trace_read": ([p, p, p], i32),
@@ -338,8 +341,27 @@ def snaps_calibrate_alu(device: int = 0) -> float:
     return v.value
 
 
+def snaps_serving_stats(ctx: int):
+    """(launches that served two or more requests, requests they served)."""
+    a, b = ctypes.c_int64(), ctypes.c_int64()
+    _check(lib().snaps_serving_stats(ctx, ctypes.byref(a), ctypes.byref(b)), "snaps_serving_stats")
+    return a.value, b.value
+
+
+def snaps_set_wait_limit(ctx: int, spins: int = 0) -> None:
+    """Tries after which a tensor-core pipeline wait gives up (0 = the default)."""
+    _check(lib().snaps_set_wait_limit(ctx, int(spins)), "snaps_set_wait_limit")
+
+
 def snaps_trace(ctx: int, enable: bool = True) -> None:
     _check(lib().snaps_trace(ctx, 1 if enable else 0), "snaps_trace")
+
+
+def snaps_trace_steps(ctx: int):
+    """(steps loaded, all steps) of the subspace-batched join since tracing was enabled."""
+    a, b = ctypes.c_int64(), ctypes.c_int64()
+    _check(lib().snaps_trace_steps(ctx, ctypes.byref(a), ctypes.byref(b)), "snaps_trace_steps")
+    return a.value, b.value
 
 
 def snaps_trace_read(ctx: int):

@@ -104,6 +104,8 @@ struct snaps_ctx {
     int n_slots = 4;
     std::vector<Slot *> slots;
     bool stopping = false;
+    std::atomic<long long> fused_launches{0};  // launches that joined two or more requests
+    std::atomic<long long> fused_requests{0};  // requests served by those launches
     std::atomic<int> n_pops{0};
 
     // kernels one radix sort launches, by n (counted from a stream capture
@@ -111,6 +113,9 @@ struct snaps_ctx {
     std::mutex cap_mu;
     cudaStream_t cap_stream = nullptr;
     std::unordered_map<int64_t, int> sort_kernels;
+
+    // spins after which a tensor-core pipeline wait gives up (0 = the default)
+    std::atomic<unsigned> wait_limit{0};
 
     // index route per (population size class, subspace dimension, k class),
     // recorded by snaps_autotune
@@ -144,6 +149,9 @@ struct Request {
     std::vector<uint16_t> masks;
     std::vector<float> eps;
     size_t footprint = 0;
+    // every subspace joined on its own (plain form, no chunk of kTreeMinActive
+    // or more, no grid index) and little work: may share a launch with others
+    bool fusable = false;
     Clock::time_point t_submit, t_admit, t_done;
     bool done = false;
     bool running = false;
@@ -286,7 +294,7 @@ snaps_status validate(const JobSpec &j)
     return SNAPS_OK;
 }
 
-// Split the requested subspaces between the tree kernel (chunks with >= 2
+// Split the requested subspaces between the tree kernel (chunks with >= kTreeMinActive
 // requested subspaces) and the subspace-at-a-time kernel (everything else,
 // listed in groups of 32).
 struct Plan {
@@ -415,7 +423,7 @@ Plan make_plan(const JobSpec &j)
             // decides for the subspaces that would be joined on their own.
             snaps_tune_entry te;
             const bool tuned = tune_lookup(j.pop->ctx, j.pop->n, d, j.k, &te);
-            const bool alone = tc_form || per_chunk[(uint32_t)j.masks[m] >> kTreeLowBits] < 2;
+            const bool alone = tc_form || per_chunk[(uint32_t)j.masks[m] >> kTreeLowBits] < kTreeMinActive;
             if (tuned) mult = te.cell_mult;
             grid = index == SNAPS_INDEX_GRID ||
                    (tuned && alone ? te.grid != 0 : j.pop->n >= SNAPS_GRID_AUTO_N);
@@ -475,7 +483,7 @@ Plan make_plan(const JobSpec &j)
     std::vector<int> lone = extra;
     for (int c = 0; c < n_chunk; ++c) {
         if (count[c] == 0) continue;
-        if (count[c] == 1) {
+        if (count[c] < kTreeMinActive) {
             for (int L = 0; L < kTreeWidth; ++L)
                 if (first[size_t(c) * kTreeWidth + L] >= 0) lone.push_back(first[size_t(c) * kTreeWidth + L]);
             continue;
@@ -707,6 +715,7 @@ snaps_status run_job(snaps_ctx *ctx, const JobSpec &j, cudaStream_t st, Scratch 
     SNAPS_CHECK_CUDA(cudaMemsetAsync(&ctrl->error, 0, sizeof(unsigned), st));
 
     JoinShape shape{p->x, n, p->n_pad, j.k};
+    shape.wait_limit = ctx->wait_limit.load();
     JoinOut out{L.scores, L.knn_idx, L.knn_dist, L.eps_count};
     const int n_chunks = (int)pl.chunks.size();
     for (int b0 = 0; b0 < n_chunks; b0 += pl.order_batch) {
@@ -815,11 +824,123 @@ JobSpec spec_of(Request *r)
     return j;
 }
 
+// Serving: requests that share one launch.  At most kFuseMaxBatch requests,
+// each of at most kFuseMaxWork candidate-pair evaluations (n (n - 1) x
+// subspaces), so that one batch stays short next to the requests that arrive
+// while it runs.
+constexpr int kFuseMaxBatch = 32;
+constexpr double kFuseMaxWork = 4.0e10;
+
+bool fusable_plan(const JobSpec &j, const Plan &pl)
+{
+    const double work = (double)j.pop->n * (double)(j.pop->n - 1) * (double)j.n_masks;
+    return (j.precision & 0xFFu) == SNAPS_FP32 && pl.chunks.empty() && pl.grids.empty() && pl.blocks.empty() &&
+           !j.knn_idx && !j.knn_dist && !j.eps_count && !j.eps_mean && work <= kFuseMaxWork;
+}
+
+// Run fusable requests together: each gets its own outputs and scratch, and
+// the subspaces of all of them are joined by one work-list launch per kNN-list
+// size (k <= 16, k <= 32) -- a small request then no longer fills the GPU on
+// its own.  The finishing kernel and the copies follow per request.  Returns
+// the batch's status (every request in it gets the same).
+snaps_status run_batch(snaps_ctx *ctx, const std::vector<JobSpec> &jobs, cudaStream_t st, Scratch &scratch,
+                       DeviceControl *ctrl)
+{
+    struct Part {
+        Plan pl;
+        Layout L;
+        size_t off = 0;
+        bool dev_scores, dev_norm, dev_top;
+    };
+    std::vector<Part> parts(jobs.size());
+    size_t total = 0;
+    std::vector<WorkItem> items[2];
+    int ctas[2] = {0, 0};
+    for (size_t q = 0; q < jobs.size(); ++q) {
+        const JobSpec &j = jobs[q];
+        Part &pt = parts[q];
+        pt.pl = make_plan(j);
+        pt.dev_scores = is_device_ptr(j.scores);
+        pt.dev_norm = is_device_ptr(j.norm);
+        pt.dev_top = is_device_ptr(j.top);
+        pt.L = layout_job(j, pt.pl, nullptr, pt.dev_scores, pt.dev_norm, pt.dev_top, false, false, false);
+        pt.off = total;
+        total += (pt.L.bytes + 255) & ~size_t(255);
+        for (const MaskGroup &g : pt.pl.groups)
+            for (int l = 0; l < 32; ++l) {
+                if (g.mask[l] == 0u) continue;
+                WorkItem w{};
+                w.x = j.pop->x;
+                w.n = (int)j.pop->n;
+                w.k = j.k;
+                w.mask = g.mask[l];
+                w.eps2 = g.eps2[l];
+                const int c = j.k <= 16 ? 0 : 1;
+                w.first_cta = ctas[c];
+                ctas[c] += (int)((j.pop->n + 255) / 256);
+                w.scores = nullptr;                 // known once the layout is
+                w.pad = (int)q << 16 | g.slot[l];   // request and output slot until then
+                items[c].push_back(w);
+            }
+    }
+    const size_t item_off = total;
+    total += sizeof(WorkItem) * (items[0].size() + items[1].size()) + 256;
+    SNAPS_TRY(scratch_reserve(ctx, scratch, total));
+    char *base = (char *)scratch.ptr;
+    for (size_t q = 0; q < jobs.size(); ++q) {
+        Part &pt = parts[q];
+        pt.L = layout_job(jobs[q], pt.pl, base + pt.off, pt.dev_scores, pt.dev_norm, pt.dev_top, false, false, false);
+        SNAPS_CHECK_CUDA(cudaMemsetAsync(pt.L.scores, 0, (size_t)jobs[q].n_masks * 4 * jobs[q].pop->n * sizeof(float), st));
+    }
+    for (int c = 0; c < 2; ++c)
+        for (WorkItem &w : items[c]) {
+            const int q = w.pad >> 16, slot = w.pad & 0xffff;
+            w.scores = parts[q].L.scores + (size_t)slot * 4 * jobs[q].pop->n;
+            w.pad = 0;
+        }
+    SNAPS_CHECK_CUDA(cudaMemsetAsync(&ctrl->error, 0, sizeof(unsigned), st));
+    WorkItem *dev_items = (WorkItem *)(base + ((item_off + 255) & ~size_t(255)));
+    {
+        TraceScope ts(ctx, SNAPS_PHASE_JOIN_LANE, st, (items[0].empty() ? 0 : 1) + (items[1].empty() ? 0 : 1));
+        WorkItem *d = dev_items;
+        for (int c = 0; c < 2; ++c) {
+            if (items[c].empty()) continue;
+            SNAPS_CHECK_CUDA(cudaMemcpyAsync(d, items[c].data(), sizeof(WorkItem) * items[c].size(),
+                                             cudaMemcpyHostToDevice, st));
+            SNAPS_TRY(launch_join_worklist(d, (int)items[c].size(), ctas[c], c == 0 ? 16 : 32, st));
+            d += items[c].size();
+        }
+    }
+    for (size_t q = 0; q < jobs.size(); ++q) {
+        const JobSpec &j = jobs[q];
+        const Part &pt = parts[q];
+        const int64_t n = j.pop->n;
+        const size_t nm = (size_t)j.n_masks;
+        if (j.norm || j.top) {
+            TraceScope ts(ctx, j.norm ? SNAPS_PHASE_NORM : SNAPS_PHASE_TOP, st);
+            SNAPS_TRY(launch_finish(pt.L.scores, n, j.n_masks, pt.L.norm, j.top ? j.top_n : 0, pt.L.top, st));
+        }
+        if (j.scores && !pt.dev_scores)
+            SNAPS_CHECK_CUDA(cudaMemcpyAsync(j.scores, pt.L.scores, nm * 4 * n * sizeof(float), cudaMemcpyDeviceToHost, st));
+        if (j.norm && !pt.dev_norm)
+            SNAPS_CHECK_CUDA(cudaMemcpyAsync(j.norm, pt.L.norm, nm * 4 * n * sizeof(float), cudaMemcpyDeviceToHost, st));
+        if (j.top && !pt.dev_top)
+            SNAPS_CHECK_CUDA(cudaMemcpyAsync(j.top, pt.L.top, nm * 4 * (size_t)j.top_n * sizeof(int32_t),
+                                             cudaMemcpyDeviceToHost, st));
+    }
+    unsigned err = 0;
+    SNAPS_CHECK_CUDA(cudaMemcpyAsync(&err, &ctrl->error, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+    SNAPS_CHECK_CUDA(cudaStreamSynchronize(st));
+    if (err) FAIL(SNAPS_ECUDA, "a fused join met an error (error word 0x%x)", err);
+    return SNAPS_OK;
+}
+
 void worker_loop(snaps_ctx *ctx, Slot *slot)
 {
     cudaSetDevice(ctx->device);
     for (;;) {
-        Request *r = nullptr;
+        std::vector<Request *> batch;
+        size_t grow = 0;
         {
             std::unique_lock<std::mutex> lk(ctx->q_mu);
             for (;;) {
@@ -832,29 +953,55 @@ void worker_loop(snaps_ctx *ctx, Slot *slot)
                         std::lock_guard<std::mutex> g(ctx->mem_mu);
                         held = ctx->held;
                     }
-                    const size_t grow = h->footprint > slot->scratch.cap ? h->footprint : 0;
-                    if (held + ctx->reserved + grow <= ctx->budget || ctx->reserved == 0) {
+                    const size_t g0 = h->footprint > slot->scratch.cap ? h->footprint : 0;
+                    if (held + ctx->reserved + g0 <= ctx->budget || ctx->reserved == 0) {
                         ctx->queue.pop_front();
+                        batch.push_back(h);
+                        // continuous batching: the fusable requests queued right behind a
+                        // fusable one join its launch, while the budget allows
+                        size_t need = h->footprint;
+                        while (h->fusable && !ctx->queue.empty() && (int)batch.size() < kFuseMaxBatch) {
+                            Request *nx = ctx->queue.front();
+                            if (!nx->fusable) break;
+                            const size_t need2 = need + nx->footprint + 4096;
+                            const size_t g2 = need2 > slot->scratch.cap ? need2 : 0;
+                            if (held + ctx->reserved + g2 > ctx->budget) break;
+                            ctx->queue.pop_front();
+                            batch.push_back(nx);
+                            need = need2;
+                        }
+                        grow = need > slot->scratch.cap ? need : 0;
                         ctx->reserved += grow;
-                        h->running = true;
-                        h->t_admit = Clock::now();
-                        r = h;
+                        for (Request *b : batch) {
+                            b->running = true;
+                            b->t_admit = Clock::now();
+                        }
                         break;
                     }
                 }
                 ctx->q_cv.wait(lk);
             }
         }
-        const size_t grow = r->footprint > slot->scratch.cap ? r->footprint : 0;
-        snaps_status s = run_job(ctx, spec_of(r), slot->stream, slot->scratch, slot->ctrl, true);
+        snaps_status s;
+        if (batch.size() == 1) {
+            s = run_job(ctx, spec_of(batch[0]), slot->stream, slot->scratch, slot->ctrl, true);
+        } else {
+            std::vector<JobSpec> jobs;
+            for (Request *b : batch) jobs.push_back(spec_of(b));
+            s = run_batch(ctx, jobs, slot->stream, slot->scratch, slot->ctrl);
+            ctx->fused_launches.fetch_add(1);
+            ctx->fused_requests.fetch_add((long long)batch.size());
+        }
         {
             std::lock_guard<std::mutex> lk(ctx->q_mu);
             ctx->reserved -= grow;
-            r->status = s;
-            r->done = true;
-            r->running = false;
-            r->t_done = Clock::now();
-            r->req.pop->inflight.fetch_sub(1);
+            for (Request *r : batch) {
+                r->status = s;
+                r->done = true;
+                r->running = false;
+                r->t_done = Clock::now();
+                r->req.pop->inflight.fetch_sub(1);
+            }
         }
         ctx->done_cv.notify_all();
         ctx->q_cv.notify_all();
@@ -906,6 +1053,7 @@ snaps_status snaps_create(int device, size_t hbm_budget_bytes, snaps_ctx **out)
         return s;
     }
     ctx->ctrl = (DeviceControl *)c;
+    SNAPS_CHECK_CUDA(cudaMemset(ctx->ctrl, 0, sizeof(DeviceControl)));
     *out = ctx;
     return SNAPS_OK;
 }
@@ -1593,6 +1741,7 @@ snaps_status snaps_submit(snaps_ctx *ctx, const snaps_request *req, uint64_t *ti
         return s;
     }
     r->footprint = job_footprint(j);
+    r->fusable = fusable_plan(j, make_plan(j));
     if (r->footprint > ctx->budget) {
         const size_t need = r->footprint;
         delete r;
@@ -1666,6 +1815,23 @@ snaps_status snaps_cancel(snaps_ctx *ctx, uint64_t ticket)
     return SNAPS_OK;
 }
 
+snaps_status snaps_serving_stats(snaps_ctx *ctx, int64_t *fused_launches, int64_t *fused_requests)
+{
+    clear_error();
+    if (!ctx) FAIL(SNAPS_EINVAL, "ctx is NULL");
+    if (fused_launches) *fused_launches = ctx->fused_launches.load();
+    if (fused_requests) *fused_requests = ctx->fused_requests.load();
+    return SNAPS_OK;
+}
+
+snaps_status snaps_set_wait_limit(snaps_ctx *ctx, unsigned spins)
+{
+    clear_error();
+    if (!ctx) FAIL(SNAPS_EINVAL, "ctx is NULL");
+    ctx->wait_limit.store(spins);
+    return SNAPS_OK;
+}
+
 snaps_status snaps_trace(snaps_ctx *ctx, int enable)
 {
     clear_error();
@@ -1678,8 +1844,25 @@ snaps_status snaps_trace(snaps_ctx *ctx, int enable)
             ctx->spare.push_back(m.b);
         }
         ctx->marks.clear();
+        // the subspace-batched join's step counters restart too
+        SNAPS_CHECK_CUDA(cudaDeviceSynchronize());
+        SNAPS_CHECK_CUDA(cudaMemset(&ctx->ctrl->steps_loaded, 0, 2 * sizeof(unsigned long long)));
+        SNAPS_CHECK_CUDA(cudaDeviceSynchronize());
     }
     ctx->tracing = enable != 0;
+    return SNAPS_OK;
+}
+
+snaps_status snaps_trace_steps(snaps_ctx *ctx, int64_t *steps_loaded, int64_t *steps_total)
+{
+    clear_error();
+    if (!ctx) FAIL(SNAPS_EINVAL, "ctx is NULL");
+    ON_DEVICE(ctx->device);
+    unsigned long long v[2] = {0ull, 0ull};
+    SNAPS_CHECK_CUDA(cudaDeviceSynchronize());
+    SNAPS_CHECK_CUDA(cudaMemcpy(v, &ctx->ctrl->steps_loaded, sizeof(v), cudaMemcpyDeviceToHost));
+    if (steps_loaded) *steps_loaded = (int64_t)v[0];
+    if (steps_total) *steps_total = (int64_t)v[1];
     return SNAPS_OK;
 }
 

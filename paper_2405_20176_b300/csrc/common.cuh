@@ -75,6 +75,11 @@ struct DeviceControl {
     unsigned long long next_work;
     unsigned int error;   // 0 = fine; otherwise a kErr* code
     unsigned int pad;
+    // subspace-batched join: 64-row steps of the candidate streams that were
+    // loaded (not skipped by their box bound), and all steps, summed over the
+    // launches since they were last cleared
+    unsigned long long steps_loaded;
+    unsigned long long steps_total;
 };
 constexpr unsigned kErrTimeout = 1u;
 constexpr unsigned kErrBadRow = 2u;  // a row's stored original index is out of range

@@ -236,6 +236,56 @@ __global__ void __launch_bounds__(kSQ, 2)
     }
 }
 
+// The work-list form: CTA b finds its item by a binary search over the
+// items' first CTAs, then joins that item's 256 queries from row
+// 256 (b - first_cta) exactly as join_single_kernel does.
+template <int KMAX>
+__global__ void __launch_bounds__(kSQ, 2)
+    join_worklist_kernel(const WorkItem *__restrict__ items, int n_items)
+{
+    extern __shared__ __align__(16) unsigned char single_smem[];
+    SingleSmem<KMAX> &sm = *reinterpret_cast<SingleSmem<KMAX> *>(single_smem);
+    const int b = (int)blockIdx.x;
+    int lo = 0, hi = n_items - 1;  // the last item whose first CTA is <= b
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (items[mid].first_cta <= b) lo = mid;
+        else hi = mid - 1;
+    }
+    const WorkItem it = items[lo];
+    const int p0 = (b - it.first_cta) * kSQ;
+    if (it.mask == 0u || p0 >= it.n) return;  // the whole CTA leaves before any barrier
+    JoinOut o{it.scores, nullptr, nullptr, nullptr};
+    switch (__popc(it.mask)) {
+    case 2: join_one<2, KMAX>(sm, it.x, it.n, it.mask, it.eps2, 0, it.k, o, p0); break;
+    case 3: join_one<3, KMAX>(sm, it.x, it.n, it.mask, it.eps2, 0, it.k, o, p0); break;
+    case 4: join_one<4, KMAX>(sm, it.x, it.n, it.mask, it.eps2, 0, it.k, o, p0); break;
+    case 5: join_one<5, KMAX>(sm, it.x, it.n, it.mask, it.eps2, 0, it.k, o, p0); break;
+    case 6: join_one<6, KMAX>(sm, it.x, it.n, it.mask, it.eps2, 0, it.k, o, p0); break;
+    case 7: join_one<7, KMAX>(sm, it.x, it.n, it.mask, it.eps2, 0, it.k, o, p0); break;
+    case 8: join_one<8, KMAX>(sm, it.x, it.n, it.mask, it.eps2, 0, it.k, o, p0); break;
+    case 9: join_one<9, KMAX>(sm, it.x, it.n, it.mask, it.eps2, 0, it.k, o, p0); break;
+    case 10: join_one<10, KMAX>(sm, it.x, it.n, it.mask, it.eps2, 0, it.k, o, p0); break;
+    case 11: join_one<11, KMAX>(sm, it.x, it.n, it.mask, it.eps2, 0, it.k, o, p0); break;
+    case 12: join_one<12, KMAX>(sm, it.x, it.n, it.mask, it.eps2, 0, it.k, o, p0); break;
+    case 13: join_one<13, KMAX>(sm, it.x, it.n, it.mask, it.eps2, 0, it.k, o, p0); break;
+    case 14: join_one<14, KMAX>(sm, it.x, it.n, it.mask, it.eps2, 0, it.k, o, p0); break;
+    case 15: join_one<15, KMAX>(sm, it.x, it.n, it.mask, it.eps2, 0, it.k, o, p0); break;
+    default: break;  // the host rejects masks of fewer than 2 features
+    }
+}
+
+template <int KMAX>
+snaps_status launch_worklist(const WorkItem *items, int n_items, int n_ctas, cudaStream_t st)
+{
+    const size_t smem = sizeof(SingleSmem<KMAX>);
+    auto kern = join_worklist_kernel<KMAX>;
+    SNAPS_CHECK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    kern<<<(unsigned)n_ctas, kSQ, smem, st>>>(items, n_items);
+    SNAPS_CHECK_CUDA(cudaGetLastError());
+    return SNAPS_OK;
+}
+
 template <int KMAX>
 snaps_status launch_single(const JoinShape &s, const MaskGroup *groups, int n_groups, const JoinOut &o,
                            cudaStream_t st)
@@ -250,6 +300,13 @@ snaps_status launch_single(const JoinShape &s, const MaskGroup *groups, int n_gr
 }
 
 }  // namespace
+
+snaps_status launch_join_worklist(const WorkItem *items, int n_items, int n_ctas, int kmax, cudaStream_t st)
+{
+    if (n_items <= 0 || n_ctas <= 0) return SNAPS_OK;
+    if (kmax <= 16) return launch_worklist<16>(items, n_items, n_ctas, st);
+    return launch_worklist<32>(items, n_items, n_ctas, st);
+}
 
 snaps_status launch_join_single(const JoinShape &s, const MaskGroup *groups, int n_groups, const JoinOut &o,
                                 cudaStream_t st)

@@ -137,6 +137,8 @@ struct WarpState {
     float eps2[kW];                 // radii of this chunk
     float escale[kW];               // 2^20 / eps
     float2 nxq[16];                 // the query's negated features, as (a, b) pairs
+    unsigned long long stat_loaded; // steps loaded and steps in the streams of this warp's items
+    unsigned long long stat_total;
 };
 
 // Two CTAs share an SM: 2 x 8 warps (k <= 16, 128 registers a thread) or
@@ -443,12 +445,22 @@ __global__ void __launch_bounds__(CW * 32, kCtasPerSm<CW>)
     WarpState<KMAX> &ws = sm.ws[warp];
     const int ws_off = (int)((const unsigned char *)&sm.ws[warp] - tree_smem);
 
+    if (lane == 0) {
+        ws.stat_loaded = 0ull;
+        ws.stat_total = 0ull;
+    }
     for (;;) {
         // ---- next work item (one query of one chunk), claimed by the warp -----------
         unsigned long long wc = 0;
         if (lane == 0) wc = atomicAdd(&ctrl->next_work, 1ull);
         const long long w = (long long)__shfl_sync(dev::kFull, wc, 0);
-        if (w >= total) return;
+        if (w >= total) {
+            if (lane == 0) {
+                atomicAdd(&ctrl->steps_loaded, ws.stat_loaded);
+                atomicAdd(&ctrl->steps_total, ws.stat_total);
+            }
+            return;
+        }
         const TreeChunk *ch = &chunks[w / n];
         // the chunk's rows (in the chunk's own order when each chunk has a copy)
         const float4 *__restrict__ x = s.x + (w / n) * s.chunk_stride;
@@ -506,6 +518,7 @@ __global__ void __launch_bounds__(CW * 32, kCtasPerSm<CW>)
         const int n_high = __popc(high);
         int wbase = init_steps, next_w = init_steps;
         unsigned live = 0u;
+        int taken = 0;  // steps of the stream loaded after the set-up phase
         auto take = [&]() -> int {
             while (live == 0u) {
                 if (next_w >= n_steps) return -1;
@@ -539,6 +552,7 @@ __global__ void __launch_bounds__(CW * 32, kCtasPerSm<CW>)
             }
             const int b = __ffs(live) - 1;
             live &= live - 1u;
+            ++taken;
             return wbase + b;
         };
         StepRows cur;
@@ -589,6 +603,10 @@ __global__ void __launch_bounds__(CW * 32, kCtasPerSm<CW>)
             u = un;
         }
         if (tcount > 0) flush_tuples<KMAX>(ws_off, tcount, k);
+        if (lane == 0) {
+            ws.stat_loaded += (unsigned long long)(taken + init_steps);
+            ws.stat_total += (unsigned long long)n_steps;
+        }
 
         // ---- end of the work item: lane L reports subspace L ---------------------------
         {

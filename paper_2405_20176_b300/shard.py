@@ -7,8 +7,9 @@ and each goes to the rank with the least cost so far (the longest-first
 greedy form of least-loaded scheduling, within 4/3 of the best assignment).
 A unit is a whole 32-subspace chunk -- the subspaces (H << 5) | L that share
 one high part H, which the subspace-batched join evaluates together -- when
-two or more of its subspaces are requested, and otherwise a single subspace;
-splitting a chunk would repeat its shared arithmetic on two GPUs.  No data
+four or more of its subspaces are requested (the library's threshold for that
+kernel), and otherwise a single subspace; splitting a chunk would repeat its
+shared arithmetic on two GPUs.  No data
 moves between ranks while they compute; per-subspace results are gathered on
 rank 0 afterwards.
 
@@ -28,6 +29,7 @@ from collections import defaultdict
 import numpy as np
 
 LOW_BITS = 5  # subspaces per chunk: 2^5
+TREE_MIN_ACTIVE = 4  # requested subspaces from which a chunk takes the subspace-batched join
 
 
 def units(masks, n: int):
@@ -47,7 +49,7 @@ def units(masks, n: int):
     pairs = float(n) * float(n - 1)
     out = []
     for _, members in sorted(by_chunk.items()):
-        if len(members) >= 2:
+        if len(members) >= TREE_MIN_ACTIVE:
             out.append((pairs * (45.0 + 3.0 * len(members)), members))
         else:
             extra.extend(members)

@@ -114,3 +114,50 @@ def test_poll_timeout_returns_eagain():
         snaps.snaps_release(pop)
     finally:
         snaps.snaps_destroy(ctx)
+
+
+def test_small_requests_share_launches():
+    """Continuous batching: small requests on several populations, with
+    different k, queued behind a slot that is busy, are joined by shared
+    launches; each result is the same as the request alone."""
+    ctx = snaps.snaps_create(0)
+    try:
+        snaps.snaps_set_slots(ctx, 1)
+        rng = np.random.default_rng(11)
+        allm = snaps_inputs.all_masks()
+        # a large request keeps the one slot busy while the small ones queue
+        big_pop = snaps.snaps_index(ctx, snaps_inputs.population(9000, 2))
+        big_out = torch.empty((512, 4, 9000), device="cuda")
+        pops = [snaps.snaps_index(ctx, snaps_inputs.population(int(n), int(s)))
+                for n, s in [(700, 1), (1500, 2), (2300, 3)]]
+        sizes = [700, 1500, 2300]
+        small = []
+        for r in range(24):
+            pi = int(rng.integers(0, 3))
+            masks = rng.choice(allm, size=int(rng.integers(1, 6)), replace=False).astype(np.uint16)
+            k = int(rng.choice([5, 10, 20]))
+            n = sizes[pi]
+            sc = torch.empty((masks.size, 4, n), device="cuda")
+            tp = torch.empty((masks.size, 4, min(100, n)), dtype=torch.int32, device="cuda")
+            small.append((pi, masks, k, sc, tp))
+        torch.cuda.synchronize()
+        tickets = [snaps.snaps_submit(ctx, big_pop, allm[:512], 10, scores=big_out)]
+        for pi, masks, k, sc, tp in small:
+            tickets.append(snaps.snaps_submit(ctx, pops[pi], masks, k, scores=sc, top=tp,
+                                              top_n=min(100, sizes[pi])))
+        for t in tickets:
+            assert snaps.snaps_poll(ctx, t, -1).status == snaps.SNAPS_OK
+        launches, served = snaps.snaps_serving_stats(ctx)
+        assert launches >= 1 and served >= 2 * launches, (launches, served)
+        torch.cuda.synchronize()
+        for pi, masks, k, sc, tp in small:
+            n = sizes[pi]
+            a_sc = np.zeros((masks.size, 4, n), dtype=np.float32)
+            a_tp = np.zeros((masks.size, 4, min(100, n)), dtype=np.int32)
+            snaps.snaps_scores(pops[pi], masks, k, scores=a_sc, top=a_tp, top_n=min(100, n))
+            np.testing.assert_array_equal(sc.cpu().numpy(), a_sc)
+            np.testing.assert_array_equal(tp.cpu().numpy(), a_tp)
+        for p in pops + [big_pop]:
+            snaps.snaps_release(p)
+    finally:
+        snaps.snaps_destroy(ctx)
