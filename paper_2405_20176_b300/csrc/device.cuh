@@ -153,22 +153,5 @@ __device__ __forceinline__ void list_insert(unsigned ballot, float d2, int j, fl
     }
 }
 
-// Sequential sorted insertion into one thread's private list (used where one
-// lane owns one subspace).  Returns the new k-th squared distance.
-__device__ __forceinline__ float private_insert(float *ld, int *lj, int k, float d2, int j) {
-    int p = k - 1;
-    while (p > 0) {
-        const float pd = ld[p - 1];
-        const int pj = lj[p - 1];
-        if (!(d2 < pd || (d2 == pd && j < pj))) break;
-        ld[p] = pd;
-        lj[p] = pj;
-        --p;
-    }
-    ld[p] = d2;
-    lj[p] = j;
-    return ld[k - 1];
-}
-
 }  // namespace dev
 }  // namespace snaps

@@ -129,7 +129,9 @@ struct WarpState {
     int lj[kW][KMAX + 1];           // free of bank conflicts
     unsigned long long esum[kW];    // exact quantised eps distance sums
     unsigned epart[kW];             // this flush's partial sums (<= kTBuf terms of <= 2^20 + 1)
-    float T[kW];                    // current k-th squared distance
+    float T[kW];                    // current k-th squared distance: the list's largest entry
+    int Tj[kW];                     // its original index
+    int Tp[kW];                     // its position in the (unsorted) list
     float tc[kW];                   // pass threshold max(T, eps) by L
     alignas(16) float tcd[kW];      // the same in DFS order, read four at a time by the walk
     float tcmax;                    // the largest of them: a bound for the whole tree
@@ -180,6 +182,30 @@ __device__ __forceinline__ void update_tcmax(WarpState<KMAX> &ws)
     __syncwarp();
 }
 
+// A kNN list is kept unsorted, with its largest entry by (distance, index)
+// tracked: a better candidate overwrites that entry, and a rescan of the k
+// entries (independent loads) finds the new largest.  Lists are sorted once,
+// when their query's results are written.
+__device__ __forceinline__ void list_offer(float *ld, int *lj, int k, float d2, int j, float &T, int &Tj, int &Tp)
+{
+    if (!(d2 < T || (d2 == T && j < Tj))) return;
+    ld[Tp] = d2;
+    lj[Tp] = j;
+    float mx = ld[0];
+    int mj = lj[0], mp = 0;
+    for (int p = 1; p < k; ++p) {
+        const float v = ld[p];
+        const int q = lj[p];
+        const bool gt = v > mx || (v == mx && q > mj);
+        mx = gt ? v : mx;
+        mj = gt ? q : mj;
+        mp = gt ? p : mp;
+    }
+    T = mx;
+    Tj = mj;
+    Tp = mp;
+}
+
 // Process the buffered event tuples, 32 at a time with every lane busy: eps
 // counts and exact distance sums for the tuples within eps (shared-memory
 // atomics), then the tuples at or below their subspace's current k-th
@@ -215,23 +241,12 @@ __device__ __noinline__ bool flush_tuples(int ws_off, int count, int k)
         const int rank = __popc(same & pend & lower);
         for (int r = 0; pend; ++r) {
             if (want && rank == r) {
-                float *ld = ws.ld[L];
-                int *lj = ws.lj[L];
-                const float T = ld[k - 1];
-                if (d2 < T || (d2 == T && j < lj[k - 1])) {
-                    int p = k - 1;
-                    while (p > 0) {
-                        const float pd = ld[p - 1];
-                        const int pj = lj[p - 1];
-                        if (!(d2 < pd || (d2 == pd && j < pj))) break;
-                        ld[p] = pd;
-                        lj[p] = pj;
-                        --p;
-                    }
-                    ld[p] = d2;
-                    lj[p] = j;
-                    ws.T[L] = ld[k - 1];
-                }
+                float T = ws.T[L];
+                int Tj = ws.Tj[L], Tp = ws.Tp[L];
+                list_offer(ws.ld[L], ws.lj[L], k, d2, j, T, Tj, Tp);
+                ws.T[L] = T;
+                ws.Tj[L] = Tj;
+                ws.Tp[L] = Tp;
             }
             const bool mine = want && rank == r;
             pend &= ~__ballot_sync(dev::kFull, mine);
@@ -388,6 +403,7 @@ __device__ __noinline__ void setup_phase(int ws_off, const float4 *__restrict__ 
     const float e2 = ws.eps2[L];
     const float sc = ws.escale[L];
     float T = ws.T[L];
+    int Tj = ws.Tj[L], Tp = ws.Tp[L];
     int cnt = 0;
     unsigned long long qs = 0;
     float *stg = reinterpret_cast<float *>(ws.tbuf);  // [32][64], columns XOR-swizzled by row
@@ -417,12 +433,13 @@ __device__ __noinline__ void setup_phase(int ws_off, const float4 *__restrict__ 
                 ++cnt;
                 qs += dev::eps_quant(val, sc);
             }
-            if (use && (val < T || (val == T && oc < ws.lj[L][k - 1])))
-                T = dev::private_insert(ws.ld[L], ws.lj[L], k, val, oc);
+            if (use) list_offer(ws.ld[L], ws.lj[L], k, val, oc, T, Tj, Tp);
         }
     }
     __syncwarp();
     ws.T[L] = T;
+    ws.Tj[L] = Tj;
+    ws.Tp[L] = Tp;
     ws.cnt[L] = cnt;
     ws.esum[L] = qs;
     ws.tc[L] = mine ? fmaxf(next_up(T), eps_up(e2)) : -CUDART_INF_F;
@@ -496,6 +513,8 @@ __global__ void __launch_bounds__(CW * 32, kCtasPerSm<CW>)
             ws.epart[L] = 0u;
             ws.cnt[L] = 0;
             ws.T[L] = (((active >> L) & 1u) && k > 0) ? CUDART_INF_F : -CUDART_INF_F;
+            ws.Tj[L] = 0x7fffffff;
+            ws.Tp[L] = 0;
         }
         __syncwarp();
         // The candidate stream: all steps of 64 rows, starting at the query's own
@@ -619,6 +638,21 @@ __global__ void __launch_bounds__(CW * 32, kCtasPerSm<CW>)
                 sc[n + orig_i] = dev::eps_mean(ws.esum[L], cnt, ws.escale[L]);
                 if (o.eps_count) o.eps_count[(int64_t)slot * n + orig_i] = cnt;
                 if (k > 0) {
+                    // sort the list by (distance, index); the mean is summed in that order
+                    float *ld = ws.ld[L];
+                    int *lj = ws.lj[L];
+                    for (int p = 1; p < k; ++p) {
+                        const float v = ld[p];
+                        const int j = lj[p];
+                        int q = p;
+                        while (q > 0 && (ld[q - 1] > v || (ld[q - 1] == v && lj[q - 1] > j))) {
+                            ld[q] = ld[q - 1];
+                            lj[q] = lj[q - 1];
+                            --q;
+                        }
+                        ld[q] = v;
+                        lj[q] = j;
+                    }
                     float msum = 0.f;
                     for (int p = 0; p < k; ++p) {
                         const float dd = sqrtf(ws.ld[L][p]);
