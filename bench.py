@@ -46,13 +46,14 @@ COMPARES_PER_SM_CLK = 64     # FP32 compare throughput per SM per clock
 MUFU_PER_SM_CLK = 16         # special-function (square root) throughput per SM per clock
 FMA_LANES_PER_SM_CLK = 128   # FP32 add / FMA lane-operations per SM per clock
 # DRAM bytes (read + write) per pair-subspace evaluation, from one ncu capture
-# of each kernel (dram__bytes_read.sum + dram__bytes_write.sum): the tree join
-# on one 32-subspace chunk at N = 31,693 (7.83 MB + 3.97 MB), the tensor-core
-# join on one block of 256 subspaces at N = 31,693 (0.35 MB + 0.98 MB).  Both
-# kernels read their candidates from L2, so DRAM traffic grows with the
-# evaluations only through the outputs and the row copies.
-TREE_DRAM_BYTES_PER_EVAL = (7.829248e6 + 3.973376e6) / (31693 * 31692 * 32)
-TC_DRAM_BYTES_PER_EVAL = (0.35e6 + 0.98e6) / (31693 * 31692 * 256)
+# of each kernel as it stands (dram__bytes_read.sum + dram__bytes_write.sum):
+# the tree join on one 32-subspace chunk at N = 31,693 (7.83 MB + 5.01 MB),
+# the tensor-core join on one block of 256 subspaces at N = 31,693 (354 MB +
+# 982 MB: its per-query writes scatter over 256 output rows, which the L2
+# cannot hold).  Both kernels read their candidates from L2, so DRAM traffic
+# grows with the evaluations only through the outputs and the row copies.
+TREE_DRAM_BYTES_PER_EVAL = (7.8336e6 + 5.005824e6) / (31693 * 31692 * 32)
+TC_DRAM_BYTES_PER_EVAL = (354.470144e6 + 981.903872e6) / (31693 * 31692 * 256)
 
 
 def _load_peaks():
@@ -305,7 +306,7 @@ def run_ours(args, rank, world, dist):
                 "executed_basis": "64-row steps of the candidate streams loaded and evaluated over all steps "
                                   "(the rest skipped by their box bound, which proves every pair fails), "
                                   "counted by the kernel during the timed steps",
-                "traffic_basis": "DRAM bytes per launch: an ncu capture of one 32-subspace chunk (11.8 MB for "
+                "traffic_basis": "DRAM bytes per launch: an ncu capture of one 32-subspace chunk (12.8 MB for "
                                  "3.2e10 evaluations) scaled by the launch's evaluations",
                 "peak_basis": f"{props.multi_processor_count} SMs x {COMPARES_PER_SM_CLK} FP32 "
                               f"compares/clk x {max_mhz:.0f} MHz (one compare per pair-subspace "
@@ -315,20 +316,21 @@ def run_ours(args, rank, world, dist):
                 "frac_of_measured_alu": (achieved / measured_alu) if achieved else None}
 
     def tensor_roofline(trace, steps):
-        """Tensor roofline of the tensor-core join: 2 x 16 FLOPs (K = 16, FP16 or BF16)
-        per (pair, subspace) evaluation against the measured dense BF16 peak (FP16 runs
-        at the same rate)."""
+        """Tensor roofline of the tensor-core join: 2 x 32 FLOPs per (pair, subspace)
+        evaluation (two K = 16 MMAs, over the high and the low parts of the squared
+        differences, FP16 or BF16) against the measured dense BF16 peak (FP16 runs at
+        the same rate)."""
         tc_ms, tc_launches = trace["join_tc"]
-        flops = 2.0 * 16 * evals_per_step * steps
+        flops = 2.0 * 32 * evals_per_step * steps
         achieved = flops / (tc_ms / 1e3) / 1e12 if tc_ms > 0 else None
         peak = PEAKS.get("bf16_tflops_sustained") or PEAKS.get("bf16_tflops") or 1400.0
         return {"bound": "tensor", "kernel": "join_tc", "achieved": achieved, "peak": peak,
                 "unit": "TFLOP/s", "frac": (achieved / peak) if achieved else None,
                 "traffic": TC_DRAM_BYTES_PER_EVAL * evals_per_step,
-                "traffic_basis": "DRAM bytes per launch: an ncu capture of one 256-subspace block (1.33 MB "
+                "traffic_basis": "DRAM bytes per launch: an ncu capture of one 256-subspace block (1.34 GB "
                                  "for 2.6e11 evaluations) scaled by the launch's evaluations",
                 "peak_basis": "measured dense BF16 GEMM, sustained (MEASURED_PEAKS.json); FP16 "
-                              "has the same dense rate",
+                              "has the same dense rate; 64 FLOPs per evaluation (two K = 16 MMAs)",
                 "evals_per_s": evals_per_step * steps / (tc_ms / 1e3) if tc_ms > 0 else None,
                 "kernel_ms_per_launch": tc_ms / max(tc_launches, 1)}
 
@@ -349,8 +351,9 @@ def run_ours(args, rank, world, dist):
                                         if not kn.startswith("_")},
                   "gpu_launches": int(sum(v[1] for kn, v in tc_trace.items() if not kn.startswith("_"))),
                   "clocks": tc_clocks,
-                  "exactness": f"bit-identical to the plain FP32 join ({form_name[form][3:].upper()} "
-                               f"filter, every survivor recomputed in FP32)"}
+                  "exactness": (f"eps counts, kNN lists, in-degrees and kNN means bit-identical to the plain "
+                                f"FP32 join; mean eps distances from the {form_name[form][3:].upper()} "
+                                f"high/low accumulator, within 1e-5")}
 
     # end to end through the C ABI with host buffers
     e2e = None
@@ -492,6 +495,7 @@ def run_serving(args, count=None, with_tc=None):
                 "clocks": clk.summary()}
 
     main = stream(head)
+    main["fused_launches"], main["fused_requests"] = snaps.snaps_serving_stats(ctx)
     tc = stream(snaps.SNAPS_TC_F16) if with_tc else None
     for h in handles:
         snaps.snaps_release(h)
@@ -506,6 +510,8 @@ def run_serving(args, count=None, with_tc=None):
         "p99_latency_ms": main["p99_latency_ms"],
         "p50_queue_ms": main["p50_queue_ms"],
         "p99_queue_ms": main["p99_queue_ms"],
+        "shared_launches": main["fused_launches"],
+        "requests_in_shared_launches": main["fused_requests"],
         "requests": main["requests"],
         "failed": main["failed"],
         "makespan_s": main["makespan_s"],
@@ -821,7 +827,7 @@ def main():
             sv = run_serving(args, count=args.serving_leg, with_tc=True)
             keep = ("value", "unit", "p50_latency_ms", "p99_latency_ms", "p50_queue_ms", "p99_queue_ms",
                     "requests", "failed", "makespan_s", "arrival_rate_per_s", "mean_service_alone_s",
-                    "config", "clocks")
+                    "shared_launches", "requests_in_shared_launches", "config", "clocks")
             res["serving"] = {key: sv[key] for key in keep}
             res["serving"]["tc_f16"] = {key: sv["tc_f16"][key] for key in
                                         ("value", "p50_latency_ms", "p99_latency_ms", "p50_queue_ms",
