@@ -344,7 +344,14 @@ typedef struct snaps_result {
 
 /* Queue a request.  The context's scheduler admits queued requests in
  * arrival order as soon as a slot and enough of the HBM budget are free, so
- * requests that arrive while others run overlap them on the device.
+ * requests that arrive while others run overlap them on the device.  A
+ * request of more than 2e11 candidate-pair evaluations (n (n - 1) x
+ * subspaces) runs in parts of its subspace list, each about that much work;
+ * a part holds a multiple of 32 subspaces in the FP32 form (one subspace at a
+ * time once 32 would exceed 2e11) and a multiple of 256 in the tensor-core
+ * forms, whose launches cost a whole 256-subspace block.  Between parts its
+ * slot serves the small requests queued behind it (see snaps_serving_stats),
+ * so they wait for one part, not for the whole request.
  * Errors: EINVAL (malformed request), ENOMEM (the request alone exceeds the
  * budget). */
 snaps_status snaps_submit(snaps_ctx *ctx, const snaps_request *req, uint64_t *ticket);

@@ -935,6 +935,101 @@ snaps_status run_batch(snaps_ctx *ctx, const std::vector<JobSpec> &jobs, cudaStr
     return SNAPS_OK;
 }
 
+// A request of more than kUnitWork candidate-pair evaluations runs in parts
+// of its subspace list, each about that much work, and between parts the slot
+// serves the small requests queued meanwhile: a large request then delays them
+// by one part, not by all of its work.  A part holds whole launch units: a
+// multiple of 32 subspaces (one subset-tree chunk, when the list runs chunk by
+// chunk) in the FP32 form, a multiple of a tensor-core block in the
+// tensor-core forms, whose launch costs a full block however few subspaces it
+// carries.
+constexpr double kUnitWork = 2.0e11;
+
+int part_size(const JobSpec &j, double pairs)
+{
+    const int unit = (j.precision & 0xFFu) == SNAPS_FP32 ? (1 << kTreeLowBits) : kTcBlockWidth;
+    const int per = std::max(1, (int)(kUnitWork / pairs));
+    if (per < unit && (j.precision & 0xFFu) == SNAPS_FP32) return per;
+    return std::max(unit, per / unit * unit);
+}
+
+// Complete finished requests and wake their pollers.
+void complete(snaps_ctx *ctx, const std::vector<Request *> &done, snaps_status s, size_t grow)
+{
+    {
+        std::lock_guard<std::mutex> lk(ctx->q_mu);
+        ctx->reserved -= grow;
+        for (Request *r : done) {
+            r->status = s;
+            r->done = true;
+            r->running = false;
+            r->t_done = Clock::now();
+            r->req.pop->inflight.fetch_sub(1);
+        }
+    }
+    ctx->done_cv.notify_all();
+    ctx->q_cv.notify_all();
+}
+
+snaps_status run_fused(snaps_ctx *ctx, const std::vector<Request *> &batch, Slot *slot)
+{
+    if (batch.size() == 1) return run_job(ctx, spec_of(batch[0]), slot->stream, slot->scratch, slot->ctrl, true);
+    std::vector<JobSpec> jobs;
+    for (Request *b : batch) jobs.push_back(spec_of(b));
+    const snaps_status s = run_batch(ctx, jobs, slot->stream, slot->scratch, slot->ctrl);
+    ctx->fused_launches.fetch_add(1);
+    ctx->fused_requests.fetch_add((long long)batch.size());
+    return s;
+}
+
+// Between the parts of a large request: the fusable requests at the head of
+// the queue whose scratch fits the slot's as it is (no allocation), run
+// together.
+void serve_waiting(snaps_ctx *ctx, Slot *slot)
+{
+    std::vector<Request *> batch;
+    {
+        std::lock_guard<std::mutex> lk(ctx->q_mu);
+        size_t need = 0;
+        while (!ctx->queue.empty() && (int)batch.size() < kFuseMaxBatch) {
+            Request *h = ctx->queue.front();
+            if (!h->fusable || need + h->footprint + 4096 > slot->scratch.cap) break;
+            ctx->queue.pop_front();
+            need += h->footprint + 4096;
+            h->running = true;
+            h->t_admit = Clock::now();
+            batch.push_back(h);
+        }
+    }
+    if (batch.empty()) return;
+    complete(ctx, batch, run_fused(ctx, batch, slot), 0);
+}
+
+// Run one request, in parts when it is large.
+snaps_status run_request(snaps_ctx *ctx, Request *r, Slot *slot)
+{
+    const JobSpec full = spec_of(r);
+    const double pairs = (double)full.pop->n * (double)(full.pop->n - 1);
+    if (pairs * full.n_masks <= kUnitWork) return run_job(ctx, full, slot->stream, slot->scratch, slot->ctrl, true);
+    const int per = part_size(full, pairs);
+    if (per >= full.n_masks) return run_job(ctx, full, slot->stream, slot->scratch, slot->ctrl, true);
+    const size_t n = (size_t)full.pop->n;
+    snaps_status s = SNAPS_OK;
+    for (int m0 = 0; m0 < full.n_masks && s == SNAPS_OK; m0 += per) {
+        JobSpec part = full;
+        const int m = std::min(per, full.n_masks - m0);
+        part.masks = full.masks + m0;
+        part.n_masks = m;
+        if (full.eps) part.eps = full.eps + m0;
+        if (full.scores) part.scores = full.scores + (size_t)m0 * 4 * n;
+        if (full.norm) part.norm = full.norm + (size_t)m0 * 4 * n;
+        if (full.top) part.top = full.top + (size_t)m0 * 4 * (size_t)full.top_n;
+        s = run_job(ctx, part, slot->stream, slot->scratch, slot->ctrl, true);
+        if (s == SNAPS_OK && m0 + per < full.n_masks) serve_waiting(ctx, slot);
+    }
+    return s;
+}
+
 void worker_loop(snaps_ctx *ctx, Slot *slot)
 {
     cudaSetDevice(ctx->device);
@@ -982,29 +1077,8 @@ void worker_loop(snaps_ctx *ctx, Slot *slot)
                 ctx->q_cv.wait(lk);
             }
         }
-        snaps_status s;
-        if (batch.size() == 1) {
-            s = run_job(ctx, spec_of(batch[0]), slot->stream, slot->scratch, slot->ctrl, true);
-        } else {
-            std::vector<JobSpec> jobs;
-            for (Request *b : batch) jobs.push_back(spec_of(b));
-            s = run_batch(ctx, jobs, slot->stream, slot->scratch, slot->ctrl);
-            ctx->fused_launches.fetch_add(1);
-            ctx->fused_requests.fetch_add((long long)batch.size());
-        }
-        {
-            std::lock_guard<std::mutex> lk(ctx->q_mu);
-            ctx->reserved -= grow;
-            for (Request *r : batch) {
-                r->status = s;
-                r->done = true;
-                r->running = false;
-                r->t_done = Clock::now();
-                r->req.pop->inflight.fetch_sub(1);
-            }
-        }
-        ctx->done_cv.notify_all();
-        ctx->q_cv.notify_all();
+        const snaps_status s = batch.size() == 1 ? run_request(ctx, batch[0], slot) : run_fused(ctx, batch, slot);
+        complete(ctx, batch, s, grow);
     }
 }
 

@@ -161,3 +161,47 @@ def test_small_requests_share_launches():
             snaps.snaps_release(p)
     finally:
         snaps.snaps_destroy(ctx)
+
+
+def test_large_request_runs_in_parts_and_lets_small_ones_through():
+    """A request of more than 2e11 pair evaluations runs in parts of its
+    subspace list; small requests queued behind it on the one slot are served
+    between parts, so they finish before it does.  Every result equals the
+    request alone."""
+    ctx = snaps.snaps_create(0)
+    try:
+        snaps.snaps_set_slots(ctx, 1)
+        allm = snaps_inputs.all_masks()
+        big_n = 20000
+        big_pop = snaps.snaps_index(ctx, snaps_inputs.population(big_n, 4))
+        big_masks = allm[::16][:1536]          # 4e8 pairs x 1,536 subspaces: three parts or more
+        big_sc = torch.empty((big_masks.size, 4, big_n), device="cuda")
+        big_tp = np.zeros((big_masks.size, 4, 100), dtype=np.int32)  # a host output too
+        pop = snaps.snaps_index(ctx, snaps_inputs.population(900, 5))
+        rng = np.random.default_rng(4)
+        small = []
+        for _ in range(6):
+            masks = rng.choice(allm, size=3, replace=False).astype(np.uint16)
+            small.append((masks, torch.empty((3, 4, 900), device="cuda")))
+        torch.cuda.synchronize()
+        t_big = snaps.snaps_submit(ctx, big_pop, big_masks, 10, scores=big_sc, top=big_tp, top_n=100)
+        t_small = [snaps.snaps_submit(ctx, pop, m, 10, scores=sc) for m, sc in small]
+        r_small = [snaps.snaps_poll(ctx, t, -1) for t in t_small]
+        r_big = snaps.snaps_poll(ctx, t_big, -1)
+        assert r_big.status == snaps.SNAPS_OK and all(r.status == snaps.SNAPS_OK for r in r_small)
+        # every small request was done while the large one still ran
+        assert max(r.latency_us for r in r_small) < r_big.latency_us
+        torch.cuda.synchronize()
+        a_sc = np.zeros((big_masks.size, 4, big_n), dtype=np.float32)
+        a_tp = np.zeros_like(big_tp)
+        snaps.snaps_scores(big_pop, big_masks, 10, scores=a_sc, top=a_tp, top_n=100)
+        np.testing.assert_array_equal(big_sc.cpu().numpy(), a_sc)
+        np.testing.assert_array_equal(big_tp, a_tp)
+        for masks, sc in small:
+            a = np.zeros((3, 4, 900), dtype=np.float32)
+            snaps.snaps_scores(pop, masks, 10, scores=a)
+            np.testing.assert_array_equal(sc.cpu().numpy(), a)
+        snaps.snaps_release(pop)
+        snaps.snaps_release(big_pop)
+    finally:
+        snaps.snaps_destroy(ctx)
