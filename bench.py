@@ -52,7 +52,7 @@ FMA_LANES_PER_SM_CLK = 128   # FP32 add / FMA lane-operations per SM per clock
 # 982 MB: its per-query writes scatter over 256 output rows, which the L2
 # cannot hold).  Both kernels read their candidates from L2, so DRAM traffic
 # grows with the evaluations only through the outputs and the row copies.
-TREE_DRAM_BYTES_PER_EVAL = (7.8336e6 + 5.005824e6) / (31693 * 31692 * 32)
+TREE_DRAM_BYTES_PER_EVAL = (7.82208e6 + 3.229696e6) / (31693 * 31692 * 32)
 TC_DRAM_BYTES_PER_EVAL = (354.470144e6 + 981.903872e6) / (31693 * 31692 * 256)
 
 
@@ -306,7 +306,7 @@ def run_ours(args, rank, world, dist):
                 "executed_basis": "64-row steps of the candidate streams loaded and evaluated over all steps "
                                   "(the rest skipped by their box bound, which proves every pair fails), "
                                   "counted by the kernel during the timed steps",
-                "traffic_basis": "DRAM bytes per launch: an ncu capture of one 32-subspace chunk (12.8 MB for "
+                "traffic_basis": "DRAM bytes per launch: an ncu capture of one 32-subspace chunk (11.1 MB for "
                                  "3.2e10 evaluations) scaled by the launch's evaluations",
                 "peak_basis": f"{props.multi_processor_count} SMs x {COMPARES_PER_SM_CLK} FP32 "
                               f"compares/clk x {max_mhz:.0f} MHz (one compare per pair-subspace "

@@ -38,11 +38,17 @@
 // and stored pair-planar (common.cuh); every row carries its original index in
 // float 15, and lists, ties and outputs use original indices, so results do
 // not depend on the order.  A query's stream starts at its own tile -- its
-// neighbourhood in those features -- and wraps around.  The first 256
-// candidates (the set-up phase, out of line) go straight into the lists: the
-// walk's node values are transposed through shared memory so that lane L
-// scans subspace L's values and keeps its list privately.  The thresholds then
-// start tight instead of sending every early candidate to the flush.
+// neighbourhood in those features -- and wraps around.  A set-up phase (out
+// of line) first bounds every subspace's k-th distance from the first 1,024
+// candidates of the stream: each lane keeps, per subspace, the smallest of its
+// own candidates' distances, and the k-th smallest of those 32 group minima
+// is an upper bound (k distinct candidates lie at or below it).  Each list
+// starts as k placeholder entries at that bound, so the thresholds start
+// tight, and the main loop then walks the whole stream, the set-up's steps
+// included; only candidates at or below the bound become kNN events.  This
+// costs a fold and a minimum per node and one 32-value sort per subspace,
+// where inserting the early candidates one by one into the lists cost a
+// serial list update for each of the many that improved an early list.
 //
 // Two CTAs share an SM (16 warps with k <= 16), with no barriers between
 // warps: every warp streams at its own pace.
@@ -60,7 +66,7 @@ namespace {
 constexpr int kLB = kTreeLowBits;  // 5
 constexpr int kW = kTreeWidth;     // 32 subspaces per chunk
 constexpr int kTile = 256;
-constexpr int kInit = 256;         // candidates handled lane-per-subspace first (one tile)
+constexpr int kInit = 1024;        // candidates that bound the k-th distances in the set-up phase
 constexpr int kTBuf = 1024;        // event tuples buffered per warp
 constexpr int kTFlushAt = kTBuf - 64;  // a node appends at most 64 tuples
 constexpr int kFlushMin = 16;      // tuples that trigger an end-of-step flush
@@ -116,7 +122,7 @@ constexpr DfsPos make_dfs_pos() {
     return t;
 }
 __constant__ DfsPos kDfsPos = make_dfs_pos();
-static_assert(kTBuf * 2 >= kW * 64, "the set-up transpose fits the tuple buffer");
+static_assert(kTBuf * 2 >= kW * (kW + 1), "the set-up transpose fits the tuple buffer");
 static_assert(kTBuf * ((1u << 20) + 1u) < (1ull << 32), "a flush's eps partial sums fit 32 bits");
 static_assert(kDfs.node[1] == 16 && kDfs.parent[kW / 2] > 0, "DFS order as expected");
 
@@ -288,26 +294,6 @@ __device__ __forceinline__ void walk(float2 (&v)[kW], const float2 (&d)[15], con
     }
 }
 
-// The walk without thresholds (set-up phase): every node's two values go to
-// the transpose buffer as soon as they are folded -- row L (the node's
-// subspace), columns lane ^ L (candidate a) and 32 + (lane ^ L) (candidate b),
-// so that these stores and the row scans that follow touch 32 different banks.
-template <int P>
-__device__ __forceinline__ void fold_store(float2 (&v)[kW], const float2 (&d)[15], float *stg, unsigned lane)
-{
-    if constexpr (P < kW) {
-        if constexpr (P > 0) {
-            constexpr int b = kDfs.bit[P];
-            constexpr int par = kDfs.parent[P];
-            v[P] = __ffma2_rn(d[b], d[b], v[par]);
-        }
-        constexpr int L = kDfs.node[P];
-        stg[L * 64 + (lane ^ L)] = v[P].x;
-        stg[L * 64 + 32 + (lane ^ L)] = v[P].y;
-        fold_store<P + 1>(v, d, stg, lane);
-    }
-}
-
 // Append the kNN / eps tuples of this lane's triggered subspaces (bit L of
 // `bits`: either candidate fell below subspace L's pass threshold in the
 // walk).  Every round each lane takes its lowest remaining subspace, so the
@@ -389,8 +375,51 @@ __device__ __forceinline__ float2 root_fold(const float2 (&d)[15], uint32_t high
     return v;
 }
 
+// Sorts a[0..N) ascending (bitonic network, N a power of two).
+template <int N>
+__device__ __forceinline__ void sort_net(float (&a)[N])
+{
+#pragma unroll
+    for (int size = 2; size <= N; size <<= 1)
+#pragma unroll
+        for (int stride = size >> 1; stride > 0; stride >>= 1)
+#pragma unroll
+            for (int e = 0; e < N; ++e) {
+                const int f = e ^ stride;
+                if (f > e) {
+                    const float x = a[e], y = a[f];
+                    const bool up = (e & size) == 0;
+                    a[e] = up ? fminf(x, y) : fmaxf(x, y);
+                    a[f] = up ? fmaxf(x, y) : fminf(x, y);
+                }
+            }
+}
+
+// The walk with a running minimum per node (set-up phase): mn[L] <- min(mn[L],
+// both candidates' squared distances in subspace L).
+template <int P>
+__device__ __forceinline__ void fold_min(float2 (&v)[kW], const float2 (&d)[15], float (&mn)[kW])
+{
+    if constexpr (P < kW) {
+        if constexpr (P > 0) {
+            constexpr int b = kDfs.bit[P];
+            constexpr int par = kDfs.parent[P];
+            v[P] = __ffma2_rn(d[b], d[b], v[par]);
+        }
+        constexpr int L = kDfs.node[P];
+        mn[L] = fminf(mn[L], fminf(v[P].x, v[P].y));
+        fold_min<P + 1>(v, d, mn);
+    }
+}
+
 // Set-up phase (see the kernel), kept out of line so that its registers do
-// not add to the main loop's.
+// not add to the main loop's.  Each lane folds its candidates of the first
+// steps and keeps, per subspace, the smallest squared distance among them: 32
+// groups of candidates (one per lane) and their 32 minima per subspace.  The
+// k-th smallest of those minima bounds the subspace's k-th distance from
+// above -- k distinct candidates lie at or below it -- and its list starts as
+// k entries (bound, largest index), which any candidate at or below the bound
+// displaces.  The steps themselves are walked again by the main loop.
 template <int KMAX, bool CMP>
 __device__ __noinline__ void setup_phase(int ws_off, const float4 *__restrict__ x, int64_t i, int64_t n,
                                          uint32_t high, uint32_t active, int64_t s0, int64_t n_steps, int k)
@@ -398,51 +427,58 @@ __device__ __noinline__ void setup_phase(int ws_off, const float4 *__restrict__ 
     WarpState<KMAX> &ws = *reinterpret_cast<WarpState<KMAX> *>(tree_smem + ws_off);
     const unsigned lane = dev::lane_id();
     const float2 *nxq = ws.nxq;
-    const uint32_t L = lane;
-    const bool mine = (active >> L) & 1u;
-    const float e2 = ws.eps2[L];
-    const float sc = ws.escale[L];
-    float T = ws.T[L];
-    int Tj = ws.Tj[L], Tp = ws.Tp[L];
-    int cnt = 0;
-    unsigned long long qs = 0;
-    float *stg = reinterpret_cast<float *>(ws.tbuf);  // [32][64], columns XOR-swizzled by row
+    float mn[kW];
+#pragma unroll
+    for (int L = 0; L < kW; ++L) mn[L] = CUDART_INF_F;
     const int64_t init_steps = std::min<int64_t>(kInit / 64, n_steps);
-    StepRows r;
-    load_step(x, s0 % n_steps, lane, r);
     for (int64_t u = 0; u < init_steps; ++u) {
         const int64_t step = (s0 + u) % n_steps;
+        StepRows r;
+        load_step(x, step, lane, r);
         float2 d[15];
 #pragma unroll
         for (int f = 0; f < 15; ++f) d[f] = __fadd2_rn(feat_pair(r, f), nxq[f]);
-        const int oa = __float_as_int(r.r[7].z), ob = __float_as_int(r.r[7].w);
-        // the next step's rows load while this one is folded and scanned
-        if (u + 1 < init_steps) load_step(x, (s0 + u + 1) % n_steps, lane, r);
+        if ((i >> 6) == step) {
+            // the query itself is in this step: make it infinitely far
+            const int64_t ja = step * 64 + lane, jb = ja + 32;
+#pragma unroll
+            for (int f = 0; f < 15; ++f) {
+                if (ja == i) d[f].x = CUDART_INF_F;
+                if (jb == i) d[f].y = CUDART_INF_F;
+            }
+        }
+        // (padding rows are +inf and fold to +inf)
         float2 v[kW];
         v[0] = root_fold<CMP>(d, high);
-        __syncwarp();
-        fold_store<0>(v, d, stg, lane);
-        __syncwarp();
-        for (int c = 0; c < 64; ++c) {
-            const float val = stg[L * 64 + (c ^ L)];
-            const int oc = __shfl_sync(dev::kFull, c < 32 ? oa : ob, c & 31);
-            const int64_t row = step * 64 + c;
-            // the query itself and padding rows take no part
-            const bool use = mine && row < n && row != i;
-            if (use && val <= e2) {
-                ++cnt;
-                qs += dev::eps_quant(val, sc);
-            }
-            if (use) list_offer(ws.ld[L], ws.lj[L], k, val, oc, T, Tj, Tp);
-        }
+        fold_min<0>(v, d, mn);
     }
+    // transpose: row L <- the 32 lanes' minima of subspace L
+    float *stg = reinterpret_cast<float *>(ws.tbuf);  // [32][33]
     __syncwarp();
-    ws.T[L] = T;
-    ws.Tj[L] = Tj;
-    ws.Tp[L] = Tp;
-    ws.cnt[L] = cnt;
-    ws.esum[L] = qs;
-    ws.tc[L] = mine ? fmaxf(next_up(T), eps_up(e2)) : -CUDART_INF_F;
+#pragma unroll
+    for (int L = 0; L < kW; ++L) stg[L * 33 + lane] = mn[L];
+    __syncwarp();
+    const uint32_t L = lane;
+    float g[kW];
+#pragma unroll
+    for (int c = 0; c < kW; ++c) g[c] = stg[L * 33 + c];
+    sort_net<kW>(g);
+    float bound = g[0];
+#pragma unroll
+    for (int c = 1; c < kW; ++c) bound = (c == k - 1) ? g[c] : bound;
+    __syncwarp();
+    const bool mine = (active >> L) & 1u;
+    const float e2 = ws.eps2[L];
+    if (mine && k > 0) {
+        for (int p = 0; p < k; ++p) {
+            ws.ld[L][p] = bound;
+            ws.lj[L][p] = 0x7fffffff;
+        }
+        ws.T[L] = bound;
+        ws.Tj[L] = 0x7fffffff;
+        ws.Tp[L] = 0;
+    }
+    ws.tc[L] = mine ? fmaxf(next_up(ws.T[L]), eps_up(e2)) : -CUDART_INF_F;
     ws.tcd[kDfsPos.pos[L]] = ws.tc[L];
     update_tcmax(ws);
 }
@@ -535,9 +571,9 @@ __global__ void __launch_bounds__(CW * 32, kCtasPerSm<CW>)
         const int init_steps = std::min(kInit / 64, n_steps);
         const float2 *box = s.box ? s.box + (w / n) * s.box_stride : nullptr;
         const int n_high = __popc(high);
-        int wbase = init_steps, next_w = init_steps;
+        int wbase = 0, next_w = 0;  // the set-up's steps are walked again
         unsigned live = 0u;
-        int taken = 0;  // steps of the stream loaded after the set-up phase
+        int taken = 0;  // steps of the stream loaded by the main loop
         auto take = [&]() -> int {
             while (live == 0u) {
                 if (next_w >= n_steps) return -1;
@@ -623,7 +659,7 @@ __global__ void __launch_bounds__(CW * 32, kCtasPerSm<CW>)
         }
         if (tcount > 0) flush_tuples<KMAX>(ws_off, tcount, k);
         if (lane == 0) {
-            ws.stat_loaded += (unsigned long long)(taken + init_steps);
+            ws.stat_loaded += (unsigned long long)(taken + init_steps);  // the set-up's loads included
             ws.stat_total += (unsigned long long)n_steps;
         }
 
