@@ -113,6 +113,11 @@ def parse():
                     help="instead of the batching workload, time one call over 256 seeded subspaces of each "
                          "dimension (all of them where fewer exist) through the tensor-core form and the "
                          "plain form, N = --n objects")
+    ap.add_argument("--precision-config", action="store_true",
+                    help="instead of the batching workload, the precision workload: N = 250,000 objects "
+                         "(--precision-n), the plain FP32 join against both tensor-core forms on 256 "
+                         "subspaces (eight whole 32-subspace chunks) and on 256 random subspaces")
+    ap.add_argument("--precision-n", type=int, default=250_000)
     ap.add_argument("--serving-max-n", type=int, default=100000)
     ap.add_argument("--serving-max-masks", type=int, default=64)
     ap.add_argument("--serving-slots", type=int, default=4)
@@ -624,6 +629,70 @@ def run_by_dimension(args):
                                    f"form without the grid index; one warm-up call, one timed call each"}}
 
 
+def run_precision(args):
+    """Precision workload: the plain FP32 join and both tensor-core forms on
+    the same population and subspaces, two subspace sets of 256 each: eight
+    whole 32-subspace chunks (the all-subspace workload's shape, where the
+    plain form runs the subspace-batched tree join) and 256 random subspaces
+    (where it joins each subspace on its own).  One warm-up call on a small
+    population, then one timed call per form and set (library trace on the
+    launch stream).  The errors against the FP64 oracle on sampled queries
+    at this size come from tests/test_gpu_precision.py."""
+    import torch
+
+    import paper_2405_20176_b300 as snaps
+
+    torch.cuda.set_device(0)
+    n = args.precision_n
+    x = snaps_inputs.population(n, 0)
+    sets = {"chunks": snaps_inputs.chunk_sample(8, SAMPLE_SEED),
+            "random": snaps_inputs.mask_sample(256, SAMPLE_SEED)}
+    forms = {"fp32": snaps.SNAPS_FP32, "tc_f16": snaps.SNAPS_TC_F16, "tc_bf16": snaps.SNAPS_TC_BF16}
+    ctx = snaps.snaps_create(0)
+    warm = snaps.snaps_index(ctx, torch.from_numpy(snaps_inputs.population(4096, 1)).cuda())
+    sc = torch.empty((256, 4, 4096), device="cuda")
+    for m in sets.values():
+        for prec in forms.values():
+            snaps.snaps_scores(warm, m, args.k, precision=prec, scores=sc)
+    torch.cuda.synchronize()
+    snaps.snaps_release(warm)
+    pop = snaps.snaps_index(ctx, torch.from_numpy(x).cuda())
+    sc = torch.empty((256, 4, n), device="cuda")
+    top = torch.empty((256, 4, 100), dtype=torch.int32, device="cuda")
+    rows = {}
+    with ClockSampler(0) as clk:
+        for sname, m in sets.items():
+            row = {}
+            for fname, prec in forms.items():
+                snaps.snaps_trace(ctx, True)
+                ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                ev0.record()
+                snaps.snaps_scores(pop, m, args.k, precision=prec, scores=sc[:m.size], top=top[:m.size],
+                                   top_n=100)
+                ev1.record()
+                torch.cuda.synchronize()
+                tr = snaps.snaps_trace_read(ctx)
+                snaps.snaps_trace(ctx, False)
+                ms = ev0.elapsed_time(ev1)
+                row[fname] = {"ms": ms, "objects_x_subspaces_per_s": float(n) * m.size / (ms / 1e3),
+                              "evals_per_s": float(n) * (n - 1) * m.size / (ms / 1e3),
+                              "phase_ms": {k: v[0] for k, v in tr.items() if v[1]}}
+                print(f"[bench] precision {sname} {fname}: {ms:.1f} ms", file=sys.stderr, flush=True)
+            for fname in ("tc_f16", "tc_bf16"):
+                row[fname]["vs_plain"] = row["fp32"]["ms"] / row[fname]["ms"]
+            rows[sname] = row
+    snaps.snaps_release(pop)
+    snaps.snaps_destroy(ctx)
+    return {"metric": "objects*subspaces/s, tensor-core forms vs plain FP32 (precision workload)",
+            "unit": "objects*subspaces/s", "n": n, "k": args.k, "sets": rows, "clocks": clk.summary(),
+            "dtype": "f32 (plain), f16 / bf16 high+low parts with f32 accumulation (tensor-core forms)",
+            "data": "synthetic",
+            "config": {"workload": f"N={n} objects (seed 0); 'chunks': eight whole 32-subspace chunks "
+                                   f"(seed {SAMPLE_SEED}), 'random': 256 random subspaces (seed {SAMPLE_SEED}); "
+                                   f"k={args.k}, eps=0.05*sqrt(d); scores and top-100 on the device; one "
+                                   f"timed call per form and set after a warm-up on 4,096 objects"}}
+
+
 def run_rubin(args):
     """Rubin-scale leg: two-feature subspaces of a 5,000,000-object population
     through the grid index (sort-by-cell, Sec. 3.8.1), scores and top-100 on the
@@ -813,6 +882,9 @@ def main():
         return 0
     if args.by_dimension:
         print(json.dumps(run_by_dimension(args)))
+        return 0
+    if args.precision_config:
+        print(json.dumps(run_precision(args)))
         return 0
     dist = None
     if world > 1:

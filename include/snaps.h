@@ -82,6 +82,15 @@ typedef enum snaps_status {
 #define SNAPS_TC_F16 1u          /* tensor-core contraction, high/low FP16 parts, exact FP32 recompute near
                                   * eps and the k-th distance */
 #define SNAPS_TC_BF16 2u         /* the same with BF16 parts: a 4x wider margin, more recomputes */
+/* The tensor-core forms join subspaces in blocks of 256 (sorted by
+ * dimension), and a block costs about the same however few it carries.  A
+ * block is formed only with at least a minimum fill of subspaces: the
+ * context's value from snaps_set_tc_min_fill, else snaps_autotune_tc's choice
+ * for the population's size class, else SNAPS_TC_MIN_FILL.  Subspaces left
+ * over (every one of a request smaller than that) take the plain FP32
+ * routes, which return the same counts, kNN lists and in-degrees. */
+#define SNAPS_TC_MIN_FILL 128
+#define SNAPS_TC_NEVER 257       /* a minimum fill that keeps every subspace off the tensor cores */
 #define SNAPS_INDEX_GRID 0x100u  /* subspaces of <= 4 features always take the grid index */
 #define SNAPS_INDEX_NONE 0x200u  /* no grid index: every subspace is joined by brute force */
 /* Without either index flag, subspaces of <= 4 features take the grid index
@@ -305,12 +314,41 @@ typedef struct snaps_tune_entry {
  * Errors: EINVAL, ENOMEM, ECUDA. */
 snaps_status snaps_autotune(snaps_pop *pop, int k, snaps_tune_entry *out, void *stream);
 
+/* Measurements and choice of snaps_autotune_tc. */
+typedef struct snaps_tc_tune {
+    int min_fill;     /* fewest subspaces for which a tensor-core block pays, 1..SNAPS_TC_NEVER */
+    double ms_block;  /* one tensor-core block of 256 subspaces of 3..12 features */
+    double ms_lone;   /* ms per subspace of the same set joined on its own in plain FP32 */
+} snaps_tc_tune;
+
+/* Choose the subspaces-per-block threshold of the tensor-core forms for
+ * populations of this one's size class (floor(log2 n)) and this k class.  It
+ * times one block of 256 subspaces of 3..12 features (a fixed pseudo-random
+ * choice) in `precision` (SNAPS_TC_F16 or SNAPS_TC_BF16) and 32 of them
+ * joined one at a time in plain FP32, on the population or, above
+ * SNAPS_TUNE_MAX_N objects, an evenly strided sample of it.  The block pays
+ * once it carries more subspaces than its time buys on their own:
+ * min_fill = ceil(ms_block / ms_lone), capped at SNAPS_TC_NEVER.  Later
+ * tensor-core calls on such populations form blocks only with at least that
+ * many subspaces (see SNAPS_TC_MIN_FILL).  The paper has no counterpart.
+ * out: host, or NULL.  The call synchronises `stream`.
+ * Errors: EINVAL (pop NULL, bad precision or k, fewer than 3 features, a
+ * population outside the unit range), ENOMEM, ECUDA. */
+snaps_status snaps_autotune_tc(snaps_pop *pop, int k, uint32_t precision, snaps_tc_tune *out, void *stream);
+
+/* Fix the minimum fill of tensor-core blocks for every later call on `ctx`,
+ * whatever the population's size: 1 puts every subspace of a tensor-core
+ * call on the tensor cores, SNAPS_TC_NEVER none; 0 goes back to the tuned or
+ * built-in choice.  Errors: EINVAL (ctx NULL, fill outside 0..SNAPS_TC_NEVER). */
+snaps_status snaps_set_tc_min_fill(snaps_ctx *ctx, int fill);
+
 /* Record a choice without timing it, for populations of n's size class and
  * this k class: e->d (2..4), e->grid, e->cell_mult (in (0, 64]; the times are
  * ignored).  Errors: EINVAL. */
 snaps_status snaps_autotune_set(snaps_ctx *ctx, int64_t n, int k, const snaps_tune_entry *e);
 
-/* Forget every recorded choice (the built-in rule applies again).
+/* Forget every recorded choice, the tensor-core minimum fills included (the
+ * built-in rules apply again; a fill set by snaps_set_tc_min_fill stays).
  * Errors: EINVAL (ctx NULL). */
 snaps_status snaps_autotune_clear(snaps_ctx *ctx);
 

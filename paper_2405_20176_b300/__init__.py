@@ -36,6 +36,8 @@ SNAPS_TC_BF16 = 2
 SNAPS_INDEX_GRID = 0x100
 SNAPS_INDEX_NONE = 0x200
 SNAPS_GRID_AUTO_N = 65536
+SNAPS_TC_MIN_FILL = 128
+SNAPS_TC_NEVER = 257
 SNAPS_STATIC_MAX_N = 32768
 SNAPS_STATIC_MAX_MASKS = 32768
 SNAPS_PHASE_INDEX, SNAPS_PHASE_JOIN_TREE, SNAPS_PHASE_JOIN_LANE, SNAPS_PHASE_NORM, SNAPS_PHASE_TOP, \
@@ -66,6 +68,10 @@ class snaps_request(ctypes.Structure):
 class snaps_tune_entry(ctypes.Structure):
     _fields_ = [("d", ctypes.c_int), ("grid", ctypes.c_int), ("cell_mult", ctypes.c_float),
                 ("ms_brute", ctypes.c_double), ("ms_grid", ctypes.c_double * 3)]
+
+
+class snaps_tc_tune(ctypes.Structure):
+    _fields_ = [("min_fill", ctypes.c_int), ("ms_block", ctypes.c_double), ("ms_lone", ctypes.c_double)]
 
 
 class snaps_result(ctypes.Structure):
@@ -115,6 +121,8 @@ def lib():
             "snaps_autotune": ([p, i32, p, p], i32),
             "snaps_autotune_clear": ([p], i32),
             "snaps_autotune_set": ([p, i64, i32, p], i32),
+            "snaps_autotune_tc": ([p, i32, u32, p, p], i32),
+            "snaps_set_tc_min_fill": ([p, i32], i32),
         }
         for name, (args, res) in sig.items():
             fn = getattr(L, name)
@@ -312,6 +320,19 @@ def snaps_autotune_set(ctx: int, n: int, k: int, d: int, grid: bool, cell_mult: 
 
 def snaps_autotune_clear(ctx: int) -> None:
     _check(lib().snaps_autotune_clear(ctx), "snaps_autotune_clear")
+
+
+def snaps_autotune_tc(pop: int, k: int, precision: int = SNAPS_TC_F16, stream=None) -> dict:
+    """Time one tensor-core block against subspaces joined on their own and
+    record the block's minimum fill for this population's size class."""
+    out = snaps_tc_tune()
+    _check(lib().snaps_autotune_tc(pop, k, precision, ctypes.byref(out), _stream(stream)), "snaps_autotune_tc")
+    return {"min_fill": out.min_fill, "ms_block": out.ms_block, "ms_lone": out.ms_lone}
+
+
+def snaps_set_tc_min_fill(ctx: int, fill: int) -> None:
+    """Fewest subspaces a tensor-core block carries on this context (0: tuned or built-in)."""
+    _check(lib().snaps_set_tc_min_fill(ctx, fill), "snaps_set_tc_min_fill")
 
 
 def snaps_scores_static(device: int, feat, masks, k: int, eps=None, flags: int = SNAPS_NORM_MINMAX,

@@ -121,6 +121,11 @@ struct snaps_ctx {
     // recorded by snaps_autotune
     std::mutex tune_mu;
     std::unordered_map<uint32_t, snaps_tune_entry> tune;
+    // fewest subspaces a tensor-core block carries, per (size class, k class),
+    // recorded by snaps_autotune_tc; a value set by snaps_set_tc_min_fill
+    // (> 0) overrides it for every size
+    std::unordered_map<uint32_t, int> tc_fill;
+    std::atomic<int> tc_fill_override{0};
 
     // tracing
     std::mutex tr_mu;
@@ -353,6 +358,18 @@ bool tune_lookup(snaps_ctx *ctx, int64_t n, int d, int k, snaps_tune_entry *e)
     return true;
 }
 
+// Fewest subspaces for which the tensor-core forms fill a block: the
+// context's override, else snaps_autotune_tc's choice for this size and k
+// class, else the built-in SNAPS_TC_MIN_FILL.
+int tc_min_fill(snaps_ctx *ctx, int64_t n, int k)
+{
+    const int o = ctx->tc_fill_override.load();
+    if (o > 0) return o;
+    std::lock_guard<std::mutex> g(ctx->tune_mu);
+    auto it = ctx->tc_fill.find(tune_key(n, 0, k));
+    return it == ctx->tc_fill.end() ? SNAPS_TC_MIN_FILL : it->second;
+}
+
 GridSpec make_grid(const JobSpec &j, int m, float eps2, float cell_mult)
 {
     const snaps_pop *p = j.pop;
@@ -436,14 +453,24 @@ Plan make_plan(const JobSpec &j)
         }
     }
     if (tc_form) {
-        // the tensor-core join takes any subspaces, 128 at a time; sorted by
-        // dimension, so that the threads of a warp see similar hit rates
+        // The tensor-core join takes any subspaces, a block of kTcBlockWidth
+        // at a time, sorted by dimension so that the threads of a warp see
+        // similar hit rates.  A block costs about the same however few
+        // subspaces it carries, so a block is formed only with at least
+        // min_fill of them; the subspaces left over (all of them in a small
+        // request) take the plain FP32 routes below, which return the same
+        // counts, lists and in-degrees.
         std::vector<int> order = rest;
         std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
             const int da = popc16(j.masks[a]), db = popc16(j.masks[b]);
             return da != db ? da < db : j.masks[a] < j.masks[b];
         });
-        const int nr = (int)order.size();
+        const int fill = std::max(1, tc_min_fill(j.pop->ctx, j.pop->n, j.k));
+        int nr = (int)order.size();
+        const int tail = nr % kTcBlockWidth;
+        if (fill > kTcBlockWidth) nr = 0;
+        else if (tail > 0 && tail < fill) nr -= tail;
+        rest.assign(order.begin() + nr, order.end());
         for (int b = 0; b < nr; b += kTcBlockWidth) {
             TcBlock blk{};
             for (int c = 0; c < kTcBlockWidth; ++c) {
@@ -462,7 +489,6 @@ Plan make_plan(const JobSpec &j)
             }
             pl.blocks.push_back(blk);
         }
-        return pl;
     }
     const int f = j.pop->f;
     const int n_chunk = f > kTreeLowBits ? 1 << (f - kTreeLowBits) : 1;
@@ -834,8 +860,8 @@ constexpr double kFuseMaxWork = 4.0e10;
 bool fusable_plan(const JobSpec &j, const Plan &pl)
 {
     const double work = (double)j.pop->n * (double)(j.pop->n - 1) * (double)j.n_masks;
-    return (j.precision & 0xFFu) == SNAPS_FP32 && pl.chunks.empty() && pl.grids.empty() && pl.blocks.empty() &&
-           !j.knn_idx && !j.knn_dist && !j.eps_count && !j.eps_mean && work <= kFuseMaxWork;
+    return pl.chunks.empty() && pl.grids.empty() && pl.blocks.empty() && !j.knn_idx && !j.knn_dist &&
+           !j.eps_count && !j.eps_mean && work <= kFuseMaxWork;
 }
 
 // Run fusable requests together: each gets its own outputs and scratch, and
@@ -1671,6 +1697,118 @@ snaps_status snaps_autotune(snaps_pop *pop, int k, snaps_tune_entry *out, void *
     return SNAPS_OK;
 }
 
+snaps_status snaps_autotune_tc(snaps_pop *pop, int k, uint32_t precision, snaps_tc_tune *out, void *stream)
+{
+    clear_error();
+    if (!pop) FAIL(SNAPS_EINVAL, "pop is NULL");
+    if (precision != SNAPS_TC_F16 && precision != SNAPS_TC_BF16)
+        FAIL(SNAPS_EINVAL, "precision must be SNAPS_TC_F16 or SNAPS_TC_BF16 (got %u)", precision);
+    if (!pop->unit_range) FAIL(SNAPS_EINVAL, "the tensor-core forms need every feature to span at most 1");
+    ON_DEVICE(pop->ctx->device);
+    snaps_ctx *ctx = pop->ctx;
+    const int64_t n = pop->n;
+    const int f = pop->f;
+    if (k < 1 || k > SNAPS_MAX_K || k > n - 1) FAIL(SNAPS_EINVAL, "k must be in 1..min(%d, n - 1)", SNAPS_MAX_K);
+    if (f < 3) FAIL(SNAPS_EINVAL, "the population needs >= 3 features");
+    cudaStream_t st = (cudaStream_t)stream;
+
+    // The subspaces timed: every subspace of 3..12 of the f features, in a
+    // fixed pseudo-random order (a multiplicative hash of the mask), the first
+    // kTcBlockWidth of them -- a block of mixed dimensions, as a request of
+    // random subspaces fills one.
+    std::vector<uint16_t> all;
+    for (uint32_t v = 1; v < (1u << f); ++v) {
+        const int d = popc16(v);
+        if (d >= 3 && d <= 12) all.push_back((uint16_t)v);
+    }
+    std::stable_sort(all.begin(), all.end(), [](uint16_t a, uint16_t b) {
+        return (uint32_t)(a * 2654435761u) < (uint32_t)(b * 2654435761u);
+    });
+    const int nb = (int)std::min<size_t>(all.size(), kTcBlockWidth);
+    const int nl = std::min(nb, 32);
+
+    // the population it times: this one, or an evenly strided sample of it
+    snaps_pop *tp = pop;
+    float *feat = nullptr, *sample = nullptr, *scores = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    const int saved = ctx->tc_fill_override.exchange(1);  // every block on the tensor cores while timing
+    auto cleanup = [&]() {
+        ctx->tc_fill_override.store(saved);
+        if (tp != pop) snaps_release(tp);
+        if (feat) cudaFree(feat);
+        if (sample) cudaFree(sample);
+        if (scores) cudaFree(scores);
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+    };
+    const int64_t m = std::min<int64_t>(n, SNAPS_TUNE_MAX_N);
+    if (m < n) {
+        const int64_t stride = n / m;
+        if (cudaMalloc(&feat, sizeof(float) * (size_t)n * f) != cudaSuccess ||
+            cudaMalloc(&sample, sizeof(float) * (size_t)m * f) != cudaSuccess) {
+            cleanup();
+            FAIL(SNAPS_ENOMEM, "no device memory for the tuning sample");
+        }
+        snaps_status r = snaps_pop_features(pop, feat, stream);
+        if (r == SNAPS_OK &&
+            cudaMemcpy2DAsync(sample, sizeof(float) * f, feat, sizeof(float) * f * stride, sizeof(float) * f,
+                              (size_t)m, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+            r = SNAPS_ECUDA;
+        if (r == SNAPS_OK) r = snaps_index(ctx, sample, m, f, 0u, stream, &tp);
+        if (r != SNAPS_OK) {
+            tp = pop;
+            cleanup();
+            FAIL(r == SNAPS_ECUDA ? SNAPS_ECUDA : r, "building the tuning sample failed");
+        }
+    }
+    const int kk = (int)std::min<int64_t>(k, m - 1);
+    if (cudaMalloc(&scores, sizeof(float) * (size_t)nb * 4 * (size_t)m) != cudaSuccess ||
+        cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        cleanup();
+        FAIL(SNAPS_ENOMEM, "no device memory for the tuning scores");
+    }
+    // ms of one call over the first `count` subspaces, after one untimed call
+    auto timed = [&](int count, uint32_t prec, double *ms) -> snaps_status {
+        for (int rep = 0; rep < 2; ++rep) {
+            if (rep == 1 && cudaEventRecord(e0, st) != cudaSuccess) return SNAPS_ECUDA;
+            const snaps_status q = snaps_scores(tp, all.data(), count, kk, nullptr, prec | SNAPS_INDEX_NONE, scores,
+                                                nullptr, nullptr, 0, stream);
+            if (q != SNAPS_OK) return q;
+        }
+        float t = 0.f;
+        if (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+            cudaEventElapsedTime(&t, e0, e1) != cudaSuccess)
+            return SNAPS_ECUDA;
+        *ms = t;
+        return SNAPS_OK;
+    };
+    snaps_tc_tune res{};
+    snaps_status r = timed(nb, precision, &res.ms_block);
+    double ms_group = 0.0;
+    if (r == SNAPS_OK) r = timed(nl, SNAPS_FP32, &ms_group);
+    cleanup();
+    if (r != SNAPS_OK) return r;
+    res.ms_lone = ms_group / nl;
+    // the block pays once it carries more subspaces than its time buys on their own
+    const double need = res.ms_lone > 0.0 ? std::ceil(res.ms_block / res.ms_lone) : (double)SNAPS_TC_NEVER;
+    res.min_fill = (int)std::min<double>(SNAPS_TC_NEVER, std::max(1.0, need));
+    {
+        std::lock_guard<std::mutex> g(ctx->tune_mu);
+        ctx->tc_fill[tune_key(n, 0, k)] = res.min_fill;
+    }
+    if (out) *out = res;
+    return SNAPS_OK;
+}
+
+snaps_status snaps_set_tc_min_fill(snaps_ctx *ctx, int fill)
+{
+    clear_error();
+    if (!ctx) FAIL(SNAPS_EINVAL, "ctx is NULL");
+    if (fill < 0 || fill > SNAPS_TC_NEVER) FAIL(SNAPS_EINVAL, "fill must be in 0..%d (got %d)", SNAPS_TC_NEVER, fill);
+    ctx->tc_fill_override.store(fill);
+    return SNAPS_OK;
+}
+
 snaps_status snaps_autotune_set(snaps_ctx *ctx, int64_t n, int k, const snaps_tune_entry *e)
 {
     clear_error();
@@ -1689,6 +1827,7 @@ snaps_status snaps_autotune_clear(snaps_ctx *ctx)
     if (!ctx) FAIL(SNAPS_EINVAL, "ctx is NULL");
     std::lock_guard<std::mutex> g(ctx->tune_mu);
     ctx->tune.clear();
+    ctx->tc_fill.clear();
     return SNAPS_OK;
 }
 

@@ -70,6 +70,16 @@ def mask_sample(count: int, seed: int, f: int = N_FEATURES) -> np.ndarray:
     return m[pick]
 
 
+def chunk_sample(count: int, seed: int, f: int = N_FEATURES) -> np.ndarray:
+    """``count`` whole blocks of 32 masks (h << 5) | l, l = 0..31, that share a
+    high part h over features 5.. of at least two features (so each block holds
+    all 32 of its masks), h drawn with ``seed``; ascending mask value."""
+    highs = np.array([h for h in range(1 << (f - 5)) if bin(h).count("1") >= 2])
+    rng = np.random.default_rng(seed)
+    pick = np.sort(rng.choice(highs, size=min(count, highs.size), replace=False))
+    return np.array([(int(h) << 5) | low for h in pick for low in range(32)], dtype=np.uint16)
+
+
 def pairs_and_full(f: int = N_FEATURES) -> np.ndarray:
     """The full f-feature mask plus every two-feature mask (106 for f = 15)."""
     two = [(1 << a) | (1 << b) for a in range(f) for b in range(a + 1, f)]

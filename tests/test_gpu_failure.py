@@ -18,6 +18,7 @@ pytestmark = pytest.mark.gpu
 def test_bounded_waits_give_up_and_the_context_recovers():
     ctx = snaps.snaps_create(0)
     try:
+        snaps.snaps_set_tc_min_fill(ctx, 1)  # the 40 subspaces form a tensor-core block
         x = snaps_inputs.population(3000, 5)
         masks = snaps_inputs.mask_sample(40, 5)
         pop = snaps.snaps_index(ctx, x)

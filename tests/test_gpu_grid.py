@@ -24,6 +24,7 @@ NONE = snaps.SNAPS_INDEX_NONE
 @pytest.fixture(scope="module")
 def ctx():
     c = snaps.snaps_create(0)
+    snaps.snaps_set_tc_min_fill(c, 1)  # the tensor-core form's subspaces on the tensor cores
     yield c
     snaps.snaps_destroy(c)
 

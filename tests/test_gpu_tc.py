@@ -21,6 +21,9 @@ pytestmark = pytest.mark.gpu
 @pytest.fixture(scope="module")
 def ctx():
     c = snaps.snaps_create(0)
+    # these tests exercise the tensor-core kernel itself: every block is formed
+    # however few subspaces it carries
+    snaps.snaps_set_tc_min_fill(c, 1)
     yield c
     snaps.snaps_destroy(c)
 
