@@ -68,8 +68,8 @@ constexpr int kW = kTreeWidth;     // 32 subspaces per chunk
 constexpr int kTile = 256;
 constexpr int kInit = 1024;        // candidates that bound the k-th distances in the set-up phase
 constexpr int kTBuf = 1024;        // event tuples buffered per warp
-constexpr int kTFlushAt = kTBuf - 64;  // a node appends at most 64 tuples
-constexpr int kFlushMin = 16;      // tuples that trigger an end-of-step flush
+constexpr int kTFlushAt = kTBuf - 128;  // a round of appends adds at most 128 tuples
+constexpr int kFlushMin = 64;      // tuples that trigger an end-of-step flush
 
 // Depth-first order of the subset tree over the low kLB bits: node L's parent
 // is L with its lowest set bit cleared, and its children add a bit below that.
@@ -143,6 +143,7 @@ struct WarpState {
     float tcmax;                    // the largest of them: a bound for the whole tree
     int cnt[kW];                    // eps-neighbour counts
     float eps2[kW];                 // radii of this chunk
+    int claim[kW];                  // flush: the lane that inserts into list L this round
     float escale[kW];               // 2^20 / eps
     float2 nxq[16];                 // the query's negated features, as (a, b) pairs
     unsigned long long stat_loaded; // steps loaded and steps in the streams of this warp's items
@@ -215,17 +216,17 @@ __device__ __forceinline__ void list_offer(float *ld, int *lj, int k, float d2, 
 // Process the buffered event tuples, 32 at a time with every lane busy: eps
 // counts and exact distance sums for the tuples within eps (shared-memory
 // atomics), then the tuples at or below their subspace's current k-th
-// distance enter its sorted list.  Lanes holding tuples of different
-// subspaces insert at the same time (each into its own list); lanes that share
-// a subspace take turns in lane order.  The k smallest (distance, original
-// index) pairs do not depend on the order of insertion.  Returns true when a
-// kNN list changed.
+// distance are offered to its list.  Lanes holding tuples of different
+// subspaces insert at the same time (each into its own list); of the lanes
+// that share a subspace, one per round claims the list (the last writer of a
+// shared slot), the others retry.  The k smallest (distance, original index)
+// pairs do not depend on the order of insertion.  Returns true when a kNN list
+// changed.
 template <int KMAX>
 __device__ __noinline__ bool flush_tuples(int ws_off, int count, int k)
 {
     WarpState<KMAX> &ws = *reinterpret_cast<WarpState<KMAX> *>(tree_smem + ws_off);
     const unsigned lane = dev::lane_id();
-    const unsigned lower = (1u << lane) - 1u;
     unsigned changed = 0;  // bit L: list L changed
     __syncwarp();
     for (int b = 0; b < count; b += 32) {
@@ -241,25 +242,26 @@ __device__ __noinline__ bool flush_tuples(int ws_off, int count, int k)
         }
         const bool want = ok && d2 <= ws.T[L];  // T is -inf for inactive subspaces and k = 0
         unsigned pend = __ballot_sync(dev::kFull, want);
-        if (!pend) continue;
-        // rank among the pending lanes of the same subspace
-        const unsigned same = __match_any_sync(dev::kFull, want ? L : 32 + (int)lane);
-        const int rank = __popc(same & pend & lower);
-        for (int r = 0; pend; ++r) {
-            if (want && rank == r) {
+        bool w = want;
+        while (pend) {
+            // one of the lanes that want list L inserts this round
+            if (w) ws.claim[L] = (int)lane;
+            __syncwarp();
+            const bool mine = w && ws.claim[L] == (int)lane;
+            if (mine) {
                 float T = ws.T[L];
                 int Tj = ws.Tj[L], Tp = ws.Tp[L];
                 list_offer(ws.ld[L], ws.lj[L], k, d2, j, T, Tj, Tp);
                 ws.T[L] = T;
                 ws.Tj[L] = Tj;
                 ws.Tp[L] = Tp;
+                changed |= 1u << L;
             }
-            const bool mine = want && rank == r;
-            pend &= ~__ballot_sync(dev::kFull, mine);
-            changed |= __reduce_or_sync(dev::kFull, mine ? (1u << L) : 0u);
-            __syncwarp();
+            w = w && !mine;
+            pend = __ballot_sync(dev::kFull, w);
         }
     }
+    changed = __reduce_or_sync(dev::kFull, changed);
     __syncwarp();
     ws.esum[lane] += ws.epart[lane];
     ws.epart[lane] = 0u;
@@ -296,13 +298,25 @@ __device__ __forceinline__ void walk(float2 (&v)[kW], const float2 (&d)[15], con
 
 // Append the kNN / eps tuples of this lane's triggered subspaces (bit L of
 // `bits`: either candidate fell below subspace L's pass threshold in the
-// walk).  Every round each lane takes its lowest remaining subspace, so the
-// rounds number the most subspaces any one lane triggered.  The node's
-// distances are recomputed from the root with the walk's own FFMA2 chain (the
-// low features of L folded from the highest down), so they are bit-identical
-// to the walk's; a round appends at most 64 tuples, and a nearly full buffer
-// is flushed.  Out of line: it runs on a minority of steps, and inlined its
-// registers would count against the walk's.  Returns the new tuple count.
+// walk).  Every round each lane takes its two lowest remaining subspaces, so
+// the rounds number half the most subspaces any one lane triggered, and the
+// two recomputations and threshold loads of a round are independent of each
+// other.  A node's distances are recomputed from the root with the walk's own
+// FFMA2 chain (the low features of L folded from the highest down), so they
+// are bit-identical to the walk's; a round appends at most 128 tuples, and a
+// nearly full buffer is flushed.  Out of line: it runs on a minority of
+// steps, and inlined its registers would count against the walk's.  Returns
+// the new tuple count.
+__device__ __forceinline__ float2 node_of(float2 v, int L, float2 d0, float2 d1, float2 d2, float2 d3, float2 d4)
+{
+    if (L & 16) v = __ffma2_rn(d4, d4, v);
+    if (L & 8) v = __ffma2_rn(d3, d3, v);
+    if (L & 4) v = __ffma2_rn(d2, d2, v);
+    if (L & 2) v = __ffma2_rn(d1, d1, v);
+    if (L & 1) v = __ffma2_rn(d0, d0, v);
+    return v;
+}
+
 template <int KMAX>
 __device__ __noinline__ int append_hits(int ws_off, unsigned bits, float2 root, float2 d0, float2 d1,
                                         float2 d2, float2 d3, float2 d4, int count, int ja, int jb, int k)
@@ -310,23 +324,29 @@ __device__ __noinline__ int append_hits(int ws_off, unsigned bits, float2 root, 
     WarpState<KMAX> &ws = *reinterpret_cast<WarpState<KMAX> *>(tree_smem + ws_off);
     const unsigned lower = (1u << dev::lane_id()) - 1u;
     while (__any_sync(dev::kFull, bits != 0u)) {
-        const bool has = bits != 0u;
-        const int L = has ? __ffs(bits) - 1 : 0;
+        const bool h1 = bits != 0u;
+        const int L1 = h1 ? __ffs(bits) - 1 : 0;
         bits &= bits - 1u;
-        float2 v = root;
-        if (L & 16) v = __ffma2_rn(d4, d4, v);
-        if (L & 8) v = __ffma2_rn(d3, d3, v);
-        if (L & 4) v = __ffma2_rn(d2, d2, v);
-        if (L & 2) v = __ffma2_rn(d1, d1, v);
-        if (L & 1) v = __ffma2_rn(d0, d0, v);
-        const float tc = ws.tc[L];
-        const bool pa = has && v.x < tc, pb = has && v.y < tc;
-        const unsigned ba = __ballot_sync(dev::kFull, pa);
-        const unsigned bb = __ballot_sync(dev::kFull, pb);
-        if (pa) ws.tbuf[count + __popc(ba & lower)] = make_uint2(__float_as_uint(v.x), (L << 24) | (ja & 0xffffff));
-        count += __popc(ba);
-        if (pb) ws.tbuf[count + __popc(bb & lower)] = make_uint2(__float_as_uint(v.y), (L << 24) | (jb & 0xffffff));
-        count += __popc(bb);
+        const bool h2 = bits != 0u;
+        const int L2 = h2 ? __ffs(bits) - 1 : 0;
+        bits &= bits - 1u;
+        const float2 v1 = node_of(root, L1, d0, d1, d2, d3, d4);
+        const float2 v2 = node_of(root, L2, d0, d1, d2, d3, d4);
+        const float t1 = ws.tc[L1], t2 = ws.tc[L2];
+        const bool p1a = h1 && v1.x < t1, p1b = h1 && v1.y < t1;
+        const bool p2a = h2 && v2.x < t2, p2b = h2 && v2.y < t2;
+        const unsigned b1a = __ballot_sync(dev::kFull, p1a);
+        const unsigned b1b = __ballot_sync(dev::kFull, p1b);
+        const unsigned b2a = __ballot_sync(dev::kFull, p2a);
+        const unsigned b2b = __ballot_sync(dev::kFull, p2b);
+        const int o1b = count + __popc(b1a);
+        const int o2a = o1b + __popc(b1b);
+        const int o2b = o2a + __popc(b2a);
+        if (p1a) ws.tbuf[count + __popc(b1a & lower)] = make_uint2(__float_as_uint(v1.x), (L1 << 24) | (ja & 0xffffff));
+        if (p1b) ws.tbuf[o1b + __popc(b1b & lower)] = make_uint2(__float_as_uint(v1.y), (L1 << 24) | (jb & 0xffffff));
+        if (p2a) ws.tbuf[o2a + __popc(b2a & lower)] = make_uint2(__float_as_uint(v2.x), (L2 << 24) | (ja & 0xffffff));
+        if (p2b) ws.tbuf[o2b + __popc(b2b & lower)] = make_uint2(__float_as_uint(v2.y), (L2 << 24) | (jb & 0xffffff));
+        count = o2b + __popc(b2b);
         if (count > kTFlushAt) {
             flush_tuples<KMAX>(ws_off, count, k);
             count = 0;
