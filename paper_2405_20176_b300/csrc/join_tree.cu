@@ -135,9 +135,8 @@ struct WarpState {
     int lj[kW][KMAX + 1];           // free of bank conflicts
     unsigned long long esum[kW];    // exact quantised eps distance sums
     unsigned epart[kW];             // this flush's partial sums (<= kTBuf terms of <= 2^20 + 1)
-    float T[kW];                    // current k-th squared distance: the list's largest entry
+    float T[kW];                    // current k-th squared distance: the heap's root
     int Tj[kW];                     // its original index
-    int Tp[kW];                     // its position in the (unsorted) list
     float tc[kW];                   // pass threshold max(T, eps) by L
     alignas(16) float tcd[kW];      // the same in DFS order, read four at a time by the walk
     float tcmax;                    // the largest of them: a bound for the whole tree
@@ -189,28 +188,39 @@ __device__ __forceinline__ void update_tcmax(WarpState<KMAX> &ws)
     __syncwarp();
 }
 
-// A kNN list is kept unsorted, with its largest entry by (distance, index)
-// tracked: a better candidate overwrites that entry, and a rescan of the k
-// entries (independent loads) finds the new largest.  Lists are sorted once,
-// when their query's results are written.
-__device__ __forceinline__ void list_offer(float *ld, int *lj, int k, float d2, int j, float &T, int &Tj, int &Tp)
+// A kNN list is a max-heap of k entries by (distance, index): entry 0 is the
+// largest, the current k-th nearest.  A better candidate replaces it and
+// sinks to its place, at most log2(k) levels.  Lists are sorted once, when
+// their query's results are written.
+__device__ __forceinline__ bool key_gt(float a, int ja, float b, int jb) { return a > b || (a == b && ja > jb); }
+
+__device__ __forceinline__ void list_offer(float *ld, int *lj, int k, float d2, int j, float &T, int &Tj)
 {
     if (!(d2 < T || (d2 == T && j < Tj))) return;
-    ld[Tp] = d2;
-    lj[Tp] = j;
-    float mx = ld[0];
-    int mj = lj[0], mp = 0;
-    for (int p = 1; p < k; ++p) {
-        const float v = ld[p];
-        const int q = lj[p];
-        const bool gt = v > mx || (v == mx && q > mj);
-        mx = gt ? v : mx;
-        mj = gt ? q : mj;
-        mp = gt ? p : mp;
+    int p = 0;
+    for (;;) {
+        int c = 2 * p + 1;
+        if (c >= k) break;
+        float cd = ld[c];
+        int cj = lj[c];
+        if (c + 1 < k) {
+            const float rd = ld[c + 1];
+            const int rj = lj[c + 1];
+            if (key_gt(rd, rj, cd, cj)) {
+                c = c + 1;
+                cd = rd;
+                cj = rj;
+            }
+        }
+        if (!key_gt(cd, cj, d2, j)) break;
+        ld[p] = cd;
+        lj[p] = cj;
+        p = c;
     }
-    T = mx;
-    Tj = mj;
-    Tp = mp;
+    ld[p] = d2;
+    lj[p] = j;
+    T = ld[0];
+    Tj = lj[0];
 }
 
 // Process the buffered event tuples, 32 at a time with every lane busy: eps
@@ -250,11 +260,10 @@ __device__ __noinline__ bool flush_tuples(int ws_off, int count, int k)
             const bool mine = w && ws.claim[L] == (int)lane;
             if (mine) {
                 float T = ws.T[L];
-                int Tj = ws.Tj[L], Tp = ws.Tp[L];
-                list_offer(ws.ld[L], ws.lj[L], k, d2, j, T, Tj, Tp);
+                int Tj = ws.Tj[L];
+                list_offer(ws.ld[L], ws.lj[L], k, d2, j, T, Tj);
                 ws.T[L] = T;
                 ws.Tj[L] = Tj;
-                ws.Tp[L] = Tp;
                 changed |= 1u << L;
             }
             w = w && !mine;
@@ -496,7 +505,6 @@ __device__ __noinline__ void setup_phase(int ws_off, const float4 *__restrict__ 
         }
         ws.T[L] = bound;
         ws.Tj[L] = 0x7fffffff;
-        ws.Tp[L] = 0;
     }
     ws.tc[L] = mine ? fmaxf(next_up(ws.T[L]), eps_up(e2)) : -CUDART_INF_F;
     ws.tcd[kDfsPos.pos[L]] = ws.tc[L];
@@ -570,7 +578,6 @@ __global__ void __launch_bounds__(CW * 32, kCtasPerSm<CW>)
             ws.cnt[L] = 0;
             ws.T[L] = (((active >> L) & 1u) && k > 0) ? CUDART_INF_F : -CUDART_INF_F;
             ws.Tj[L] = 0x7fffffff;
-            ws.Tp[L] = 0;
         }
         __syncwarp();
         // The candidate stream: all steps of 64 rows, starting at the query's own
