@@ -47,12 +47,12 @@ MUFU_PER_SM_CLK = 16         # special-function (square root) throughput per SM 
 FMA_LANES_PER_SM_CLK = 128   # FP32 add / FMA lane-operations per SM per clock
 # DRAM bytes (read + write) per pair-subspace evaluation, from one ncu capture
 # of each kernel as it stands (dram__bytes_read.sum + dram__bytes_write.sum):
-# the tree join on one 32-subspace chunk at N = 31,693 (7.83 MB + 5.01 MB),
+# the tree join on one 32-subspace chunk at N = 31,693 (7.82 MB + 3.25 MB),
 # the tensor-core join on one block of 256 subspaces at N = 31,693 (354 MB +
 # 982 MB: its per-query writes scatter over 256 output rows, which the L2
 # cannot hold).  Both kernels read their candidates from L2, so DRAM traffic
 # grows with the evaluations only through the outputs and the row copies.
-TREE_DRAM_BYTES_PER_EVAL = (7.82208e6 + 3.229696e6) / (31693 * 31692 * 32)
+TREE_DRAM_BYTES_PER_EVAL = (7.82336e6 + 3.246336e6) / (31693 * 31692 * 32)
 TC_DRAM_BYTES_PER_EVAL = (354.470144e6 + 981.903872e6) / (31693 * 31692 * 256)
 
 

@@ -114,6 +114,25 @@ __device__ __forceinline__ unsigned eps_quant_fma_pipe(float d2, float scale) {
     return __float_as_uint(__fadd_rn(p, 12582912.f)) - 0x4B400000u;
 }
 
+// eps_quant_fma_pipe's value plus 0x4B400000 (the bits of the rounded float).
+// A branch-free kernel adds this for every candidate, with d2 capped at eps^2:
+// a candidate beyond eps then adds eps_quant_fma_pipe(eps^2) + 0x4B400000, a
+// known constant, and one correction per round of candidates
+// (eps_round_sum) leaves the exact sum of the neighbours' quantised
+// distances, with no per-candidate select.  The 32-bit sum wraps; the result
+// is exact while the neighbours' true sum fits 32 bits.
+__device__ __forceinline__ unsigned eps_quant_biased(float d2, float scale) {
+    const float p = __fmul_rn(eps_sqrt(d2), scale);
+    return __float_as_uint(__fadd_rn(p, 12582912.f));
+}
+
+// The exact quantised sum of a round's eps-neighbours from the biased sum of
+// all `slots` candidates of the round (`hits` of them within eps) and the
+// quantised value of eps^2 itself.
+__device__ __forceinline__ unsigned eps_round_sum(unsigned biased, unsigned slots, unsigned hits, unsigned q_eps) {
+    return biased - slots * 0x4B400000u - (slots - hits) * q_eps;
+}
+
 // Mean distance from the exact quantised sum.
 __device__ __forceinline__ float eps_mean(unsigned long long qsum, int cnt, float scale) {
     if (cnt <= 0 || scale == 0.f) return 0.f;
@@ -151,6 +170,43 @@ __device__ __forceinline__ void list_insert(unsigned ballot, float d2, int j, fl
         }
         T = __shfl_sync(kFull, my_d, k - 1);
     }
+}
+
+// A kNN list as a max-heap of k (squared distance, original index) entries,
+// entry p at ld[p * stride], lj[p * stride]; entry 0 is the largest by
+// (distance, index), the current k-th nearest.  Replace it with (d2, j),
+// which must be smaller, and sink the new entry to its place: at most
+// log2(k) levels, where an unsorted list needs a rescan of all k entries.
+// The list is sorted once, when its query's results are written.
+__device__ __forceinline__ bool knn_key_gt(float a, int ja, float b, int jb)
+{
+    return a > b || (a == b && ja > jb);
+}
+
+__device__ __forceinline__ void heap_sink_root(float *ld, int *lj, int stride, int k, float d2, int j)
+{
+    int p = 0;
+    for (;;) {
+        int c = 2 * p + 1;
+        if (c >= k) break;
+        float cd = ld[c * stride];
+        int cj = lj[c * stride];
+        if (c + 1 < k) {
+            const float rd = ld[(c + 1) * stride];
+            const int rj = lj[(c + 1) * stride];
+            if (knn_key_gt(rd, rj, cd, cj)) {
+                c = c + 1;
+                cd = rd;
+                cj = rj;
+            }
+        }
+        if (!knn_key_gt(cd, cj, d2, j)) break;
+        ld[p * stride] = cd;
+        lj[p * stride] = cj;
+        p = c;
+    }
+    ld[p * stride] = d2;
+    lj[p * stride] = j;
 }
 
 }  // namespace dev

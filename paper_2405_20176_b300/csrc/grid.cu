@@ -368,8 +368,8 @@ __global__ void __launch_bounds__(kGridWarps * 32, 2)
 // outside a query's own block are tested too; they only make its kNN list
 // tighter sooner, and every decision is the exact canonical distance.
 //
-// Each thread keeps its eps count, exact quantised sum and an unsorted kNN
-// list (largest entry tracked) privately.  A query whose k-th distance is not
+// Each thread keeps its eps count, exact quantised sum and a kNN list kept as
+// a max-heap (dev::heap_sink_root) privately.  A query whose k-th distance is not
 // below R w afterwards (the reach beyond which the rings begin) may have
 // nearer objects outside the scanned block; it is appended to the ring list
 // and joined afresh by grid_ring_kernel, and this kernel writes nothing for it.
@@ -391,17 +391,6 @@ __device__ __forceinline__ float comp(const float4 &v, int f)
     return f == 0 ? v.x : (f == 1 ? v.y : (f == 2 ? v.z : v.w));
 }
 
-// dev::eps_quant's value, for the eps-neighbours of a subspace whose scale
-// maps eps to 2^20, without the conversion unit: the product p < 2^22 is
-// rounded as dev::eps_quant rounds it, and adding 1.5 * 2^23 (an even
-// integer, in a binade where floats are the integers) rounds p to the
-// nearest integer, ties to even, exactly as __float2uint_rn does.
-__device__ __forceinline__ unsigned quant_rn(float d2, float scale)
-{
-    const float p = __fmul_rn(dev::eps_sqrt(d2), scale);
-    return __float_as_uint(__fadd_rn(p, 12582912.f)) - 0x4B400000u;
-}
-
 __device__ __forceinline__ int fastest_cell(const GridSpec &g, const int (&c)[3]) { return g.D == 2 ? c[1] : c[2]; }
 
 template <typename V, int KMAX>
@@ -421,6 +410,7 @@ __global__ void __launch_bounds__(kTileQ, 4)
     const bool do_eps = g.eps2 >= 0.f;
     const float e2 = g.eps2;
     const float esc = dev::eps_scale(g.eps2).scale;
+    const unsigned q_eps = dev::eps_quant_fma_pipe(e2, esc);  // a candidate beyond eps adds this
     // objects outside a query's (2R + 1)^D block are at least this far away
     const float reach = (float)R * g.w * (1.f - 1.f / 1024.f);
     const float reach2 = reach * reach;
@@ -449,7 +439,7 @@ __global__ void __launch_bounds__(kTileQ, 4)
             sm.lj[e][t] = 0x7fffffff;
         }
         float T = (act && k > 0) ? CUDART_INF_F : -CUDART_INF_F;  // largest list entry
-        int Tj = 0x7fffffff, Tp = 0;
+        int Tj = 0x7fffffff;
         unsigned cnt = 0;
         unsigned long long qs = 0ull;
 
@@ -471,7 +461,8 @@ __global__ void __launch_bounds__(kTileQ, 4)
                     __syncthreads();
                     if (!act) continue;
                     const int cend = c0 + cn;
-                    unsigned qr = 0u;  // this round's quantised sum: <= kTileC terms of <= 2^20 + 1
+                    unsigned qb = 0u;  // this round's biased sum over all its candidates (wraps)
+                    const unsigned cnt0 = cnt;
 #pragma unroll 2
                     for (int u = 0; u < cn; u += 4) {
                         // the canonical fold of four candidates, two per f32x2 instruction,
@@ -490,10 +481,8 @@ __global__ void __launch_bounds__(kTileQ, 4)
 #pragma unroll
                         for (int h = 0; h < 4; ++h) {
                             const float d2 = (h & 1) ? acc[h >> 1].y : acc[h >> 1].x;
-                            const bool in = d2 <= e2;
-                            const unsigned qv = quant_rn(fminf(d2, e2), esc);
-                            cnt += in ? 1u : 0u;
-                            qr += in ? qv : 0u;
+                            cnt += d2 <= e2 ? 1u : 0u;
+                            qb += dev::eps_quant_biased(fminf(d2, e2), esc);
                         }
                         // kNN: one test for the four, then each
                         if (fminf(fminf(acc[0].x, acc[0].y), fminf(acc[1].x, acc[1].y)) <= T) {
@@ -505,28 +494,17 @@ __global__ void __launch_bounds__(kTileQ, 4)
                                 if (cp != q && cp < cend) {
                                     const int oj = sm.corig[u + h];
                                     if (d2 < T || oj < Tj) {
-                                        sm.ld[Tp][t] = d2;
-                                        sm.lj[Tp][t] = oj;
-                                        float mx = sm.ld[0][t];
-                                        int mj = sm.lj[0][t], mp = 0;
-                                        for (int e = 1; e < k; ++e) {
-                                            const float v = sm.ld[e][t];
-                                            const int j = sm.lj[e][t];
-                                            const bool gt = v > mx || (v == mx && j > mj);
-                                            mx = gt ? v : mx;
-                                            mj = gt ? j : mj;
-                                            mp = gt ? e : mp;
-                                        }
-                                        T = mx;
-                                        Tj = mj;
-                                        Tp = mp;
+                                        dev::heap_sink_root(&sm.ld[0][t], &sm.lj[0][t], kTileQ, k, d2, oj);
+                                        T = sm.ld[0][t];
+                                        Tj = sm.lj[0][t];
                                     }
                                 }
                             }
                         }
                         }
                     }
-                    qs += qr;
+                    // the neighbours' exact sum: <= kTileC terms of <= 2^20 + 1
+                    qs += dev::eps_round_sum(qb, (unsigned)((cn + 3) & ~3), cnt - cnt0, q_eps);
                 }
         };
         // the segment's own cells first and then the rows outwards, so that the

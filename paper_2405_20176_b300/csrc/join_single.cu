@@ -13,8 +13,8 @@
 // starts at the CTA's own rows, which are neighbours in the stored cell
 // order, so the kNN thresholds are tight early; it then wraps around.
 //
-// Each thread keeps its eps count, the exact quantised distance sum and an
-// unsorted kNN list with its largest entry tracked.  The query meets itself
+// Each thread keeps its eps count, the exact quantised distance sum and a
+// kNN list kept as a max-heap (dev::heap_sink_root).  The query meets itself
 // once in the stream (distance 0); that eps hit is taken off at the end and
 // the kNN test skips it by position.  Results equal every other path's bit
 // for bit.
@@ -64,6 +64,7 @@ __device__ __forceinline__ void join_one(SingleSmem<KMAX> &sm, const float4 *__r
     const bool act = q < n;
     const bool do_eps = e2 >= 0.f;
     const float esc = dev::eps_scale(e2).scale;
+    const unsigned q_eps = dev::eps_quant_fma_pipe(e2, esc);  // a candidate beyond eps adds this
 
     // this thread's query, compact
     int qorig = 0;
@@ -87,7 +88,7 @@ __device__ __forceinline__ void join_one(SingleSmem<KMAX> &sm, const float4 *__r
         sm.lj[e][t] = 0x7fffffff;
     }
     float T = (act && k > 0) ? CUDART_INF_F : -CUDART_INF_F;  // largest list entry
-    int Tj = 0x7fffffff, Tp = 0;
+    int Tj = 0x7fffffff;
     unsigned cnt = 0;
     unsigned long long qs = 0ull;
 
@@ -110,7 +111,8 @@ __device__ __forceinline__ void join_one(SingleSmem<KMAX> &sm, const float4 *__r
             __syncthreads();
             if (!act) continue;
             const int cend = c0 + cn;
-            unsigned qr = 0u;  // this round's quantised sum: <= kSC terms of <= 2^20 + 1
+            unsigned qb = 0u;  // this round's biased sum over all its candidates (wraps)
+            const unsigned cnt0 = cnt;
 #pragma unroll 2
             for (int u = 0; u < cn; u += 4) {
                 float2 acc[2];
@@ -126,10 +128,8 @@ __device__ __forceinline__ void join_one(SingleSmem<KMAX> &sm, const float4 *__r
 #pragma unroll
                 for (int h = 0; h < 4; ++h) {
                     const float d2 = (h & 1) ? acc[h >> 1].y : acc[h >> 1].x;
-                    const bool in = d2 <= e2;
-                    const unsigned qv = dev::eps_quant_fma_pipe(fminf(d2, e2), esc);
-                    cnt += in ? 1u : 0u;
-                    qr += in ? qv : 0u;
+                    cnt += d2 <= e2 ? 1u : 0u;
+                    qb += dev::eps_quant_biased(fminf(d2, e2), esc);
                 }
                 // kNN: one test for the four, then each
                 if (fminf(fminf(acc[0].x, acc[0].y), fminf(acc[1].x, acc[1].y)) <= T) {
@@ -141,28 +141,17 @@ __device__ __forceinline__ void join_one(SingleSmem<KMAX> &sm, const float4 *__r
                             if (cp != q && cp < cend) {
                                 const int oj = sm.corig[u + h];
                                 if (d2 < T || oj < Tj) {
-                                    sm.ld[Tp][t] = d2;
-                                    sm.lj[Tp][t] = oj;
-                                    float mx = sm.ld[0][t];
-                                    int mj = sm.lj[0][t], mp = 0;
-                                    for (int e = 1; e < k; ++e) {
-                                        const float lv = sm.ld[e][t];
-                                        const int lj = sm.lj[e][t];
-                                        const bool gt = lv > mx || (lv == mx && lj > mj);
-                                        mx = gt ? lv : mx;
-                                        mj = gt ? lj : mj;
-                                        mp = gt ? e : mp;
-                                    }
-                                    T = mx;
-                                    Tj = mj;
-                                    Tp = mp;
+                                    dev::heap_sink_root(&sm.ld[0][t], &sm.lj[0][t], kSQ, k, d2, oj);
+                                    T = sm.ld[0][t];
+                                    Tj = sm.lj[0][t];
                                 }
                             }
                         }
                     }
                 }
             }
-            qs += qr;
+            // the neighbours' exact sum: <= kSC terms of <= 2^20 + 1
+            qs += dev::eps_round_sum(qb, (unsigned)((cn + 3) & ~3), cnt - cnt0, q_eps);
         }
     };
     scan(p0, n);  // the CTA's own rows first, then the rest

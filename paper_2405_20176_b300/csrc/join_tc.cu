@@ -53,9 +53,9 @@
 // has been read), issues the MMAs and commits them to `mma_done`; consumers
 // wait for `mma_done`, filter and decide, and arrive on `t_empty`.
 //
-// kNN lists are kept unsorted with their largest entry tracked: a better
-// candidate overwrites that entry and the k entries are rescanned; each list
-// is sorted once, when its query's results are written.
+// kNN lists are max-heaps: a better candidate replaces the largest entry and
+// sinks to its place; each list is sorted once, when its query's results are
+// written.
 //
 // Start-up: the 32 rows around the query (in the stored cell order) are
 // staged in shared memory and folded exactly first (by the first thread of
@@ -239,35 +239,23 @@ __device__ __forceinline__ float fold_exact(const float4 *xq, const float4 *base
 }
 
 // A thread's kNN list: k entries (squared distance, original index) in shared
-// memory, unsorted, with its largest entry by (distance, index) tracked in
-// registers.  Unused entries are (+inf, INT_MAX).
+// memory, entry-major, kept as a max-heap (dev::heap_sink_root); its largest
+// entry by (distance, index) is mirrored in registers.  Unused entries are
+// (+inf, INT_MAX).
 struct KnnMax {
     float T;   // largest distance: the k-th nearest so far (+inf until k entries)
     int Tj;    // its index
-    int Tp;    // its position
 };
 
 // Insert (d2, oj) into thread `tid`'s list when it beats the largest entry by
-// (distance, index); the new largest entry is found by a rescan.
+// (distance, index).
 template <int KMAX>
 __device__ __forceinline__ void knn_offer(TcSmem<KMAX> &sm, int tid, int k, float d2, int oj, KnnMax &m)
 {
     if (d2 < m.T || (d2 == m.T && oj < m.Tj)) {
-        sm.ld[m.Tp][tid] = d2;
-        sm.lj[m.Tp][tid] = oj;
-        float mx = sm.ld[0][tid];
-        int mj = sm.lj[0][tid], mp = 0;
-        for (int p = 1; p < k; ++p) {
-            const float v = sm.ld[p][tid];
-            const int j = sm.lj[p][tid];
-            const bool gt = v > mx || (v == mx && j > mj);
-            mx = gt ? v : mx;
-            mj = gt ? j : mj;
-            mp = gt ? p : mp;
-        }
-        m.T = mx;
-        m.Tj = mj;
-        m.Tp = mp;
+        dev::heap_sink_root(&sm.ld[0][tid], &sm.lj[0][tid], kConsumers, k, d2, oj);
+        m.T = sm.ld[0][tid];
+        m.Tj = sm.lj[0][tid];
     }
 }
 
@@ -515,7 +503,6 @@ __global__ void __launch_bounds__(kCtaThreads, 1)
             KnnMax km;
             km.T = (act && k > 0) ? CUDART_INF_F : -CUDART_INF_F;
             km.Tj = 0x7fffffff;
-            km.Tp = 0;
             int cnt = 0;
             unsigned long long qs = 0ull;
             if (act && cpart == 0) {

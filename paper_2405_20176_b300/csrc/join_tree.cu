@@ -188,37 +188,12 @@ __device__ __forceinline__ void update_tcmax(WarpState<KMAX> &ws)
     __syncwarp();
 }
 
-// A kNN list is a max-heap of k entries by (distance, index): entry 0 is the
-// largest, the current k-th nearest.  A better candidate replaces it and
-// sinks to its place, at most log2(k) levels.  Lists are sorted once, when
-// their query's results are written.
-__device__ __forceinline__ bool key_gt(float a, int ja, float b, int jb) { return a > b || (a == b && ja > jb); }
-
+// A kNN list is a max-heap of k entries by (distance, index) (dev::heap_sink_root):
+// entry 0 is the largest, the current k-th nearest, and T / Tj mirror it.
 __device__ __forceinline__ void list_offer(float *ld, int *lj, int k, float d2, int j, float &T, int &Tj)
 {
     if (!(d2 < T || (d2 == T && j < Tj))) return;
-    int p = 0;
-    for (;;) {
-        int c = 2 * p + 1;
-        if (c >= k) break;
-        float cd = ld[c];
-        int cj = lj[c];
-        if (c + 1 < k) {
-            const float rd = ld[c + 1];
-            const int rj = lj[c + 1];
-            if (key_gt(rd, rj, cd, cj)) {
-                c = c + 1;
-                cd = rd;
-                cj = rj;
-            }
-        }
-        if (!key_gt(cd, cj, d2, j)) break;
-        ld[p] = cd;
-        lj[p] = cj;
-        p = c;
-    }
-    ld[p] = d2;
-    lj[p] = j;
+    dev::heap_sink_root(ld, lj, 1, k, d2, j);
     T = ld[0];
     Tj = lj[0];
 }
