@@ -48,12 +48,12 @@ FMA_LANES_PER_SM_CLK = 128   # FP32 add / FMA lane-operations per SM per clock
 # DRAM bytes (read + write) per pair-subspace evaluation, from one ncu capture
 # of each kernel as it stands (dram__bytes_read.sum + dram__bytes_write.sum):
 # the tree join on one 32-subspace chunk at N = 31,693 (7.82 MB + 3.25 MB),
-# the tensor-core join on one block of 256 subspaces at N = 31,693 (354 MB +
-# 982 MB: its per-query writes scatter over 256 output rows, which the L2
+# the tensor-core join on one block of 256 subspaces at N = 31,693 (351 MB +
+# 980 MB: its per-query writes scatter over 256 output rows, which the L2
 # cannot hold).  Both kernels read their candidates from L2, so DRAM traffic
 # grows with the evaluations only through the outputs and the row copies.
 TREE_DRAM_BYTES_PER_EVAL = (7.82336e6 + 3.246336e6) / (31693 * 31692 * 32)
-TC_DRAM_BYTES_PER_EVAL = (354.470144e6 + 981.903872e6) / (31693 * 31692 * 256)
+TC_DRAM_BYTES_PER_EVAL = (350.9632e6 + 980.276224e6) / (31693 * 31692 * 256)
 
 
 def _load_peaks():
@@ -332,7 +332,7 @@ def run_ours(args, rank, world, dist):
         return {"bound": "tensor", "kernel": "join_tc", "achieved": achieved, "peak": peak,
                 "unit": "TFLOP/s", "frac": (achieved / peak) if achieved else None,
                 "traffic": TC_DRAM_BYTES_PER_EVAL * evals_per_step,
-                "traffic_basis": "DRAM bytes per launch: an ncu capture of one 256-subspace block (1.34 GB "
+                "traffic_basis": "DRAM bytes per launch: an ncu capture of one 256-subspace block (1.33 GB "
                                  "for 2.6e11 evaluations) scaled by the launch's evaluations",
                 "peak_basis": "measured dense BF16 GEMM, sustained (MEASURED_PEAKS.json); FP16 "
                               "has the same dense rate; 64 FLOPs per evaluation (two K = 16 MMAs)",
