@@ -214,22 +214,37 @@ __device__ __noinline__ bool flush_tuples(int ws_off, int count, int k)
     const unsigned lane = dev::lane_id();
     unsigned changed = 0;  // bit L: list L changed
     __syncwarp();
+    // eps counts and exact distance sums; the kNN candidates are compacted to
+    // the front of the buffer (in place: a batch writes at most as many as it read)
+    int nw = 0;
     for (int b = 0; b < count; b += 32) {
         const int idx = b + (int)lane;
         const bool ok = idx < count;
         const uint2 t = ok ? ws.tbuf[idx] : make_uint2(0x7f800000u, 0u);
         const int L = (int)(t.y >> 24);
-        const int j = (int)(t.y & 0xffffffu);
         const float d2 = __uint_as_float(t.x);
         if (ok && d2 <= ws.eps2[L]) {
             atomicAdd(&ws.cnt[L], 1);
             atomicAdd(&ws.epart[L], dev::eps_quant(d2, ws.escale[L]));
         }
         const bool want = ok && d2 <= ws.T[L];  // T is -inf for inactive subspaces and k = 0
-        unsigned pend = __ballot_sync(dev::kFull, want);
-        bool w = want;
+        const unsigned wb = __ballot_sync(dev::kFull, want);
+        if (want) ws.tbuf[nw + __popc(wb & ((1u << lane) - 1u))] = t;
+        nw += __popc(wb);
+        __syncwarp();
+    }
+    // then the kNN offers, 32 candidates at a time
+    for (int b = 0; b < nw; b += 32) {
+        const int idx = b + (int)lane;
+        const bool ok = idx < nw;
+        const uint2 t = ok ? ws.tbuf[idx] : make_uint2(0x7f800000u, 0u);
+        const int L = (int)(t.y >> 24);
+        const int j = (int)(t.y & 0xffffffu);
+        const float d2 = __uint_as_float(t.x);
+        bool w = ok;
+        unsigned pend = __ballot_sync(dev::kFull, w);
         while (pend) {
-            // one of the lanes that want list L inserts this round
+            // one of the lanes that hold list L inserts this round
             if (w) ws.claim[L] = (int)lane;
             __syncwarp();
             const bool mine = w && ws.claim[L] == (int)lane;
