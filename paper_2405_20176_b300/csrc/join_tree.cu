@@ -14,16 +14,17 @@
 // 64 rows, packed so that the f32x2 instructions (FADD2/FFMA2) process both;
 // the rows are read straight from global memory (the population stays in L2),
 // the next live step's while the current one is walked.  The walk spends, per
-// subspace, one FFMA2 and two compares against the subspace's pass threshold,
-// max(current k-th distance, eps), which sits in shared memory (warp-uniform,
-// broadcast).  On steps where some lane's candidates pass somewhere, an
-// out-of-line handler recomputes the triggered subspaces' distances, each lane
-// its own subspaces, and appends (squared distance, subspace, candidate)
-// tuples to the warp's buffer.  Once enough tuples wait (or the buffer fills),
-// a flush processes 32 tuples at a time with every lane busy: eps counts and
-// exact fixed-point distance sums by shared-memory atomics, then kNN
-// insertions, lanes holding different subspaces inserting into their lists at
-// the same time.
+// subspace, one FFMA2, one FADD2 against the negated pass threshold,
+// max(current k-th distance, eps), read from shared memory (warp-uniform,
+// broadcast), and a sign-bit OR and shift.  On steps where some lane's
+// candidates pass somewhere, an out-of-line handler lists the warp's
+// triggered (lane, subspace) pairs and processes them 32 at a time with every
+// lane busy: it recomputes each pair's distances, counts the eps-neighbours
+// and sums their exact fixed-point distances by shared-memory atomics, and
+// appends the kNN candidates as (squared distance, subspace, candidate)
+// tuples to the warp's buffer.  Once enough tuples wait, a flush offers them
+// to the kNN lists (max-heaps), lanes holding different subspaces inserting
+// into their lists at the same time.
 //
 // Skipping: every node of a chunk's tree is at least its root, the fold over
 // the high features, so a step none of whose roots is below the chunk's
@@ -68,7 +69,10 @@ constexpr int kW = kTreeWidth;     // 32 subspaces per chunk
 constexpr int kTile = 256;
 constexpr int kInit = 1024;        // candidates that bound the k-th distances in the set-up phase
 constexpr int kTBuf = 1024;        // event tuples buffered per warp
-constexpr int kTFlushAt = kTBuf - 128;  // a round of appends adds at most 128 tuples
+// The buffer's tail stages an append's candidates (7 x 32 float2) and its
+// list of (lane, subspace) pairs (at most 32 x 32 halfwords): 480 tuples' room.
+constexpr int kTStage = kTBuf - 480;
+constexpr int kTFlushAt = kTStage - 64;  // a round of appends adds at most 64 tuples
 constexpr int kFlushMin = 64;      // tuples that trigger an end-of-step flush
 
 // Depth-first order of the subset tree over the low kLB bits: node L's parent
@@ -112,19 +116,15 @@ constexpr DfsTable make_dfs() {
 }
 constexpr DfsTable kDfs = make_dfs();
 
-// DFS position of every node L (the inverse of kDfs.node).
-struct DfsPos {
-    int pos[kW];
-};
-constexpr DfsPos make_dfs_pos() {
-    DfsPos t{};
-    for (int p = 0; p < kW; ++p) t.pos[kDfs.node[p]] = p;
-    return t;
-}
-__constant__ DfsPos kDfsPos = make_dfs_pos();
 static_assert(kTBuf * 2 >= kW * (kW + 1), "the set-up transpose fits the tuple buffer");
-static_assert(kTBuf * ((1u << 20) + 1u) < (1ull << 32), "a flush's eps partial sums fit 32 bits");
+static_assert((kTBuf - kTStage) * 8 >= 7 * 32 * 8 + 32 * 32 * 2, "an append's staging fits the buffer's tail");
+static_assert(64ull * ((1u << 20) + 1u) < (1ull << 32), "an append's eps partial sums fit 32 bits");
 static_assert(kDfs.node[1] == 16 && kDfs.parent[kW / 2] > 0, "DFS order as expected");
+
+// The walk visits node L = 8 j + m at position P = j + 4 m (j = 0..3, m =
+// 0..7): a parent (L with its lowest set bit cleared) always comes first.
+__host__ __device__ constexpr int walk_pos(int L) { return (L >> 3) + 4 * (L & 7); }
+__host__ __device__ constexpr int low_bit(int L) { return (L & 1) ? 0 : (L & 2) ? 1 : (L & 4) ? 2 : (L & 8) ? 3 : 4; }
 
 // Per consumer warp: the state of its query across the chunk's 32 subspaces.
 template <int KMAX>
@@ -134,11 +134,11 @@ struct WarpState {
     float ld[kW][KMAX + 1];         // kNN lists by L; +1 keeps both access patterns
     int lj[kW][KMAX + 1];           // free of bank conflicts
     unsigned long long esum[kW];    // exact quantised eps distance sums
-    unsigned epart[kW];             // this flush's partial sums (<= kTBuf terms of <= 2^20 + 1)
+    unsigned epart[kW];             // an append's partial sums (<= 64 terms of <= 2^20 + 1)
     float T[kW];                    // current k-th squared distance: the heap's root
     int Tj[kW];                     // its original index
     float tc[kW];                   // pass threshold max(T, eps) by L
-    alignas(16) float tcd[kW];      // the same in DFS order, read four at a time by the walk
+    alignas(16) float tcw[kW];      // the same negated, in the walk's order, read four at a time
     float tcmax;                    // the largest of them: a bound for the whole tree
     int cnt[kW];                    // eps-neighbour counts
     float eps2[kW];                 // radii of this chunk
@@ -198,15 +198,16 @@ __device__ __forceinline__ void list_offer(float *ld, int *lj, int k, float d2, 
     Tj = lj[0];
 }
 
-// Process the buffered event tuples, 32 at a time with every lane busy: eps
-// counts and exact distance sums for the tuples within eps (shared-memory
-// atomics), then the tuples at or below their subspace's current k-th
-// distance are offered to its list.  Lanes holding tuples of different
-// subspaces insert at the same time (each into its own list); of the lanes
-// that share a subspace, one per round claims the list (the last writer of a
-// shared slot), the others retry.  The k smallest (distance, original index)
-// pairs do not depend on the order of insertion.  Returns true when a kNN list
-// changed.
+// Process the buffered event tuples.  First, 32 at a time with every lane
+// busy: eps counts and exact distance sums for the tuples within eps
+// (shared-memory atomics), while the tuples at or below their subspace's
+// current k-th distance are compacted to the front of the buffer.  Then those
+// kNN candidates are offered to their lists, 32 at a time: lanes holding
+// candidates of different subspaces insert at the same time (each into its
+// own list); of the lanes that share a subspace, one per round claims the list
+// (the last writer of a shared slot), the others retry.  The k smallest
+// (distance, original index) pairs do not depend on the order of insertion.
+// Returns true when a kNN list changed.
 template <int KMAX>
 __device__ __noinline__ bool flush_tuples(int ws_off, int count, int k)
 {
@@ -223,10 +224,6 @@ __device__ __noinline__ bool flush_tuples(int ws_off, int count, int k)
         const uint2 t = ok ? ws.tbuf[idx] : make_uint2(0x7f800000u, 0u);
         const int L = (int)(t.y >> 24);
         const float d2 = __uint_as_float(t.x);
-        if (ok && d2 <= ws.eps2[L]) {
-            atomicAdd(&ws.cnt[L], 1);
-            atomicAdd(&ws.epart[L], dev::eps_quant(d2, ws.escale[L]));
-        }
         const bool want = ok && d2 <= ws.T[L];  // T is -inf for inactive subspaces and k = 0
         const unsigned wb = __ballot_sync(dev::kFull, want);
         if (want) ws.tbuf[nw + __popc(wb & ((1u << lane) - 1u))] = t;
@@ -267,45 +264,56 @@ __device__ __noinline__ bool flush_tuples(int ws_off, int count, int k)
     if ((changed >> lane) & 1u) {
         const float t = fmaxf(next_up(ws.T[lane]), eps_up(ws.eps2[lane]));
         ws.tc[lane] = t;
-        ws.tcd[kDfsPos.pos[lane]] = t;
+        ws.tcw[walk_pos(lane)] = -t;
     }
     update_tcmax(ws);
     return changed != 0u;
 }
 
-// The walk: the 32 subspace distances of this lane's two candidates in DFS
-// order (one FFMA2 per node), and the set of subspaces L in which either
-// candidate fell below its pass threshold (bit L of the OR of `bits`).  No
-// branches; four partial masks keep the ORs from forming one serial chain.
+// The walk: the 32 subspace distances of this lane's two candidates (one
+// FFMA2 per node) and the set of subspaces L in which either candidate fell
+// below its pass threshold.  The test is the sign of d2 - threshold (an FADD2
+// with the negated thresholds, exact in sign: the difference of two floats is
+// 0 only when they are equal), shifted into one of four partial masks, node
+// m of partial j at bit 7 - m; walk_bits turns them into bit L.  No branches.
 template <int P>
-__device__ __forceinline__ void walk(float2 (&v)[kW], const float2 (&d)[15], const float4 *tcd, float4 tq,
-                                     unsigned (&bits)[4])
+__device__ __forceinline__ void walk(float2 (&v)[kW], const float2 (&d)[15], const float4 *tcw, float4 tq,
+                                     unsigned (&part)[4])
 {
     if constexpr (P < kW) {
+        constexpr int j = P & 3, m = P >> 2;
+        constexpr int L = 8 * j + m;
         if constexpr (P > 0) {
-            constexpr int b = kDfs.bit[P];
-            constexpr int par = kDfs.parent[P];
-            v[P] = __ffma2_rn(d[b], d[b], v[par]);
+            constexpr int par = L & (L - 1);           // parent: the lowest set bit cleared
+            constexpr int b = low_bit(L);              // the low feature it adds
+            v[P] = __ffma2_rn(d[b], d[b], v[walk_pos(par)]);
         }
-        if constexpr ((P & 3) == 0) tq = tcd[P >> 2];  // thresholds of nodes P .. P + 3
-        constexpr int L = kDfs.node[P];
-        const float t = (P & 3) == 0 ? tq.x : (P & 3) == 1 ? tq.y : (P & 3) == 2 ? tq.z : tq.w;
-        bits[P & 3] |= ((v[P].x < t) | (v[P].y < t)) ? (1u << L) : 0u;
-        walk<P + 1>(v, d, tcd, tq, bits);
+        if constexpr (j == 0) tq = tcw[P >> 2];  // negated thresholds of positions P .. P + 3
+        const float tn = j == 0 ? tq.x : j == 1 ? tq.y : j == 2 ? tq.z : tq.w;
+        const float2 w = __fadd2_rn(v[P], make_float2(tn, tn));
+        part[j] = __funnelshift_l(__float_as_uint(w.x) | __float_as_uint(w.y), part[j], 1);
+        walk<P + 1>(v, d, tcw, tq, part);
     }
+}
+
+__device__ __forceinline__ unsigned walk_bits(const unsigned (&part)[4])
+{
+    return (__brev(part[0]) >> 24) | (__brev(part[1]) >> 16) | (__brev(part[2]) >> 8) | __brev(part[3]);
 }
 
 // Append the kNN / eps tuples of this lane's triggered subspaces (bit L of
 // `bits`: either candidate fell below subspace L's pass threshold in the
-// walk).  Every round each lane takes its two lowest remaining subspaces, so
-// the rounds number half the most subspaces any one lane triggered, and the
-// two recomputations and threshold loads of a round are independent of each
-// other.  A node's distances are recomputed from the root with the walk's own
-// FFMA2 chain (the low features of L folded from the highest down), so they
-// are bit-identical to the walk's; a round appends at most 128 tuples, and a
-// nearly full buffer is flushed.  Out of line: it runs on a minority of
-// steps, and inlined its registers would count against the walk's.  Returns
-// the new tuple count.
+// walk), with the work spread evenly over the warp.  Each lane stages its
+// two candidates (root, the low features' differences and the original
+// indices) in the tail of the tuple buffer and lists its (lane, L) pairs
+// there at its offset of the warp's prefix sum; then every lane takes one
+// pair per round, so the rounds number the warp's pairs over 32, not the
+// most any one lane triggered.  A node's distances are recomputed from the
+// root with the walk's own FFMA2 chain (the low features of L folded from the
+// highest down), so they are bit-identical to the walk's; a round appends at
+// most 64 tuples, and a nearly full buffer is flushed.  Out of line: it runs
+// on a minority of steps, and inlined its registers would count against the
+// walk's.  Returns the new tuple count.
 __device__ __forceinline__ float2 node_of(float2 v, int L, float2 d0, float2 d1, float2 d2, float2 d3, float2 d4)
 {
     if (L & 16) v = __ffma2_rn(d4, d4, v);
@@ -321,36 +329,63 @@ __device__ __noinline__ int append_hits(int ws_off, unsigned bits, float2 root, 
                                         float2 d2, float2 d3, float2 d4, int count, int ja, int jb, int k)
 {
     WarpState<KMAX> &ws = *reinterpret_cast<WarpState<KMAX> *>(tree_smem + ws_off);
-    const unsigned lower = (1u << dev::lane_id()) - 1u;
-    while (__any_sync(dev::kFull, bits != 0u)) {
-        const bool h1 = bits != 0u;
-        const int L1 = h1 ? __ffs(bits) - 1 : 0;
-        bits &= bits - 1u;
-        const bool h2 = bits != 0u;
-        const int L2 = h2 ? __ffs(bits) - 1 : 0;
-        bits &= bits - 1u;
-        const float2 v1 = node_of(root, L1, d0, d1, d2, d3, d4);
-        const float2 v2 = node_of(root, L2, d0, d1, d2, d3, d4);
-        const float t1 = ws.tc[L1], t2 = ws.tc[L2];
-        const bool p1a = h1 && v1.x < t1, p1b = h1 && v1.y < t1;
-        const bool p2a = h2 && v2.x < t2, p2b = h2 && v2.y < t2;
-        const unsigned b1a = __ballot_sync(dev::kFull, p1a);
-        const unsigned b1b = __ballot_sync(dev::kFull, p1b);
-        const unsigned b2a = __ballot_sync(dev::kFull, p2a);
-        const unsigned b2b = __ballot_sync(dev::kFull, p2b);
-        const int o1b = count + __popc(b1a);
-        const int o2a = o1b + __popc(b1b);
-        const int o2b = o2a + __popc(b2a);
-        if (p1a) ws.tbuf[count + __popc(b1a & lower)] = make_uint2(__float_as_uint(v1.x), (L1 << 24) | (ja & 0xffffff));
-        if (p1b) ws.tbuf[o1b + __popc(b1b & lower)] = make_uint2(__float_as_uint(v1.y), (L1 << 24) | (jb & 0xffffff));
-        if (p2a) ws.tbuf[o2a + __popc(b2a & lower)] = make_uint2(__float_as_uint(v2.x), (L2 << 24) | (ja & 0xffffff));
-        if (p2b) ws.tbuf[o2b + __popc(b2b & lower)] = make_uint2(__float_as_uint(v2.y), (L2 << 24) | (jb & 0xffffff));
-        count = o2b + __popc(b2b);
+    const unsigned lane = dev::lane_id();
+    const unsigned lower = (1u << lane) - 1u;
+    float2 *stg = reinterpret_cast<float2 *>(&ws.tbuf[kTStage]);
+    unsigned short *pairs = reinterpret_cast<unsigned short *>(stg + 7 * 32);
+    __syncwarp();  // a previous call's readers of the staging area are done
+    stg[0 * 32 + lane] = root;
+    stg[1 * 32 + lane] = d0;
+    stg[2 * 32 + lane] = d1;
+    stg[3 * 32 + lane] = d2;
+    stg[4 * 32 + lane] = d3;
+    stg[5 * 32 + lane] = d4;
+    stg[6 * 32 + lane] = make_float2(__int_as_float(ja), __int_as_float(jb));
+    const int c = __popc(bits);
+    int inc = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(dev::kFull, inc, o);
+        if ((int)lane >= o) inc += v;
+    }
+    const int total = __shfl_sync(dev::kFull, inc, 31);
+    int pos = inc - c;
+    for (unsigned m = bits; m; m &= m - 1u) pairs[pos++] = (unsigned short)((lane << 5) | (unsigned)(__ffs(m) - 1));
+    __syncwarp();
+    for (int e0 = 0; e0 < total; e0 += 32) {
+        const int e = e0 + (int)lane;
+        const bool has = e < total;
+        const unsigned pr = has ? pairs[e] : 0u;
+        const int o = (int)(pr >> 5), L = (int)(pr & 31u);
+        const float2 jj = stg[6 * 32 + o];
+        const float2 v = node_of(stg[o], L, stg[1 * 32 + o], stg[2 * 32 + o], stg[3 * 32 + o], stg[4 * 32 + o],
+                                 stg[5 * 32 + o]);
+        // eps-neighbours are counted here; only kNN candidates become tuples
+        const float e2 = ws.eps2[L];
+        const bool ia = has && v.x <= e2, ib = has && v.y <= e2;
+        if (ia || ib) {
+            const float es = ws.escale[L];
+            atomicAdd(&ws.cnt[L], (ia ? 1 : 0) + (ib ? 1 : 0));
+            atomicAdd(&ws.epart[L], (ia ? dev::eps_quant(v.x, es) : 0u) + (ib ? dev::eps_quant(v.y, es) : 0u));
+        }
+        const float t = ws.T[L];  // -inf for inactive subspaces and k = 0
+        const bool pa = has && v.x <= t, pb = has && v.y <= t;
+        const unsigned ba = __ballot_sync(dev::kFull, pa);
+        const unsigned bb = __ballot_sync(dev::kFull, pb);
+        const int ob = count + __popc(ba);
+        if (pa) ws.tbuf[count + __popc(ba & lower)] = make_uint2(__float_as_uint(v.x), (L << 24) | (__float_as_int(jj.x) & 0xffffff));
+        if (pb) ws.tbuf[ob + __popc(bb & lower)] = make_uint2(__float_as_uint(v.y), (L << 24) | (__float_as_int(jj.y) & 0xffffff));
+        count = ob + __popc(bb);
         if (count > kTFlushAt) {
             flush_tuples<KMAX>(ws_off, count, k);
             count = 0;
         }
     }
+    // this call's eps sums (<= 64 terms a subspace) into the exact totals
+    __syncwarp();
+    ws.esum[lane] += ws.epart[lane];
+    ws.epart[lane] = 0u;
+    __syncwarp();
     return count;
 }
 
@@ -497,7 +532,7 @@ __device__ __noinline__ void setup_phase(int ws_off, const float4 *__restrict__ 
         ws.Tj[L] = 0x7fffffff;
     }
     ws.tc[L] = mine ? fmaxf(next_up(ws.T[L]), eps_up(e2)) : -CUDART_INF_F;
-    ws.tcd[kDfsPos.pos[L]] = ws.tc[L];
+    ws.tcw[walk_pos(L)] = -ws.tc[L];
     update_tcmax(ws);
 }
 
@@ -659,8 +694,8 @@ __global__ void __launch_bounds__(CW * 32, kCtasPerSm<CW>)
             const float tmax = ws.tcmax;
             if (!__all_sync(dev::kFull, (v[0].x >= tmax) & (v[0].y >= tmax))) {
                 unsigned part[4] = {0u, 0u, 0u, 0u};
-                walk<0>(v, d, reinterpret_cast<const float4 *>(ws.tcd), make_float4(0.f, 0.f, 0.f, 0.f), part);
-                const unsigned bits = (part[0] | part[1]) | (part[2] | part[3]);
+                walk<0>(v, d, reinterpret_cast<const float4 *>(ws.tcw), make_float4(0.f, 0.f, 0.f, 0.f), part);
+                const unsigned bits = walk_bits(part);
                 if (__any_sync(dev::kFull, bits != 0u)) {
                     tcount = append_hits<KMAX>(ws_off, bits, v[0], d[0], d[1], d[2], d[3], d[4], tcount, oa, ob,
                                                k);
