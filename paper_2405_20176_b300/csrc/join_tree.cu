@@ -125,6 +125,17 @@ static_assert(kDfs.node[1] == 16 && kDfs.parent[kW / 2] > 0, "DFS order as expec
 // 0..7): a parent (L with its lowest set bit cleared) always comes first.
 __host__ __device__ constexpr int walk_pos(int L) { return (L >> 3) + 4 * (L & 7); }
 __host__ __device__ constexpr int low_bit(int L) { return (L & 1) ? 0 : (L & 2) ? 1 : (L & 4) ? 2 : (L & 8) ? 3 : 4; }
+constexpr bool walk_order_valid()
+{
+    bool seen[kW] = {};
+    for (int L = 0; L < kW; ++L) {
+        if (walk_pos(L) < 0 || walk_pos(L) >= kW || seen[walk_pos(L)]) return false;  // a permutation
+        seen[walk_pos(L)] = true;
+        if (L > 0 && !(walk_pos(L & (L - 1)) < walk_pos(L))) return false;  // parents first
+    }
+    return true;
+}
+static_assert(walk_order_valid(), "the walk visits every node once, each after its parent");
 
 // Per consumer warp: the state of its query across the chunk's 32 subspaces.
 template <int KMAX>
