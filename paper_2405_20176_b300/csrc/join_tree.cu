@@ -140,7 +140,8 @@ static_assert(walk_order_valid(), "the walk visits every node once, each after i
 // Per consumer warp: the state of its query across the chunk's 32 subspaces.
 template <int KMAX>
 struct WarpState {
-    uint2 tbuf[kTBuf];              // pending events: (d2 bits, L << 24 | candidate);
+    uint2 tbuf[kTBuf];              // pending kNN candidates: (d2 bits, L << 24 | candidate);
+                                    // its tail stages an append's candidates and pairs;
                                     // during the set-up phase, the transpose buffer
     float ld[kW][KMAX + 1];         // kNN lists by L; +1 keeps both access patterns
     int lj[kW][KMAX + 1];           // free of bank conflicts
@@ -209,16 +210,15 @@ __device__ __forceinline__ void list_offer(float *ld, int *lj, int k, float d2, 
     Tj = lj[0];
 }
 
-// Process the buffered event tuples.  First, 32 at a time with every lane
-// busy: eps counts and exact distance sums for the tuples within eps
-// (shared-memory atomics), while the tuples at or below their subspace's
-// current k-th distance are compacted to the front of the buffer.  Then those
-// kNN candidates are offered to their lists, 32 at a time: lanes holding
-// candidates of different subspaces insert at the same time (each into its
-// own list); of the lanes that share a subspace, one per round claims the list
-// (the last writer of a shared slot), the others retry.  The k smallest
-// (distance, original index) pairs do not depend on the order of insertion.
-// Returns true when a kNN list changed.
+// Process the buffered kNN candidates (the appends count the eps-neighbours
+// themselves).  First, 32 at a time with every lane busy, the candidates
+// still at or below their subspace's current k-th distance are compacted to
+// the front of the buffer.  Then they are offered to their lists, 32 at a
+// time: lanes holding candidates of different subspaces insert at the same
+// time (each into its own list); of the lanes that share a subspace, one per
+// round claims the list (the last writer of a shared slot), the others retry.
+// The k smallest (distance, original index) pairs do not depend on the order
+// of insertion.  Returns true when a kNN list changed.
 template <int KMAX>
 __device__ __noinline__ bool flush_tuples(int ws_off, int count, int k)
 {
@@ -226,8 +226,9 @@ __device__ __noinline__ bool flush_tuples(int ws_off, int count, int k)
     const unsigned lane = dev::lane_id();
     unsigned changed = 0;  // bit L: list L changed
     __syncwarp();
-    // eps counts and exact distance sums; the kNN candidates are compacted to
-    // the front of the buffer (in place: a batch writes at most as many as it read)
+    // the candidates still at or below their subspace's k-th distance are
+    // compacted to the front of the buffer (in place: a batch writes at most as
+    // many as it read)
     int nw = 0;
     for (int b = 0; b < count; b += 32) {
         const int idx = b + (int)lane;
@@ -270,7 +271,7 @@ __device__ __noinline__ bool flush_tuples(int ws_off, int count, int k)
     }
     changed = __reduce_or_sync(dev::kFull, changed);
     __syncwarp();
-    ws.esum[lane] += ws.epart[lane];
+    ws.esum[lane] += ws.epart[lane];  // an interrupted append's eps sums so far
     ws.epart[lane] = 0u;
     if ((changed >> lane) & 1u) {
         const float t = fmaxf(next_up(ws.T[lane]), eps_up(ws.eps2[lane]));
@@ -312,19 +313,22 @@ __device__ __forceinline__ unsigned walk_bits(const unsigned (&part)[4])
     return (__brev(part[0]) >> 24) | (__brev(part[1]) >> 16) | (__brev(part[2]) >> 8) | __brev(part[3]);
 }
 
-// Append the kNN / eps tuples of this lane's triggered subspaces (bit L of
-// `bits`: either candidate fell below subspace L's pass threshold in the
-// walk), with the work spread evenly over the warp.  Each lane stages its
-// two candidates (root, the low features' differences and the original
-// indices) in the tail of the tuple buffer and lists its (lane, L) pairs
-// there at its offset of the warp's prefix sum; then every lane takes one
-// pair per round, so the rounds number the warp's pairs over 32, not the
-// most any one lane triggered.  A node's distances are recomputed from the
-// root with the walk's own FFMA2 chain (the low features of L folded from the
-// highest down), so they are bit-identical to the walk's; a round appends at
-// most 64 tuples, and a nearly full buffer is flushed.  Out of line: it runs
-// on a minority of steps, and inlined its registers would count against the
-// walk's.  Returns the new tuple count.
+// Handle this lane's triggered subspaces (bit L of `bits`: either candidate
+// fell below subspace L's pass threshold in the walk), with the work spread
+// evenly over the warp.  Each lane stages its two candidates (root, the low
+// features' differences and the original indices) in the tail of the tuple
+// buffer and lists its (lane, L) pairs there at its offset of the warp's
+// prefix sum; then every lane takes one pair per round, so the rounds number
+// the warp's pairs over 32, not the most any one lane triggered.  A node's
+// distances are recomputed from the root with the walk's own FFMA2 chain (the
+// low features of L folded from the highest down), so they are bit-identical
+// to the walk's.  eps-neighbours are counted and their quantised distances
+// summed right here (shared-memory atomics, merged into the exact totals when
+// the call ends); candidates at or below the subspace's k-th distance are
+// appended as tuples for the next flush.  A round appends at most 64 tuples,
+// and a nearly full buffer is flushed.  Out of line: it runs on a minority of
+// steps, and inlined its registers would count against the walk's.  Returns
+// the new tuple count.
 __device__ __forceinline__ float2 node_of(float2 v, int L, float2 d0, float2 d1, float2 d2, float2 d3, float2 d4)
 {
     if (L & 16) v = __ffma2_rn(d4, d4, v);
