@@ -78,11 +78,12 @@ def parse():
                     help="'all', a count of seeded sample subspaces, or 'chunk:H' (H = 10 binary "
                          "digits: the 32 subspaces (H << 5) | L sharing that high part)")
     ap.add_argument("--k", type=int, default=K_DEFAULT)
-    ap.add_argument("--precision", choices=["fp32", "tc_f16", "tc_bf16", "both", "all"], default="both",
-                    help="fp32: the plain join; tc_f16 / tc_bf16: the tensor-core filtered join "
-                         "with FP16 / BF16 operands; both (default): time the plain join as the "
+    ap.add_argument("--precision", choices=["fp32", "tc_f16", "tc_bf16", "tc_tf32", "both", "all"],
+                    default="both",
+                    help="fp32: the plain join; tc_f16 / tc_bf16 / tc_tf32: the tensor-core filtered join "
+                         "with FP16 / BF16 / TF32 operands; both (default): time the plain join as the "
                          "headline and the FP16 tensor-core join beside it on the same workload; "
-                         "all: the BF16 tensor-core join beside those two")
+                         "all: the BF16 and TF32 tensor-core joins beside those two")
     ap.add_argument("--index", choices=["auto", "grid", "none"], default="auto",
                     help="grid index for subspaces of <= 4 features: the library's choice "
                          "(auto), always, or never")
@@ -231,9 +232,10 @@ def run_ours(args, rank, world, dist):
     m, n, k = masks.size, args.n, args.k
     m_total = all_masks.size
     index_flag = {"auto": 0, "grid": snaps.SNAPS_INDEX_GRID, "none": snaps.SNAPS_INDEX_NONE}[args.index]
-    head_prec = {"tc_f16": snaps.SNAPS_TC_F16, "tc_bf16": snaps.SNAPS_TC_BF16}.get(
+    head_prec = {"tc_f16": snaps.SNAPS_TC_F16, "tc_bf16": snaps.SNAPS_TC_BF16, "tc_tf32": snaps.SNAPS_TC_TF32}.get(
         args.precision, snaps.SNAPS_FP32) | index_flag
-    form_name = {snaps.SNAPS_FP32: "fp32", snaps.SNAPS_TC_F16: "tc_f16", snaps.SNAPS_TC_BF16: "tc_bf16"}
+    form_name = {snaps.SNAPS_FP32: "fp32", snaps.SNAPS_TC_F16: "tc_f16", snaps.SNAPS_TC_BF16: "tc_bf16",
+                 snaps.SNAPS_TC_TF32: "tc_tf32"}
     ctx = snaps.snaps_create(local)
     stream = torch.cuda.current_stream()
     x_dev = torch.from_numpy(x).to(dev)
@@ -343,7 +345,8 @@ def run_ours(args, rank, world, dist):
         alu_roofline(trace, args.steps)
 
     tc_legs = {}
-    for form in {"both": [snaps.SNAPS_TC_F16], "all": [snaps.SNAPS_TC_F16, snaps.SNAPS_TC_BF16]}.get(
+    for form in {"both": [snaps.SNAPS_TC_F16],
+                 "all": [snaps.SNAPS_TC_F16, snaps.SNAPS_TC_BF16, snaps.SNAPS_TC_TF32]}.get(
             args.precision, []):
         tc_ms, tc_trace, tc_clocks = timed_leg(form | index_flag, args.tc_steps, 1)
         tc_units = float(n) * m_total * args.tc_steps
@@ -647,7 +650,8 @@ def run_precision(args):
     x = snaps_inputs.population(n, 0)
     sets = {"chunks": snaps_inputs.chunk_sample(8, SAMPLE_SEED),
             "random": snaps_inputs.mask_sample(256, SAMPLE_SEED)}
-    forms = {"fp32": snaps.SNAPS_FP32, "tc_f16": snaps.SNAPS_TC_F16, "tc_bf16": snaps.SNAPS_TC_BF16}
+    forms = {"fp32": snaps.SNAPS_FP32, "tc_f16": snaps.SNAPS_TC_F16, "tc_bf16": snaps.SNAPS_TC_BF16,
+             "tc_tf32": snaps.SNAPS_TC_TF32}
     ctx = snaps.snaps_create(0)
     warm = snaps.snaps_index(ctx, torch.from_numpy(snaps_inputs.population(4096, 1)).cuda())
     sc = torch.empty((256, 4, 4096), device="cuda")
@@ -678,14 +682,14 @@ def run_precision(args):
                               "evals_per_s": float(n) * (n - 1) * m.size / (ms / 1e3),
                               "phase_ms": {k: v[0] for k, v in tr.items() if v[1]}}
                 print(f"[bench] precision {sname} {fname}: {ms:.1f} ms", file=sys.stderr, flush=True)
-            for fname in ("tc_f16", "tc_bf16"):
+            for fname in ("tc_f16", "tc_bf16", "tc_tf32"):
                 row[fname]["vs_plain"] = row["fp32"]["ms"] / row[fname]["ms"]
             rows[sname] = row
     snaps.snaps_release(pop)
     snaps.snaps_destroy(ctx)
     return {"metric": "objects*subspaces/s, tensor-core forms vs plain FP32 (precision workload)",
             "unit": "objects*subspaces/s", "n": n, "k": args.k, "sets": rows, "clocks": clk.summary(),
-            "dtype": "f32 (plain), f16 / bf16 high+low parts with f32 accumulation (tensor-core forms)",
+            "dtype": "f32 (plain), f16 / bf16 / tf32 high+low parts with f32 accumulation (tensor-core forms)",
             "data": "synthetic",
             "config": {"workload": f"N={n} objects (seed 0); 'chunks': eight whole 32-subspace chunks "
                                    f"(seed {SAMPLE_SEED}), 'random': 256 random subspaces (seed {SAMPLE_SEED}); "

@@ -76,12 +76,14 @@ typedef enum snaps_status {
 #define SNAPS_NORM_MINMAX 0x1u   /* map every feature onto [0, 1] by its min and max (Sec. 3.3) */
 #define SNAPS_NAN_TO_MEAN 0x2u   /* replace NaN by the feature's mean first (Sec. 2.1) */
 
-/* precision argument of snaps_scores / snaps_request: one of the three join
+/* precision argument of snaps_scores / snaps_request: one of the four join
  * forms, optionally OR-ed with one index choice for low-dimensional subspaces */
 #define SNAPS_FP32 0u            /* plain FP32 join */
 #define SNAPS_TC_F16 1u          /* tensor-core contraction, high/low FP16 parts, exact FP32 recompute near
                                   * eps and the k-th distance */
 #define SNAPS_TC_BF16 2u         /* the same with BF16 parts: a 4x wider margin, more recomputes */
+#define SNAPS_TC_TF32 3u         /* the same with TF32 parts (kind::tf32, K = 8 per MMA): FP16's margin,
+                                  * twice the MMAs and operand bytes */
 /* The tensor-core forms join subspaces in blocks of 256 (sorted by
  * dimension), and a block costs about the same however few it carries.  A
  * block is formed only with at least a minimum fill of subspaces: the
@@ -181,17 +183,17 @@ snaps_status snaps_eps_selfjoin(snaps_pop *pop, const uint16_t *masks, int n_mas
                                 void *stream);
 
 /* Both joins and the four outlier metrics per object and subspace (Table 2).
- * k, eps: as above.  precision: SNAPS_FP32 (plain FP32 joins), SNAPS_TC_F16
- *   or SNAPS_TC_BF16 (the squared-difference x subspace-mask contraction on
- *   the tensor cores, each scaled squared difference split into a high and a
- *   low FP16 or BF16 part, FP32 accumulation: d^2 to within 3.9e-6 (FP16) or
- *   7.4e-6 (BF16) relative.  A candidate within a margin of 2^-17 (FP16) or
- *   2^-15 (BF16) of eps^2 or of the k-th distance is recomputed exactly in
- *   FP32, which decides; one clearly inside eps is counted and its distance
- *   taken from the accumulator.  So counts, kNN lists, in-degrees and kNN
- *   means are the plain form's bits, and the mean eps distance agrees with
- *   the plain form's to 2.5e-6 (FP16) or 4.2e-6 (BF16) relative plus
- *   eps / 2^20).  The tensor-core forms need
+ * k, eps: as above.  precision: SNAPS_FP32 (plain FP32 joins), SNAPS_TC_F16,
+ *   SNAPS_TC_BF16 or SNAPS_TC_TF32 (the squared-difference x subspace-mask
+ *   contraction on the tensor cores, each scaled squared difference split
+ *   into a high and a low FP16, BF16 or TF32 part, FP32 accumulation: d^2 to
+ *   within 3.9e-6 (FP16, TF32) or 7.4e-6 (BF16) relative.  A candidate within
+ *   a margin of 2^-17 (FP16, TF32) or 2^-15 (BF16) of eps^2 or of the k-th
+ *   distance is recomputed exactly in FP32, which decides; one clearly inside
+ *   eps is counted and its distance taken from the accumulator.  So counts,
+ *   kNN lists, in-degrees and kNN means are the plain form's bits, and the
+ *   mean eps distance agrees with the plain form's to 2.5e-6 (FP16, TF32) or
+ *   4.2e-6 (BF16) relative plus eps / 2^20).  The tensor-core forms need
  *   every feature to span at most 1, which SNAPS_NORM_MINMAX guarantees
  *   (EINVAL otherwise).  Each may be OR-ed with SNAPS_INDEX_GRID or
  *   SNAPS_INDEX_NONE (see their definitions).
@@ -324,7 +326,7 @@ typedef struct snaps_tc_tune {
 /* Choose the subspaces-per-block threshold of the tensor-core forms for
  * populations of this one's size class (floor(log2 n)) and this k class.  It
  * times one block of 256 subspaces of 3..12 features (a fixed pseudo-random
- * choice) in `precision` (SNAPS_TC_F16 or SNAPS_TC_BF16) and 32 of them
+ * choice) in `precision` (SNAPS_TC_F16, SNAPS_TC_BF16 or SNAPS_TC_TF32) and 32 of them
  * joined one at a time in plain FP32, on the population or, above
  * SNAPS_TUNE_MAX_N objects, an evenly strided sample of it.  The block pays
  * once it carries more subspaces than its time buys on their own:

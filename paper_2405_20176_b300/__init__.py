@@ -33,6 +33,7 @@ SNAPS_NAN_TO_MEAN = 0x2
 SNAPS_FP32 = 0
 SNAPS_TC_F16 = 1
 SNAPS_TC_BF16 = 2
+SNAPS_TC_TF32 = 3
 SNAPS_INDEX_GRID = 0x100
 SNAPS_INDEX_NONE = 0x200
 SNAPS_GRID_AUTO_N = 65536

@@ -289,7 +289,7 @@ snaps_status validate(const JobSpec &j)
     if (j.top && (j.top_n < 1 || j.top_n > 1024 || j.top_n > p->n))
         FAIL(SNAPS_EINVAL, "top_n must be in 1..min(1024, n) (got %d)", j.top_n);
     const uint32_t form = j.precision & 0xFFu, index = j.precision & ~0xFFu;
-    if (form != SNAPS_FP32 && form != SNAPS_TC_F16 && form != SNAPS_TC_BF16)
+    if (form != SNAPS_FP32 && form != SNAPS_TC_F16 && form != SNAPS_TC_BF16 && form != SNAPS_TC_TF32)
         FAIL(SNAPS_EINVAL, "unknown precision %u", j.precision);
     if (index != 0u && index != SNAPS_INDEX_GRID && index != SNAPS_INDEX_NONE)
         FAIL(SNAPS_EINVAL, "unknown index choice in precision 0x%x", j.precision);
@@ -779,8 +779,11 @@ snaps_status run_job(snaps_ctx *ctx, const JobSpec &j, cudaStream_t st, Scratch 
     }
     if (!pl.blocks.empty()) {
         TraceScope ts(ctx, SNAPS_PHASE_JOIN_TC, st);
+        const uint32_t form = j.precision & 0xFFu;
         SNAPS_TRY(launch_join_tc(shape, L.blocks, (int)pl.blocks.size(),
-                                 (j.precision & 0xFFu) == SNAPS_TC_BF16, out, ctrl, st));
+                                 form == SNAPS_TC_TF32 ? kTcFormTF32 : form == SNAPS_TC_BF16 ? kTcFormBF16
+                                                                                              : kTcFormF16,
+                                 out, ctrl, st));
     }
     if (!pl.grids.empty()) {
         const GridBufs gb = grid_carve(L.grid, n, pl.grid_max_cells);
@@ -1701,8 +1704,8 @@ snaps_status snaps_autotune_tc(snaps_pop *pop, int k, uint32_t precision, snaps_
 {
     clear_error();
     if (!pop) FAIL(SNAPS_EINVAL, "pop is NULL");
-    if (precision != SNAPS_TC_F16 && precision != SNAPS_TC_BF16)
-        FAIL(SNAPS_EINVAL, "precision must be SNAPS_TC_F16 or SNAPS_TC_BF16 (got %u)", precision);
+    if (precision != SNAPS_TC_F16 && precision != SNAPS_TC_BF16 && precision != SNAPS_TC_TF32)
+        FAIL(SNAPS_EINVAL, "precision must be SNAPS_TC_F16, SNAPS_TC_BF16 or SNAPS_TC_TF32 (got %u)", precision);
     if (!pop->unit_range) FAIL(SNAPS_EINVAL, "the tensor-core forms need every feature to span at most 1");
     ON_DEVICE(pop->ctx->device);
     snaps_ctx *ctx = pop->ctx;

@@ -108,9 +108,13 @@ struct WorkItem {
 // must be <= kmax (16 or 32).
 snaps_status launch_join_worklist(const WorkItem *items, int n_items, int n_ctas, int kmax, cudaStream_t st);
 
-// Launch the tensor-core filtered join over `n_blocks` blocks (device array).
-// Requires every feature of the population to span at most 1.
-snaps_status launch_join_tc(const JoinShape &s, const TcBlock *blocks, int n_blocks, bool bf16,
+// Operand forms of the tensor-core join.
+constexpr int kTcFormF16 = 0, kTcFormBF16 = 1, kTcFormTF32 = 2;
+
+// Launch the tensor-core filtered join over `n_blocks` blocks (device array)
+// with FP16, BF16 or TF32 high/low parts (`form`).  Requires every feature of
+// the population to span at most 1.
+snaps_status launch_join_tc(const JoinShape &s, const TcBlock *blocks, int n_blocks, int form,
                             const JoinOut &o, DeviceControl *ctrl, cudaStream_t st);
 
 // Launch the subspace-batched tree join over `n_chunks` chunks (device array).

@@ -1,21 +1,23 @@
 // Tensor-core filtered self-join: DSSJ (Sec. 3.5) and kNNSJ (Sec. 3.6) for
 // any list of subspaces, with the one dense contraction of the method --
 // per-pair squared feature differences times the 0/1 subspace-mask matrix --
-// on the 5th-generation tensor cores (tcgen05, kind::f16 with FP16 or BF16
-// operands, FP32 accumulators in tensor memory).
+// on the 5th-generation tensor cores (tcgen05: kind::f16 with FP16 or BF16
+// operands, or kind::tf32 with TF32 operands; FP32 accumulators in tensor
+// memory).
 //
 // The contraction.  For a query i and 128 candidates j, each squared
 // difference (x_jf - x_if)^2, scaled by S = 2^11 (exact), is split into a
 // high part h = round(s) in the operand type and a low part l = round(s - h).
 // Two MMAs (M = 128 subspaces, N = 128 candidates, K = 16), one over the high
-// parts and one over the low parts, against the same mask operand, leave in
+// parts and one over the low parts, against the same mask operand (four with
+// TF32 parts, whose MMAs take K = 8: two 8-column slices each), leave in
 // tensor memory
 //     D[S][j] = S * sum_{f in S} (x_jf - x_if)^2 * (1 + e).
-// The split leaves 2^-22 relative (FP16) or 2^-18 (BF16) per term; the FP32
+// The split leaves 2^-22 relative (FP16, TF32) or 2^-18 (BF16) per term; the FP32
 // accumulation of the 30 exact products adds at most 30 roundings of 2^-23
 // (the bound for truncating adds; the hardware's own rounding is not
-// documented), 3.6e-6.  So |e| <= 3.9e-6 (FP16) or 7.4e-6 (BF16).  The
-// decisions use a margin delta (2^-17 = 7.6e-6 for FP16, 2^-15 for BF16)
+// documented), 3.6e-6.  So |e| <= 3.9e-6 (FP16, TF32) or 7.4e-6 (BF16).  The
+// decisions use a margin delta (2^-17 = 7.6e-6 for FP16 and TF32, 2^-15 for BF16)
 // that also covers the canonical FP32 fold's own rounding (<= (d + 2) 2^-24),
 // plus an absolute slack of 2^-20 (scaled) for FP16 parts below its normal
 // range:
@@ -28,7 +30,7 @@
 // So eps counts, kNN lists, in-degrees and kNN mean distances are the plain
 // FP32 path's, bit for bit; the mean eps distance takes the accumulator's
 // distances, within |e| / 2 + 2^-24 (d + 2) of the canonical ones (2.5e-6
-// relative for FP16, 4.2e-6 for BF16).  Skipped rows (padding, the query itself, the rows folded at start-up)
+// relative for FP16 and TF32, 4.2e-6 for BF16).  Skipped rows (padding, the query itself, the rows folded at start-up)
 // carry a large high part in every feature, far above any threshold (every
 // threshold is capped at 16 S, above the largest real D of a unit-range
 // population, 15 S (1 + delta)).
@@ -92,7 +94,6 @@ constexpr int kTile = 256;                // rows per staged tile (one 16 KB bul
 constexpr int kSubPerTile = kTile / kNC;  // 2
 constexpr int kWarm = 32;                 // rows folded exactly before the filter starts
 constexpr uint32_t kLBO = 128;            // K-direction step between 8x16-byte core matrices
-constexpr uint32_t kSBO = 256;            // row-direction step
 constexpr uint32_t kTmemCols = 2 * kHalves * kNC;  // 512: two accumulator sets
 constexpr float kScale = 2048.f;          // S: squared differences are scaled by 2^11
 constexpr float kRsqrtScale = 0.02209708691207961f;  // 1 / sqrt(S)
@@ -102,15 +103,27 @@ static_assert(kHalves == 2 && kTmemCols == 512, "one CTA holds all of an SM's te
 static_assert(kNC * 4 == kConsumers, "every consumer builds four features of one B row");
 static_assert(kRowPad % kTile == 0, "padded rows must cover whole tiles");
 
-template <int KMAX>
-constexpr int kStages = KMAX <= 16 ? 6 : 4;
+// Operand forms: FP16 or BF16 parts (kind::f16, K = 16 per MMA, 2-byte
+// elements) or TF32 parts (kind::tf32, K = 8 per MMA, 4-byte elements, two
+// K-slices per operand).
+constexpr int kFormF16 = kTcFormF16, kFormBF16 = kTcFormBF16, kFormTF32 = kTcFormTF32;
+template <int FORM>
+constexpr int kElemBytes = FORM == kFormTF32 ? 4 : 2;
+template <int FORM>
+constexpr uint32_t kSBO = 8 * 16 * kElemBytes<FORM>;  // row-direction step: 8 rows of 16 elements
+template <int FORM>
+constexpr int kSlices = FORM == kFormTF32 ? 2 : 1;       // MMAs per operand over the 16 columns
 
-template <int KMAX>
+template <int KMAX, int FORM>
+constexpr int kStages = FORM == kFormTF32 ? (KMAX <= 16 ? 6 : 2) : (KMAX <= 16 ? 6 : 4);
+
+template <int KMAX, int FORM>
 struct TcSmem {
-    float4 ring[kStages<KMAX>][kTile * 4];              // candidate tiles (quad-planar)
-    alignas(1024) unsigned char A[kHalves][kM * 32];    // mask bits, 128 x 16, K-major
-    alignas(1024) unsigned char Bh[2][kNC * 32];        // high parts, 128 x 16, K-major
-    alignas(1024) unsigned char Bl[2][kNC * 32];        // low parts
+    static constexpr int kOpBytes = 16 * kElemBytes<FORM>;  // one operand row: 16 columns
+    float4 ring[kStages<KMAX, FORM>][kTile * 4];         // candidate tiles (quad-planar)
+    alignas(1024) unsigned char A[kHalves][kM * kOpBytes];  // mask bits, 128 x 16, K-major
+    alignas(1024) unsigned char Bh[2][kNC * kOpBytes];      // high parts, 128 x 16, K-major
+    alignas(1024) unsigned char Bl[2][kNC * kOpBytes];      // low parts
     float ld[KMAX][kConsumers];                         // kNN lists, entry-major: private
     int lj[KMAX][kConsumers];                           // to a thread, distinct banks
     float tk[kConsumers];                               // each thread's current k-th distance
@@ -118,7 +131,7 @@ struct TcSmem {
     unsigned long long pqs[kNS];                        // sum, handed over at the item's end
     float4 warm[4][kWarm];                              // start-up rows, quad-planar
     float4 xq[4];                                       // the item's query row
-    uint64_t full[kStages<KMAX>];                       // tile landed
+    uint64_t full[kStages<KMAX, FORM>];                 // tile landed
     uint64_t b_ready[2];                                // B rows written (16 warp arrivals)
     uint64_t t_empty[2];                                // accumulators read (16 warp arrivals)
     uint64_t mma_done[2];                               // MMA batch complete (commit)
@@ -128,39 +141,58 @@ struct TcSmem {
 };
 
 // Smem matrix descriptor: K-major, no swizzle, version 1 (sm_100 family).
+template <int FORM>
 __device__ __forceinline__ uint64_t smem_desc(const void *p)
 {
     const uint32_t a = dev::smem_addr(p);
     uint64_t d = (uint64_t)((a >> 4) & 0x3FFFu);
     d |= (uint64_t)((kLBO >> 4) & 0x3FFFu) << 16;
-    d |= (uint64_t)((kSBO >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)((kSBO<FORM> >> 4) & 0x3FFFu) << 32;
     d |= (uint64_t)1 << 46;
     return d;
 }
 
-// Byte offset of element (r, k) in a K-major 16-column 16-bit operand.
+// Byte offset of element (r, k) in a K-major 16-column operand: 8 x 16-byte
+// core matrices, kLBO apart along K and kSBO apart along the rows.
+template <int FORM>
 __device__ __forceinline__ uint32_t op_off(int r, int k)
 {
-    return (uint32_t)((r >> 3) * kSBO + (k >> 3) * kLBO + (r & 7) * 16 + (k & 7) * 2);
+    constexpr int per = 16 / kElemBytes<FORM>;  // elements in a core matrix row
+    return (uint32_t)((r >> 3) * kSBO<FORM> + (k / per) * kLBO + (r & 7) * 16 + (k % per) * kElemBytes<FORM>);
 }
 
-// Operand element encodings and error margins of the two 16-bit forms.
-template <bool BF16>
-struct Op16 {
+// The TF32 value nearest x (ties away from zero in magnitude), as the bits of
+// a float whose 13 low mantissa bits are zero: exactly what the tensor core
+// reads of a 32-bit operand.
+__device__ __forceinline__ uint32_t tf32_bits(float x)
+{
+    return (__float_as_uint(x) + 0x1000u) & 0xFFFFE000u;
+}
+
+// Operand element encodings and error margins of the three forms.
+template <int FORM>
+struct Op {
+    static constexpr bool kBF16 = FORM == kFormBF16, kTF32 = FORM == kFormTF32;
     // 1.0, and the high part of every feature of a skipped row (65504 in FP16,
-    // 65536 in BF16: two of them exceed every capped threshold)
-    static constexpr uint32_t kOne = BF16 ? 0x3F80u : 0x3C00u;
-    static constexpr uint32_t kBig = BF16 ? 0x4780u : 0x7BFFu;
-    // relative margin of the decisions (see the file comment)
-    static constexpr float kDelta = BF16 ? 3.0517578125e-05f : 7.62939453125e-06f;
-    // instruction descriptor: D = F32, A and B of one type (F16 = 0, BF16 = 1),
-    // both K-major; N = 128, M = 128
-    static constexpr uint32_t kIdesc = (1u << 4) | ((BF16 ? 1u : 0u) << 7) | ((BF16 ? 1u : 0u) << 10) |
+    // 65536 in BF16 and TF32: two of them exceed every capped threshold)
+    static constexpr uint32_t kOne = kTF32 ? 0x3F800000u : kBF16 ? 0x3F80u : 0x3C00u;
+    static constexpr uint32_t kBig = kTF32 ? 0x47800000u : kBF16 ? 0x4780u : 0x7BFFu;
+    // relative margin of the decisions (see the file comment); TF32 keeps FP16's
+    // 10 explicit mantissa bits
+    static constexpr float kDelta = kBF16 ? 3.0517578125e-05f : 7.62939453125e-06f;
+    // instruction descriptor: D = F32 (bits 4-5), A and B of one type (bits 7-9,
+    // 10-12: F16 = 0, BF16 = 1 for kind::f16; TF32 = 2 for kind::tf32), both
+    // K-major; N = 128 (bits 17-22, N / 8), M = 128 (bits 24-28, M / 16)
+    static constexpr uint32_t kType = kTF32 ? 2u : kBF16 ? 1u : 0u;
+    static constexpr uint32_t kIdesc = (1u << 4) | (kType << 7) | (kType << 10) |
                                        ((uint32_t)(kNC >> 3) << 17) | ((uint32_t)(kM >> 4) << 24);
     // high and low parts of a scaled squared difference
     static __device__ __forceinline__ void split(float s, uint32_t &h, uint32_t &l)
     {
-        if constexpr (BF16) {
+        if constexpr (kTF32) {
+            h = tf32_bits(s);
+            l = tf32_bits(s - __uint_as_float(h));
+        } else if constexpr (kBF16) {
             const __nv_bfloat16 a = __float2bfloat16_rn(s);
             const __nv_bfloat16 b = __float2bfloat16_rn(s - __bfloat162float(a));
             h = __bfloat16_as_ushort(a);
@@ -249,8 +281,8 @@ struct KnnMax {
 
 // Insert (d2, oj) into thread `tid`'s list when it beats the largest entry by
 // (distance, index).
-template <int KMAX>
-__device__ __forceinline__ void knn_offer(TcSmem<KMAX> &sm, int tid, int k, float d2, int oj, KnnMax &m)
+template <class Smem>
+__device__ __forceinline__ void knn_offer(Smem &sm, int tid, int k, float d2, int oj, KnnMax &m)
 {
     if (d2 < m.T || (d2 == m.T && oj < m.Tj)) {
         dev::heap_sink_root(&sm.ld[0][tid], &sm.lj[0][tid], kConsumers, k, d2, oj);
@@ -267,10 +299,10 @@ struct Thresholds {
     float pass;    // max(e_hi, t_hi): nothing above it needs a look
 };
 
-template <bool BF16>
+template <int FORM>
 __device__ __forceinline__ Thresholds thresholds(bool act, float e2, float tk)
 {
-    constexpr float dl = Op16<BF16>::kDelta;
+    constexpr float dl = Op<FORM>::kDelta;
     Thresholds t;
     if (!act) {
         t.e_lo = t.e_hi = t.t_hi = t.pass = -CUDART_INF_F;
@@ -288,31 +320,45 @@ __device__ __forceinline__ Thresholds thresholds(bool act, float e2, float tk)
 }
 
 // Write the A row of subspace r: its mask bits as 1.0 / 0.0, 0 in column 15.
-template <bool BF16>
+template <int FORM>
 __device__ __forceinline__ void write_a_row(unsigned char *A, int r, uint32_t mask)
 {
-    constexpr uint32_t one = Op16<BF16>::kOne;
-    uint32_t w[8];
+    constexpr uint32_t one = Op<FORM>::kOne;
+    if constexpr (FORM == kFormTF32) {
+        // 16 words, four per 16-byte core-matrix row
 #pragma unroll
-    for (int p = 0; p < 8; ++p) {
-        const int f0 = 2 * p, f1 = 2 * p + 1;
-        const uint32_t lo = ((mask >> f0) & 1u) ? one : 0u;
-        const uint32_t hi = (f1 < 15 && ((mask >> f1) & 1u)) ? one : 0u;
-        w[p] = lo | (hi << 16);
+        for (int c = 0; c < 4; ++c) {
+            uint32_t w[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int f = 4 * c + e;
+                w[e] = (f < 15 && ((mask >> f) & 1u)) ? one : 0u;
+            }
+            *reinterpret_cast<uint4 *>(A + op_off<FORM>(r, 4 * c)) = make_uint4(w[0], w[1], w[2], w[3]);
+        }
+    } else {
+        uint32_t w[8];
+#pragma unroll
+        for (int p = 0; p < 8; ++p) {
+            const int f0 = 2 * p, f1 = 2 * p + 1;
+            const uint32_t lo = ((mask >> f0) & 1u) ? one : 0u;
+            const uint32_t hi = (f1 < 15 && ((mask >> f1) & 1u)) ? one : 0u;
+            w[p] = lo | (hi << 16);
+        }
+        *reinterpret_cast<uint4 *>(A + op_off<FORM>(r, 0)) = make_uint4(w[0], w[1], w[2], w[3]);
+        *reinterpret_cast<uint4 *>(A + op_off<FORM>(r, 8)) = make_uint4(w[4], w[5], w[6], w[7]);
     }
-    *reinterpret_cast<uint4 *>(A + op_off(r, 0)) = make_uint4(w[0], w[1], w[2], w[3]);
-    *reinterpret_cast<uint4 *>(A + op_off(r, 8)) = make_uint4(w[4], w[5], w[6], w[7]);
 }
 
-template <int KMAX, bool BF16>
+template <int KMAX, int FORM>
 __global__ void __launch_bounds__(kCtaThreads, 1)
     join_tc_kernel(JoinShape s, const TcBlock *__restrict__ blocks, int n_blocks, JoinOut o,
                    DeviceControl *ctrl)
 {
-    constexpr int kSt = kStages<KMAX>;
+    constexpr int kSt = kStages<KMAX, FORM>;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char *smem_al = smem_raw + ((1024u - (dev::smem_addr(smem_raw) & 1023u)) & 1023u);
-    TcSmem<KMAX> &sm = *reinterpret_cast<TcSmem<KMAX> *>(smem_al);
+    TcSmem<KMAX, FORM> &sm = *reinterpret_cast<TcSmem<KMAX, FORM> *>(smem_al);
     const int tid = threadIdx.x;
     const int warp = tid >> 5;
     const unsigned lane = tid & 31u;
@@ -381,7 +427,7 @@ __global__ void __launch_bounds__(kCtaThreads, 1)
             };
             for (int st = 0; st < kSt; ++st) issue_next();
             const long long total_sub = (long long)my_items * n_sub;
-            const uint32_t idesc = Op16<BF16>::kIdesc;
+            const uint32_t idesc = Op<FORM>::kIdesc;
             long long g = 0;
             bool ok = true;
             for (; g < total_sub; ++g) {
@@ -396,20 +442,37 @@ __global__ void __launch_bounds__(kCtaThreads, 1)
                     while (issued < tiles_done + kSt) issue_next();
                 }
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                const uint64_t bh = smem_desc(sm.Bh[b]), bl = smem_desc(sm.Bl[b]);
+                const uint64_t bh = smem_desc<FORM>(sm.Bh[b]), bl = smem_desc<FORM>(sm.Bl[b]);
 #pragma unroll
                 for (int hf = 0; hf < kHalves; ++hf) {
-                    const uint64_t adesc = smem_desc(sm.A[hf]);
+                    const uint64_t adesc = smem_desc<FORM>(sm.A[hf]);
                     const uint32_t dt = tmem + (uint32_t)((b * kHalves + hf) * kNC);
-                    // high parts overwrite the accumulator, low parts add to it
-                    asm volatile(
-                        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-                        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(dt),
-                        "l"(adesc), "l"(bh), "r"(idesc), "r"(0));
-                    asm volatile(
-                        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-                        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(dt),
-                        "l"(adesc), "l"(bl), "r"(idesc), "r"(1));
+                    // per K-slice (the TF32 form has two of eight columns each, 256 bytes
+                    // apart, so the descriptors' start addresses step by 256 >> 4 = 16);
+                    // the first high-part MMA overwrites the accumulator, the rest add to it
+#pragma unroll
+                    for (int sl = 0; sl < kSlices<FORM>; ++sl) {
+                        const uint64_t step = (uint64_t)(sl * (2 * kLBO >> 4));
+                        if constexpr (FORM == kFormTF32) {
+                            asm volatile(
+                                "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                                "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(dt),
+                                "l"(adesc + step), "l"(bh + step), "r"(idesc), "r"(sl));
+                            asm volatile(
+                                "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                                "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(dt),
+                                "l"(adesc + step), "l"(bl + step), "r"(idesc), "r"(1));
+                        } else {
+                            asm volatile(
+                                "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                                "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(dt),
+                                "l"(adesc + step), "l"(bh + step), "r"(idesc), "r"(sl));
+                            asm volatile(
+                                "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                                "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(dt),
+                                "l"(adesc + step), "l"(bl + step), "r"(idesc), "r"(1));
+                        }
+                    }
                 }
                 asm volatile(
                     "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
@@ -490,7 +553,7 @@ __global__ void __launch_bounds__(kCtaThreads, 1)
             sm.tk[tid] = CUDART_INF_F;
             if (blk != cur_blk) {
                 // no MMA reads the A operands now: every MMA issued so far was waited for
-                if (cpart == 0) write_a_row<BF16>(sm.A[half], arow, mask);
+                if (cpart == 0) write_a_row<FORM>(sm.A[half], arow, mask);
                 cur_blk = blk;
             }
             if (!cbarrier()) {  // start-up rows staged, lists cleared, masks written
@@ -515,11 +578,11 @@ __global__ void __launch_bounds__(kCtaThreads, 1)
                         ++cnt;
                         qs += dev::eps_quant(d2, esc);
                     }
-                    if (k > 0) knn_offer<KMAX>(sm, tid, k, d2, oj, km);
+                    if (k > 0) knn_offer(sm, tid, k, d2, oj, km);
                 }
             }
             if (act && k > 0) sm.tk[tid] = km.T;
-            Thresholds th = thresholds<BF16>(act, e2, km.T);
+            Thresholds th = thresholds<FORM>(act, e2, km.T);
             if (!cbarrier()) {  // every thread's start-up k-th distance is published
                 ok = false;
                 break;
@@ -541,25 +604,32 @@ __global__ void __launch_bounds__(kCtaThreads, 1)
                 uint32_t h[4], l[4];
                 if (skip) {
                     // never passes: a large high part in every feature
-                    constexpr uint32_t big = Op16<BF16>::kBig;
+                    constexpr uint32_t big = Op<FORM>::kBig;
                     h[0] = h[1] = h[2] = big;
                     h[3] = bq == 3 ? 0u : big;
                     l[0] = l[1] = l[2] = l[3] = 0u;
                 } else {
                     const float4 c = sm.ring[slot][bq * kTile + rr];
                     const float d0 = c.x - bx.x, d1 = c.y - bx.y, d2 = c.z - bx.z, d3 = c.w - bx.w;
-                    Op16<BF16>::split(d0 * d0 * kScale, h[0], l[0]);
-                    Op16<BF16>::split(d1 * d1 * kScale, h[1], l[1]);
-                    Op16<BF16>::split(d2 * d2 * kScale, h[2], l[2]);
+                    Op<FORM>::split(d0 * d0 * kScale, h[0], l[0]);
+                    Op<FORM>::split(d1 * d1 * kScale, h[1], l[1]);
+                    Op<FORM>::split(d2 * d2 * kScale, h[2], l[2]);
                     if (bq == 3) {
                         h[3] = l[3] = 0u;  // float 15 holds the original index, not a feature
                     } else {
-                        Op16<BF16>::split(d3 * d3 * kScale, h[3], l[3]);
+                        Op<FORM>::split(d3 * d3 * kScale, h[3], l[3]);
                     }
                 }
-                const uint32_t off = op_off(br, 4 * bq);
-                *reinterpret_cast<uint2 *>(&sm.Bh[u & 1][off]) = make_uint2(h[0] | (h[1] << 16), h[2] | (h[3] << 16));
-                *reinterpret_cast<uint2 *>(&sm.Bl[u & 1][off]) = make_uint2(l[0] | (l[1] << 16), l[2] | (l[3] << 16));
+                const uint32_t off = op_off<FORM>(br, 4 * bq);
+                if constexpr (FORM == kFormTF32) {
+                    *reinterpret_cast<uint4 *>(&sm.Bh[u & 1][off]) = make_uint4(h[0], h[1], h[2], h[3]);
+                    *reinterpret_cast<uint4 *>(&sm.Bl[u & 1][off]) = make_uint4(l[0], l[1], l[2], l[3]);
+                } else {
+                    *reinterpret_cast<uint2 *>(&sm.Bh[u & 1][off]) =
+                        make_uint2(h[0] | (h[1] << 16), h[2] | (h[3] << 16));
+                    *reinterpret_cast<uint2 *>(&sm.Bl[u & 1][off]) =
+                        make_uint2(l[0] | (l[1] << 16), l[2] | (l[3] << 16));
+                }
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 __syncwarp();
                 if (lane == 0) dev::mbar_arrive(&sm.b_ready[u & 1]);
@@ -586,7 +656,7 @@ __global__ void __launch_bounds__(kCtaThreads, 1)
                                        (uint32_t)((b * kHalves + half) * kNC + cpart * kColsPerThread);
                 // the smaller of the two threads' k-th distances bounds the merged list
                 const float tpart = (act && k > 0) ? sm.tk[partner] : CUDART_INF_F;
-                if (act && k > 0) th = thresholds<BF16>(act, e2, fminf(km.T, tpart));
+                if (act && k > 0) th = thresholds<FORM>(act, e2, fminf(km.T, tpart));
                 unsigned qpart = 0u;  // this sub-tile's quantised sums (<= 64 terms of <= 2^20 + 1)
 #pragma unroll 1
                 for (int h = 0; h < kColsPerThread / 32; ++h) {
@@ -639,9 +709,9 @@ __global__ void __launch_bounds__(kCtaThreads, 1)
                             ++cnt;
                             qs += dev::eps_quant(d2, esc);
                         }
-                        if (cand & bit) knn_offer<KMAX>(sm, tid, k, d2, oj, km);
+                        if (cand & bit) knn_offer(sm, tid, k, d2, oj, km);
                     }
-                    if (cand) th = thresholds<BF16>(act, e2, fminf(km.T, tpart));
+                    if (cand) th = thresholds<FORM>(act, e2, fminf(km.T, tpart));
                 }
                 qs += qpart;
                 if (act && k > 0) sm.tk[tid] = km.T;
@@ -673,7 +743,7 @@ __global__ void __launch_bounds__(kCtaThreads, 1)
                 if (o.eps_count) o.eps_count[(int64_t)slot * n + orig_i] = cnt;
                 if (k > 0) {
                     // the partner's entries into this list, then sort it by (distance, index)
-                    for (int p = 0; p < k; ++p) knn_offer<KMAX>(sm, tid, k, sm.ld[p][partner], sm.lj[p][partner], km);
+                    for (int p = 0; p < k; ++p) knn_offer(sm, tid, k, sm.ld[p][partner], sm.lj[p][partner], km);
                     for (int p = 1; p < k; ++p) {
                         const float v = sm.ld[p][tid];
                         const int j = sm.lj[p][tid];
@@ -708,12 +778,13 @@ __global__ void __launch_bounds__(kCtaThreads, 1)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols));
 }
 
-template <int KMAX, bool BF16>
+template <int KMAX, int FORM>
 snaps_status launch_tc(const JoinShape &s, const TcBlock *blocks, int n_blocks, const JoinOut &o,
                        DeviceControl *ctrl, cudaStream_t st)
 {
-    const size_t smem = sizeof(TcSmem<KMAX>) + 1024;  // slack for the 1024-byte alignment
-    auto kern = join_tc_kernel<KMAX, BF16>;
+    const size_t smem = sizeof(TcSmem<KMAX, FORM>) + 1024;  // slack for the 1024-byte alignment
+    static_assert(sizeof(TcSmem<KMAX, FORM>) + 1024 <= 227 * 1024, "the tensor-core join fits one SM");
+    auto kern = join_tc_kernel<KMAX, FORM>;
     SNAPS_CHECK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int dev = 0, sms = 0;
     SNAPS_CHECK_CUDA(cudaGetDevice(&dev));
@@ -728,16 +799,20 @@ snaps_status launch_tc(const JoinShape &s, const TcBlock *blocks, int n_blocks, 
 
 }  // namespace
 
-snaps_status launch_join_tc(const JoinShape &s, const TcBlock *blocks, int n_blocks, bool bf16,
+snaps_status launch_join_tc(const JoinShape &s, const TcBlock *blocks, int n_blocks, int form,
                             const JoinOut &o, DeviceControl *ctrl, cudaStream_t st)
 {
     if (n_blocks <= 0) return SNAPS_OK;
-    if (bf16) {
-        if (s.k <= 16) return launch_tc<16, true>(s, blocks, n_blocks, o, ctrl, st);
-        return launch_tc<32, true>(s, blocks, n_blocks, o, ctrl, st);
+    if (form == kTcFormTF32) {
+        if (s.k <= 16) return launch_tc<16, kFormTF32>(s, blocks, n_blocks, o, ctrl, st);
+        return launch_tc<32, kFormTF32>(s, blocks, n_blocks, o, ctrl, st);
     }
-    if (s.k <= 16) return launch_tc<16, false>(s, blocks, n_blocks, o, ctrl, st);
-    return launch_tc<32, false>(s, blocks, n_blocks, o, ctrl, st);
+    if (form == kTcFormBF16) {
+        if (s.k <= 16) return launch_tc<16, kFormBF16>(s, blocks, n_blocks, o, ctrl, st);
+        return launch_tc<32, kFormBF16>(s, blocks, n_blocks, o, ctrl, st);
+    }
+    if (s.k <= 16) return launch_tc<16, kFormF16>(s, blocks, n_blocks, o, ctrl, st);
+    return launch_tc<32, kFormF16>(s, blocks, n_blocks, o, ctrl, st);
 }
 
 }  // namespace snaps

@@ -26,7 +26,7 @@ def test_bounded_waits_give_up_and_the_context_recovers():
             n, m = x.shape[0], masks.size
             plain = np.zeros((m, 4, n), dtype=np.float32)
             snaps.snaps_scores(pop, masks, 10, scores=plain)
-            for form in (snaps.SNAPS_TC_F16, snaps.SNAPS_TC_BF16):
+            for form in (snaps.SNAPS_TC_F16, snaps.SNAPS_TC_BF16, snaps.SNAPS_TC_TF32):
                 snaps.snaps_set_wait_limit(ctx, 1)
                 out = np.zeros((m, 4, n), dtype=np.float32)
                 with pytest.raises(snaps.SnapsError) as ei:

@@ -1,6 +1,6 @@
 """The precision workload at its full size: N = 250,000 objects (seed 0), the
-plain FP32 join against both tensor-core forms (FP16 and BF16 high/low
-parts) on 256 subspaces -- eight whole 32-subspace chunks drawn with seed 1,
+plain FP32 join against the three tensor-core forms (FP16, BF16 and TF32
+high/low parts) on 256 subspaces -- eight whole 32-subspace chunks drawn with seed 1,
 one full tensor-core block -- with k = 10 and eps = 0.05 sqrt(d).
 
 Per form and per metric, against the FP64 oracle on 64 evenly spaced
@@ -23,7 +23,8 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 N, K = 250_000, 10
-FORMS = {"fp32": snaps.SNAPS_FP32, "tc_f16": snaps.SNAPS_TC_F16, "tc_bf16": snaps.SNAPS_TC_BF16}
+FORMS = {"fp32": snaps.SNAPS_FP32, "tc_f16": snaps.SNAPS_TC_F16, "tc_bf16": snaps.SNAPS_TC_BF16,
+         "tc_tf32": snaps.SNAPS_TC_TF32}
 
 
 def test_precision_workload_against_the_oracle():
@@ -59,7 +60,7 @@ def test_precision_workload_against_the_oracle():
             snaps.snaps_release(pop)
     finally:
         snaps.snaps_destroy(ctx)
-    for name in ("tc_f16", "tc_bf16"):
+    for name in ("tc_f16", "tc_bf16", "tc_tf32"):
         np.testing.assert_array_equal(got[name]["indeg"], got["fp32"]["indeg"], err_msg=name)
 
     x64 = oracle.normalise(x).astype(np.float64)

@@ -1,4 +1,4 @@
-"""The tensor-core filtered joins (SNAPS_TC_F16, SNAPS_TC_BF16) against the
+"""The tensor-core filtered joins (SNAPS_TC_F16, SNAPS_TC_BF16, SNAPS_TC_TF32) against the
 plain FP32 path and the FP64 oracle, across block fills, subspace mixes, k,
 ragged N and extreme radii (every candidate passing stresses the exact
 recompute).  eps counts, kNN lists, in-degrees and kNN mean distances are the
@@ -35,7 +35,7 @@ def run_both(ctx, x, masks, k, eps=None, top_n=100):
         n = x.shape[0]
         top_n = min(top_n, n)
         out = {}
-        for prec in (snaps.SNAPS_FP32, snaps.SNAPS_TC_F16, snaps.SNAPS_TC_BF16):
+        for prec in (snaps.SNAPS_FP32, snaps.SNAPS_TC_F16, snaps.SNAPS_TC_BF16, snaps.SNAPS_TC_TF32):
             sc = np.zeros((masks.size, 4, n), dtype=np.float32)
             nz = np.zeros_like(sc)
             tp = np.zeros((masks.size, 4, top_n), dtype=np.int32)
@@ -55,7 +55,7 @@ def assert_tc_matches_plain(out, eps2):
     eps distance is sqrt(eps2) / 2^20)."""
     a_sc, a_nz, a_tp = out[snaps.SNAPS_FP32]
     step = np.sqrt(np.maximum(np.asarray(eps2, dtype=np.float64), 0.0)) / 2.0 ** 20
-    for form in (snaps.SNAPS_TC_F16, snaps.SNAPS_TC_BF16):
+    for form in (snaps.SNAPS_TC_F16, snaps.SNAPS_TC_BF16, snaps.SNAPS_TC_TF32):
         sc, nz, tp = out[form]
         np.testing.assert_array_equal(sc[:, SAME], a_sc[:, SAME], err_msg=f"metrics, form {form}")
         np.testing.assert_array_equal(nz[:, SAME], a_nz[:, SAME], err_msg=f"normalised, form {form}")
@@ -100,9 +100,9 @@ def test_tc_extreme_radii_and_large_k(ctx):
     assert_tc_matches_plain(run_both(ctx, x, masks, 10, eps=tiny), eps2_of(masks, tiny))
 
 
-@pytest.mark.parametrize("form", ["f16", "bf16"])
+@pytest.mark.parametrize("form", ["f16", "bf16", "tf32"])
 def test_tc_matches_oracle(ctx, form):
-    prec = snaps.SNAPS_TC_F16 if form == "f16" else snaps.SNAPS_TC_BF16
+    prec = {"f16": snaps.SNAPS_TC_F16, "bf16": snaps.SNAPS_TC_BF16, "tf32": snaps.SNAPS_TC_TF32}[form]
     x = snaps_inputs.population(1500, 41)
     masks = snaps_inputs.mask_sample(12, 41)
     pop = snaps.snaps_index(ctx, x)
@@ -138,7 +138,7 @@ def test_tc_rejects_wide_features(ctx):
     x = (snaps_inputs.population(300, 3) * 10).astype(np.float32)
     pop = snaps.snaps_index(ctx, x, flags=0)
     try:
-        for prec in (snaps.SNAPS_TC_F16, snaps.SNAPS_TC_BF16, 3):
+        for prec in (snaps.SNAPS_TC_F16, snaps.SNAPS_TC_BF16, snaps.SNAPS_TC_TF32, 4):
             with pytest.raises(snaps.SnapsError) as ei:
                 snaps.snaps_scores(pop, [0b11], 5, precision=prec,
                                    scores=np.zeros((1, 4, 300), np.float32))
