@@ -40,7 +40,7 @@
 // float 15, and lists, ties and outputs use original indices, so results do
 // not depend on the order.  A query's stream starts at its own tile -- its
 // neighbourhood in those features -- and wraps around.  A set-up phase (out
-// of line) first bounds every subspace's k-th distance from the first 1,024
+// of line) first bounds every subspace's k-th distance from the first 768
 // candidates of the stream: each lane keeps, per subspace, the smallest of its
 // own candidates' distances, and the k-th smallest of those 32 group minima
 // is an upper bound (k distinct candidates lie at or below it).  Each list
@@ -67,13 +67,13 @@ namespace {
 constexpr int kLB = kTreeLowBits;  // 5
 constexpr int kW = kTreeWidth;     // 32 subspaces per chunk
 constexpr int kTile = 256;
-constexpr int kInit = 1024;        // candidates that bound the k-th distances in the set-up phase
+constexpr int kInit = 768;         // candidates that bound the k-th distances in the set-up phase
 constexpr int kTBuf = 1024;        // event tuples buffered per warp
 // The buffer's tail stages an append's candidates (7 x 32 float2) and its
 // list of (lane, subspace) pairs (at most 32 x 32 halfwords): 480 tuples' room.
 constexpr int kTStage = kTBuf - 480;
 constexpr int kTFlushAt = kTStage - 64;  // a round of appends adds at most 64 tuples
-constexpr int kFlushMin = 64;      // tuples that trigger an end-of-step flush
+constexpr int kFlushMin = 32;      // tuples that trigger an end-of-step flush
 
 // Depth-first order of the subset tree over the low kLB bits: node L's parent
 // is L with its lowest set bit cleared, and its children add a bit below that.
@@ -211,14 +211,13 @@ __device__ __forceinline__ void list_offer(float *ld, int *lj, int k, float d2, 
 }
 
 // Process the buffered kNN candidates (the appends count the eps-neighbours
-// themselves).  First, 32 at a time with every lane busy, the candidates
-// still at or below their subspace's current k-th distance are compacted to
-// the front of the buffer.  Then they are offered to their lists, 32 at a
-// time: lanes holding candidates of different subspaces insert at the same
-// time (each into its own list); of the lanes that share a subspace, one per
-// round claims the list (the last writer of a shared slot), the others retry.
-// The k smallest (distance, original index) pairs do not depend on the order
-// of insertion.  Returns true when a kNN list changed.
+// themselves), 32 at a time: lanes holding candidates of different subspaces
+// insert at the same time (each into its own list); of the lanes that share a
+// subspace, one per round claims the list (the last writer of a shared slot),
+// the others retry.  A candidate that a list no longer admits (its k-th
+// distance fell since the append) is turned away by the offer.  The k
+// smallest (distance, original index) pairs do not depend on the order of
+// insertion.  Returns true when a kNN list changed.
 template <int KMAX>
 __device__ __noinline__ bool flush_tuples(int ws_off, int count, int k)
 {
@@ -226,26 +225,9 @@ __device__ __noinline__ bool flush_tuples(int ws_off, int count, int k)
     const unsigned lane = dev::lane_id();
     unsigned changed = 0;  // bit L: list L changed
     __syncwarp();
-    // the candidates still at or below their subspace's k-th distance are
-    // compacted to the front of the buffer (in place: a batch writes at most as
-    // many as it read)
-    int nw = 0;
     for (int b = 0; b < count; b += 32) {
         const int idx = b + (int)lane;
         const bool ok = idx < count;
-        const uint2 t = ok ? ws.tbuf[idx] : make_uint2(0x7f800000u, 0u);
-        const int L = (int)(t.y >> 24);
-        const float d2 = __uint_as_float(t.x);
-        const bool want = ok && d2 <= ws.T[L];  // T is -inf for inactive subspaces and k = 0
-        const unsigned wb = __ballot_sync(dev::kFull, want);
-        if (want) ws.tbuf[nw + __popc(wb & ((1u << lane) - 1u))] = t;
-        nw += __popc(wb);
-        __syncwarp();
-    }
-    // then the kNN offers, 32 candidates at a time
-    for (int b = 0; b < nw; b += 32) {
-        const int idx = b + (int)lane;
-        const bool ok = idx < nw;
         const uint2 t = ok ? ws.tbuf[idx] : make_uint2(0x7f800000u, 0u);
         const int L = (int)(t.y >> 24);
         const int j = (int)(t.y & 0xffffffu);
