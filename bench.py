@@ -47,12 +47,12 @@ MUFU_PER_SM_CLK = 16         # special-function (square root) throughput per SM 
 FMA_LANES_PER_SM_CLK = 128   # FP32 add / FMA lane-operations per SM per clock
 # DRAM bytes (read + write) per pair-subspace evaluation, from one ncu capture
 # of each kernel as it stands (dram__bytes_read.sum + dram__bytes_write.sum):
-# the tree join on one 32-subspace chunk at N = 31,693 (7.83 MB + 3.41 MB),
+# the tree join on one 32-subspace chunk at N = 31,693 (7.82 MB + 3.44 MB),
 # the tensor-core join on one block of 256 subspaces at N = 31,693 (351 MB +
 # 980 MB: its per-query writes scatter over 256 output rows, which the L2
 # cannot hold).  Both kernels read their candidates from L2, so DRAM traffic
 # grows with the evaluations only through the outputs and the row copies.
-TREE_DRAM_BYTES_PER_EVAL = (7.826432e6 + 3.408384e6) / (31693 * 31692 * 32)
+TREE_DRAM_BYTES_PER_EVAL = (7.822592e6 + 3.436544e6) / (31693 * 31692 * 32)
 TC_DRAM_BYTES_PER_EVAL = (350.9632e6 + 980.276224e6) / (31693 * 31692 * 256)
 
 
@@ -313,7 +313,7 @@ def run_ours(args, rank, world, dist):
                 "executed_basis": "64-row steps of the candidate streams loaded and evaluated over all steps "
                                   "(the rest skipped by their box bound, which proves every pair fails), "
                                   "counted by the kernel during the timed steps",
-                "traffic_basis": "DRAM bytes per launch: an ncu capture of one 32-subspace chunk (11.2 MB for "
+                "traffic_basis": "DRAM bytes per launch: an ncu capture of one 32-subspace chunk (11.3 MB for "
                                  "3.2e10 evaluations) scaled by the launch's evaluations",
                 "peak_basis": f"{props.multi_processor_count} SMs x {COMPARES_PER_SM_CLK} FP32 "
                               f"compares/clk x {max_mhz:.0f} MHz (one compare per pair-subspace "
