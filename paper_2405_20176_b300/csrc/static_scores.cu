@@ -118,7 +118,7 @@ extern "C" snaps_status snaps_scores_static(int device, const float *feat, int64
     std::lock_guard<std::mutex> guard(g_static_mu);
     // The array's device address, with this device current.  Looked up on
     // every call: after a context reset the module is loaded again and the
-    // address can change.  The first call on a device may make the driver
+    // address can change.  The first call on a device may make the CUDA driver
     // load the library's device code, and with it create the array.
     void *addr = nullptr;
     {
