@@ -40,3 +40,21 @@ def test_no_device_is_an_error_status():
     with pytest.raises(snaps.SnapsError) as ei:
         snaps.snaps_create(0)
     assert ei.value.status in (snaps.SNAPS_ECUDA, snaps.SNAPS_EINVAL)
+
+
+def test_binding_constants_match_the_header():
+    import os
+    import re
+    path = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "snaps.h")
+    defines = {}
+    for name, value in re.findall(r"^#define\s+(SNAPS_\w+)\s+(0x[0-9a-fA-F]+|\d+)u?\b", open(path).read(), re.M):
+        defines[name] = int(value, 0)
+    checked = 0
+    for name, value in defines.items():
+        if hasattr(snaps, name):
+            assert getattr(snaps, name) == value, name
+            checked += 1
+    for name in ("SNAPS_FP32", "SNAPS_TC_F16", "SNAPS_TC_BF16", "SNAPS_TC_TF32", "SNAPS_TC_MIN_FILL",
+                 "SNAPS_TC_NEVER", "SNAPS_INDEX_GRID", "SNAPS_INDEX_NONE", "SNAPS_MAX_K"):
+        assert name in defines and hasattr(snaps, name), name
+    assert checked >= 15

@@ -66,3 +66,17 @@ def test_subspace_lists():
     assert pf.size == 106 and int(pf[-1]) == (1 << 15) - 1
     s = snaps_inputs.mask_sample(64, 1)
     assert s.size == 64 and np.all(np.isin(s, m)) and np.unique(s).size == 64
+
+
+def test_chunk_sample_is_whole_chunks():
+    m = snaps_inputs.chunk_sample(8, 1)
+    assert m.dtype == np.uint16 and m.size == 8 * 32
+    assert np.all(np.diff(m.astype(np.int64)) > 0)  # ascending, distinct
+    highs = np.unique(m >> 5)
+    assert highs.size == 8
+    for h in highs:
+        assert bin(int(h)).count("1") >= 2
+        np.testing.assert_array_equal(m[(m >> 5) == h] & 31, np.arange(32))
+    # every mask is a valid subspace of 2..15 features
+    assert all(2 <= bin(int(v)).count("1") <= 15 for v in m)
+    np.testing.assert_array_equal(snaps_inputs.chunk_sample(8, 1), m)
